@@ -1,0 +1,457 @@
+"""Pins for the CPU oracle: each check ties an oracle function to something
+other than itself (published values, closed forms, brute force, the paper's
+printed tables, planted mistakes). CPU only."""
+from __future__ import annotations
+
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from tests import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def csr(n, s, d):
+    return oracle.build_csr(n, s, d)
+
+
+def deg(off):
+    return np.diff(off)
+
+
+# ---------------------------------------------------------------- SplitMix64
+def test_splitmix64_published_outputs():
+    # First three outputs of SplitMix64 seeded with 0 (Vigna's reference
+    # splitmix64.c; Steele, Lea, Flood 2014).
+    assert oracle.sm64(0, 0) == 0xE220A8397B1DCDAF
+    assert oracle.sm64(0, 1) == 0x6E789E6AA1B965F4
+    assert oracle.sm64(0, 2) == 0x06C45D188009454F
+
+
+# ------------------------------------------------------------------ relabel
+@pytest.mark.parametrize("scale", [1, 2, 3, 7, 12, 16])
+def test_relabel_is_a_permutation(scale):
+    n = 1 << scale
+    img = np.array([oracle.relabel(x, scale, 1) for x in range(n)])
+    assert img.min() >= 0 and img.max() < n
+    assert np.unique(img).size == n
+    if scale >= 3:
+        assert (img != np.arange(n)).any()
+
+
+# --------------------------------------------------------------- generator
+def test_rmat_degenerate_initiators_are_closed_forms():
+    scale, seed = 10, 7
+    top = (1 << scale) - 1
+    p0, ptop = oracle.relabel(0, scale, seed), oracle.relabel(top, scale, seed)
+    # A = 1: every bit level picks quadrant (0,0): all edges are pi(0)-pi(0).
+    s, d = oracle.gen_edges(oracle.RMAT, scale, 2, seed, a=1.0, b=0.0, c=0.0)
+    assert (s == p0).all() and (d == p0).all()
+    # B = 1: source bits 0, destination bits 1.
+    s, d = oracle.gen_edges(oracle.RMAT, scale, 2, seed, a=0.0, b=1.0, c=0.0)
+    assert (s == p0).all() and (d == ptop).all()
+    # C = 1: source bits 1, destination bits 0.
+    s, d = oracle.gen_edges(oracle.RMAT, scale, 2, seed, a=0.0, b=0.0, c=1.0)
+    assert (s == ptop).all() and (d == p0).all()
+    # D = 1 - A - B - C = 1.
+    s, d = oracle.gen_edges(oracle.RMAT, scale, 2, seed, a=0.0, b=0.0, c=0.0)
+    assert (s == ptop).all() and (d == ptop).all()
+
+
+def _within(count, mean, sd, k=6.0):
+    return abs(count - mean) <= k * sd + 1
+
+
+def test_rmat_marginals_match_initiator():
+    # With A,B,C,D = .57,.19,.19,.05 (Sec. 6.2): an edge is a self-loop with
+    # probability (A+D)^S; the source is pi(0) with probability (A+B)^S, the
+    # destination is pi(0) with probability (A+C)^S, and the source is
+    # pi(2^S - 1) with probability (C+D)^S.
+    scale, ef, seed = 14, 16, 3
+    a, b, c = 0.57, 0.19, 0.19
+    dd = 1 - a - b - c
+    s, d = oracle.gen_edges(oracle.RMAT, scale, ef, seed)
+    m = s.size
+    p0 = oracle.relabel(0, scale, seed)
+    ptop = oracle.relabel((1 << scale) - 1, scale, seed)
+    for cnt, p in [((s == d).sum(), (a + dd) ** scale),
+                   ((s == p0).sum(), (a + b) ** scale),
+                   ((d == p0).sum(), (a + c) ** scale),
+                   ((s == ptop).sum(), (c + dd) ** scale)]:
+        assert _within(cnt, m * p, np.sqrt(m * p * (1 - p))), (cnt, m * p)
+
+
+def test_er_is_uniform():
+    scale, ef = 12, 16
+    s, d = oracle.gen_edges(oracle.ER, scale, ef, 5)
+    n, m = 1 << scale, s.size
+    assert m == ef * n
+    assert s.min() >= 0 and s.max() < n and d.min() >= 0 and d.max() < n
+    cnt = np.bincount(s, minlength=n)
+    # Poisson(ef) counts: mean ef, variance ef.
+    assert abs(cnt.mean() - ef) < 1e-9
+    assert 0.8 * ef < cnt.var() < 1.2 * ef
+    # self-loops: probability 1/n each
+    assert _within((s == d).sum(), m / n, np.sqrt(m / n))
+
+
+def test_generator_is_counter_based():
+    s, d = oracle.gen_edges(oracle.RMAT, 12, 16, 9)
+    s2, d2 = oracle.gen_edges(oracle.RMAT, 12, 16, 9, first=1000, count=77)
+    assert (s[1000:1077] == s2).all() and (d[1000:1077] == d2).all()
+    s3, _ = oracle.gen_edges(oracle.RMAT, 12, 16, 10)
+    assert (s3 != s).any()
+
+
+@pytest.mark.parametrize("ef,table_reach", [(16, 176864 / 262144), (32, 199849 / 262144)])
+def test_rmat_scale18_matches_paper_reach(ef, table_reach):
+    # Table 2 (ef 16): sum of v_f = 176,864 of 2^18 vertices reached.
+    # Table 4 (ef 32): NV falls to 62,295 before the last layer, about 76%.
+    # The BFS depth is 5-6 layers (Sec. 5.2). Our generator is not Graph500's
+    # bit for bit, so the check is soft: within 5 points and 4-8 layers.
+    scale = 18
+    s, d = oracle.gen_edges(oracle.RMAT, scale, ef, 1)
+    off, idx = csr(1 << scale, s, d)
+    roots = oracle.sample_roots(off, 1 << scale, 2, 4)
+    for r in roots:
+        lv, _ = oracle.bfs(off, idx, int(r))
+        reach = (lv >= 0).mean()
+        if reach < 0.01:
+            continue  # root in a small component
+        assert abs(reach - table_reach) < 0.05, reach
+        assert 4 <= lv.max() <= 8
+
+
+# ---------------------------------------------------------------------- CSR
+def brute_csr(n, s, d):
+    rows = [set() for _ in range(n)]
+    for a, b in zip(s.tolist(), d.tolist()):
+        if a != b:
+            rows[a].add(b)
+            rows[b].add(a)
+    off = [0]
+    idx = []
+    for r in rows:
+        idx.extend(sorted(r))
+        off.append(len(idx))
+    return np.array(off, np.int64), np.array(idx, np.int32)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_csr_matches_brute_force(seed):
+    n = [1, 2, 5, 33, 64, 100][seed]
+    s, d = inputs.random_edges(n, 4 * n + 3, seed)
+    off, idx = csr(n, s, d)
+    bo, bi = brute_csr(n, s, d)
+    assert (off == bo).all() and (idx == bi).all()
+
+
+def test_csr_invariants_rmat():
+    n = 1 << 12
+    s, d = oracle.gen_edges(oracle.RMAT, 12, 16, 1)
+    off, idx = csr(n, s, d)
+    assert off[0] == 0 and off[-1] == idx.size and (np.diff(off) >= 0).all()
+    src = np.repeat(np.arange(n), np.diff(off))
+    assert (src != idx).all()                                  # no self-loops
+    key = src.astype(np.int64) * n + idx
+    assert (np.diff(key) > 0).all()                            # sorted, no dups
+    rev = np.sort(idx.astype(np.int64) * n + src)
+    assert (rev == key).all()                                  # symmetric
+
+
+def test_csr_rejects_out_of_range():
+    with pytest.raises(ValueError):
+        oracle.build_csr(4, np.array([0, 4], np.int32), np.array([1, 2], np.int32))
+
+
+# -------------------------------------------------------------------- roots
+def test_roots_first_candidate_and_properties():
+    n = 1 << 10
+    s, d = inputs.cycle_edges(n)
+    off, _ = csr(n, s, d)
+    r = oracle.sample_roots(off, n, 0, 64)
+    # every vertex of a cycle has degree 2, so candidate 0 is taken:
+    assert r[0] == 0xE220A8397B1DCDAF % n
+    assert r.size == 64 and np.unique(r).size == 64
+    # degree-0 vertices are never drawn, and the draw stops when none remain
+    n2, s2, d2 = inputs.union((3, *inputs.path_edges(3)), (50, [], []))
+    off2, _ = csr(n2, s2, d2)
+    r2 = oracle.sample_roots(off2, n2, 1, 10, max_draws=100000)
+    assert sorted(r2.tolist()) == [0, 1, 2]
+
+
+# ---------------------------------------------------------------------- BFS
+def check_tree(off, idx, root, lv, pa):
+    assert oracle.check_parents(off, idx, root, lv, pa) == 0
+    assert pa[root] == root and lv[root] == 0
+
+
+def test_bfs_path_cycle_star_complete():
+    n = 37
+    off, idx = csr(n, *inputs.path_edges(n))
+    for r in [0, 5, 36]:
+        lv, pa = oracle.bfs(off, idx, r)
+        assert (lv == np.abs(np.arange(n) - r)).all()
+        check_tree(off, idx, r, lv, pa)
+    for n in [8, 9]:
+        off, idx = csr(n, *inputs.cycle_edges(n))
+        lv, _ = oracle.bfs(off, idx, 2)
+        k = np.abs(np.arange(n) - 2)
+        assert (lv == np.minimum(k, n - k)).all()
+    off, idx = csr(20, *inputs.star_edges(20))
+    lv, pa = oracle.bfs(off, idx, 0)
+    assert lv[0] == 0 and (lv[1:] == 1).all() and (pa[1:] == 0).all()
+    lv, pa = oracle.bfs(off, idx, 7)
+    exp = np.full(20, 2); exp[0] = 1; exp[7] = 0
+    assert (lv == exp).all()
+    off, idx = csr(12, *inputs.complete_edges(12))
+    lv, _ = oracle.bfs(off, idx, 4)
+    assert (lv == np.where(np.arange(12) == 4, 0, 1)).all()
+
+
+def test_bfs_grid_and_hypercube():
+    R, C = 9, 13
+    off, idx = csr(R * C, *inputs.grid_edges(R, C))
+    r = 3 * C + 5
+    lv, pa = oracle.bfs(off, idx, r)
+    rr, cc = np.divmod(np.arange(R * C), C)
+    assert (lv == np.abs(rr - 3) + np.abs(cc - 5)).all()
+    check_tree(off, idx, r, lv, pa)
+    dim = 8
+    off, idx = csr(1 << dim, *inputs.hypercube_edges(dim))
+    lv, _ = oracle.bfs(off, idx, 77)
+    pop = np.array([bin(v ^ 77).count("1") for v in range(1 << dim)])
+    assert (lv == pop).all()
+
+
+def test_bfs_disconnected_and_isolated_root():
+    n, s, d = inputs.union((10, *inputs.path_edges(10)), (5, *inputs.cycle_edges(5)), (3, [], []))
+    off, idx = csr(n, s, d)
+    lv, pa = oracle.bfs(off, idx, 0)
+    assert (lv[:10] == np.arange(10)).all() and (lv[10:] == -1).all() and (pa[10:] == -1).all()
+    lv, pa = oracle.bfs(off, idx, 16)                      # isolated vertex
+    assert lv[16] == 0 and pa[16] == 16 and (np.delete(lv, 16) == -1).all()
+
+
+def floyd_warshall(n, s, d):
+    INF = 10 ** 9
+    D = np.full((n, n), INF, dtype=np.int64)
+    np.fill_diagonal(D, 0)
+    for a, b in zip(s.tolist(), d.tolist()):
+        if a != b:
+            D[a, b] = D[b, a] = 1
+    for k in range(n):
+        D = np.minimum(D, D[:, k:k + 1] + D[k:k + 1, :])
+    return np.where(D >= INF, -1, D)
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_bfs_matches_all_pairs_brute_force(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(2, 48))
+    m = int(rng.integers(0, 3 * n))
+    s, d = inputs.random_edges(n, m, seed + 100)
+    off, idx = csr(n, s, d)
+    D = floyd_warshall(n, s, d)
+    for r in range(n):
+        lv, pa = oracle.bfs(off, idx, r)
+        assert (lv == D[r]).all()
+        check_tree(off, idx, r, lv, pa)
+
+
+# ----------------------------------------------------------- hybrid (Alg. 3)
+def first_frontier_neighbour(off, idx, lv, v):
+    for e in range(off[v], off[v + 1]):
+        if lv[idx[e]] == lv[v] - 1:
+            return idx[e]
+    return None
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_hybrid_levels_and_parents_under_any_policy(seed):
+    rng = np.random.default_rng(seed)
+    if seed % 3 == 0:
+        n = 1 << 10
+        s, d = oracle.gen_edges(oracle.RMAT, 10, 8, seed)
+    elif seed % 3 == 1:
+        n = int(rng.integers(30, 300))
+        s, d = inputs.powerlaw_edges(n, 4 * n, seed)
+    else:
+        n = int(rng.integers(30, 300))
+        s, d = inputs.random_edges(n, 2 * n, seed)
+    off, idx = csr(n, s, d)
+    root = int(np.argmax(deg(off)))
+    ref, _ = oracle.bfs(off, idx, root)
+    depth = ref.max()
+    pats = {"td": [0], "bu": [1], "alt": [0, 1] * 40, "alt2": [1, 0] * 40,
+            "rand": rng.integers(0, 2, size=depth + 2).tolist()}
+    runs = [(oracle.POLICY_EDGE, None), (oracle.POLICY_VERTEX, None)]
+    runs += [(oracle.POLICY_FORCED, p) for p in pats.values()]
+    for pol, forced in runs:
+        lv, pa, dirs, tr = oracle.hybrid_bfs(off, idx, root, pol, forced=forced)
+        assert (lv == ref).all()
+        check_tree(off, idx, root, lv, pa)
+        assert len(dirs) == depth + 1
+        for dd in range(depth + 1):
+            layer = np.nonzero(ref == dd)[0]
+            assert tr[dd, 0] == layer.size                         # v_f
+            assert tr[dd, 1] == deg(off)[layer].sum()               # e_f
+            assert tr[dd, 2] == (ref > dd).sum() + (ref < 0).sum()  # n_u
+            if dirs[dd] == 1:
+                # bottom-up parents are the first frontier hit in CSR order
+                nxt = np.nonzero(ref == dd + 1)[0]
+                for v in nxt:
+                    assert pa[v] == first_frontier_neighbour(off, idx, ref, v)
+        if forced is not None:
+            assert list(dirs) == [forced[min(i, len(forced) - 1)] for i in range(depth + 1)]
+
+
+def test_hybrid_bottom_up_examined_edges_brute_force():
+    n = 200
+    s, d = inputs.powerlaw_edges(n, 800, 4)
+    off, idx = csr(n, s, d)
+    root = int(np.argmax(deg(off)))
+    lv, pa, dirs, tr = oracle.hybrid_bfs(off, idx, root, oracle.POLICY_FORCED, forced=[1])
+    for dd in range(len(dirs)):
+        exp = 0
+        for v in range(n):
+            if 0 <= lv[v] <= dd:
+                continue
+            row = idx[off[v]:off[v + 1]].tolist()
+            hits = [i for i, u in enumerate(row) if lv[u] == dd]
+            exp += (hits[0] + 1) if hits else len(row)
+        assert tr[dd, 4] == exp
+
+
+# ----------------------------------------------------------- direction policy
+def read_rows(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+def test_policy_replays_table2():
+    n = 1 << 18
+    rows = read_rows("table2_hybrid_trace_scale18_ef16.txt")
+    cur, got = 0, []
+    for layer, v_f, n_u, f, g, approach in rows:
+        v_f, n_u, f, g = int(v_f), int(n_u), int(f), int(g)
+        assert f == n_u >> 10 and g == n >> 6          # f, g columns
+        cur = oracle.policy_decide(oracle.POLICY_VERTEX, cur, n, v_f, 0, n_u, 0)
+        got.append("BU" if cur else "TD")
+    assert got == [r[5] for r in rows]
+    # arithmetic of the printed columns
+    vf = [int(r[1]) for r in rows]
+    nu = [int(r[2]) for r in rows]
+    assert nu[0] == n - 1
+    assert all(nu[i] == nu[i - 1] - vf[i] for i in range(1, len(rows)))
+    # the literal, state-free reading of Alg. 3 disagrees with layer 5
+    lit, cur = [], 0
+    for _, v_f, n_u, f, g, _a in rows:
+        if int(v_f) > int(f):
+            cur = 1
+        elif int(v_f) < int(g):
+            cur = 0
+        lit.append("BU" if cur else "TD")
+    assert lit != got and lit[4] == "BU"
+
+
+def test_policy_replays_table4():
+    n = 1 << 18
+    rows = read_rows("table4_hybrid_layers_scale18_ef32.txt")
+    nv = [int(r[2]) for r in rows]
+    vf = [1] + [nv[i - 1] - nv[i] for i in range(1, len(nv))]
+    cur, got = 0, []
+    for v_f, n_u in zip(vf, nv):
+        cur = oracle.policy_decide(oracle.POLICY_VERTEX, cur, n, v_f, 0, n_u, 0)
+        got.append("BU" if cur else "TD")
+    assert got == [r[1] for r in rows]
+
+
+def test_policy_edge_form_thresholds():
+    n = 960                       # n / beta = 40 exactly for beta = 24
+    P = oracle.POLICY_EDGE
+    # top-down -> bottom-up iff e_f > e_u / alpha  (1960 / 14 = 140)
+    assert oracle.policy_decide(P, 0, n, 10, 141, 500, 1960, 14.0, 24.0) == 1
+    assert oracle.policy_decide(P, 0, n, 10, 140, 500, 1960, 14.0, 24.0) == 0
+    # bottom-up -> top-down iff |in| < n / beta; e_f plays no part there
+    assert oracle.policy_decide(P, 1, n, 41, 10 ** 6, 5, 1, 14.0, 24.0) == 1
+    assert oracle.policy_decide(P, 1, n, 40, 0, 5, 1, 14.0, 24.0) == 1
+    assert oracle.policy_decide(P, 1, n, 39, 0, 5, 1, 14.0, 24.0) == 0
+    assert oracle.policy_decide(P, 1, n, 40, 0, 5, 1, 14.0, 23.0) == 0   # 960 / 23 > 40
+    assert oracle.policy_decide(P, 1, n, 40, 0, 5, 1, 14.0, 25.0) == 1   # 960 / 25 < 40
+
+
+# ------------------------------------------------------------- validators
+def test_check_levels_rejects_planted_mistakes():
+    rng = np.random.default_rng(0)
+    n = 400
+    s, d = inputs.random_edges(n, 900, 1)
+    off, idx = csr(n, s, d)
+    root = int(np.argmax(deg(off)))
+    lv, pa = oracle.bfs(off, idx, root)
+    assert oracle.check_levels(off, idx, root, lv) == 0
+    reached = np.nonzero(lv > 0)[0]
+    unreached = np.nonzero(lv < 0)[0]
+    for v in rng.choice(reached, 20, replace=False):
+        for delta in (-1, 1, 2):
+            bad = lv.copy(); bad[v] += delta
+            assert oracle.check_levels(off, idx, root, bad) != 0
+        bad = lv.copy(); bad[v] = -1
+        assert oracle.check_levels(off, idx, root, bad) != 0
+    if unreached.size:
+        bad = lv.copy(); bad[unreached[0]] = 3
+        assert oracle.check_levels(off, idx, root, bad) != 0
+    # a consistent shift of everything except the root must also fail
+    bad = np.where(lv > 0, lv + 1, lv)
+    assert oracle.check_levels(off, idx, root, bad) != 0
+
+
+def test_check_parents_rejects_planted_mistakes():
+    n = 300
+    s, d = inputs.random_edges(n, 1200, 2)
+    off, idx = csr(n, s, d)
+    root = 5
+    lv, pa = oracle.bfs(off, idx, root)
+    assert oracle.check_parents(off, idx, root, lv, pa) == 0
+    for v in np.nonzero(lv > 1)[0][:30]:
+        bad = pa.copy(); bad[v] = root          # not adjacent or wrong level
+        if root not in idx[off[v]:off[v + 1]].tolist():
+            assert oracle.check_parents(off, idx, root, lv, bad) != 0
+        bad = pa.copy(); bad[v] = v
+        assert oracle.check_parents(off, idx, root, lv, bad) != 0
+        same = [u for u in idx[off[v]:off[v + 1]].tolist() if lv[u] == lv[v]]
+        if same:
+            bad = pa.copy(); bad[v] = same[0]   # an edge, but the same level
+            assert oracle.check_parents(off, idx, root, lv, bad) != 0
+    bad = pa.copy(); bad[root] = -1
+    assert oracle.check_parents(off, idx, root, lv, bad) != 0
+
+
+def test_min_parent_brute_force():
+    n = 150
+    s, d = inputs.random_edges(n, 500, 3)
+    off, idx = csr(n, s, d)
+    lv, _ = oracle.bfs(off, idx, 0)
+    mp = oracle.min_parent(off, idx, 0, lv)
+    for v in range(n):
+        nb = idx[off[v]:off[v + 1]].tolist()
+        cands = [u for u in nb if lv[v] > 0 and lv[u] == lv[v] - 1]
+        exp = 0 if v == 0 else (min(cands) if cands else -1)
+        assert mp[v] == exp
+
+
+def test_component_edges_closed_forms():
+    n, s, d = inputs.union((10, *inputs.path_edges(10)), (6, *inputs.complete_edges(6)))
+    off, idx = csr(n, s, d)
+    lv, _ = oracle.bfs(off, idx, 3)
+    assert oracle.component_edges(off, lv) == 9
+    lv, _ = oracle.bfs(off, idx, 12)
+    assert oracle.component_edges(off, lv) == 15
