@@ -1,0 +1,203 @@
+/*
+ * bfs.h -- C ABI of the GB300 hybrid breadth-first-search library.
+ *
+ * The library implements the hybrid BFS of Paredes, Riley and Lujan,
+ * "Vectorization of Hybrid Breadth First Search on the Intel Xeon Phi":
+ * a layer-synchronous traversal (Sec. 4) that runs each layer either as the
+ * top-down step of Alg. 1 or as the bottom-up step of Alg. 2 / Sec. 5, the
+ * direction being chosen per layer by the switch of Alg. 3. Every step runs in
+ * this library's own CUDA kernels for sm_103a on one GPU.
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns a bfs_status. Nothing aborts, nothing traps; on an
+ *     error bfs_last_error() returns a message for the calling thread.
+ *   - Arguments are checked on the host before any launch: null pointers,
+ *     sizes out of range and roots outside [0, n) give BFS_ERR_INVALID.
+ *   - Vertex ids are int32 in [0, n), n < 2^31. CSR offsets are int64
+ *     (n + 1 entries, offsets[0] = 0, offsets[n] = nnz); CSR indices are
+ *     int32 (nnz entries). The graph must be symmetric: the bottom-up step
+ *     reads Adj[v] as the in-edges of v (Sec. 6.2, edges are bidirectional).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream). Device pointers must belong to the current CUDA device.
+ *   - Output encoding (Sec. 4, the predecessor list P): level[v] is the hop
+ *     distance from the root, -1 when unreachable; parent[root] = root,
+ *     parent[v] = -1 when unreachable.
+ *   - A bfs_graph is not thread-safe: one call at a time per graph.
+ */
+#ifndef GB300_HYBRID_BFS_H
+#define GB300_HYBRID_BFS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define BFS_API __attribute__((visibility("default")))
+#else
+#define BFS_API
+#endif
+
+typedef enum bfs_status {
+    BFS_OK = 0,
+    BFS_ERR_INVALID = 1,   /* bad argument; nothing was launched            */
+    BFS_ERR_OOM = 2,       /* a device or pinned allocation failed          */
+    BFS_ERR_CUDA = 3,      /* a CUDA call failed; see bfs_last_error()      */
+    BFS_ERR_TIMEOUT = 4,   /* a bounded device-side wait ran out            */
+    BFS_ERR_DEPTH = 5,     /* an int8 level would exceed 127                */
+    BFS_ERR_BUSY = 6,      /* the server has no room for the request        */
+    BFS_ERR_SHUTDOWN = 7   /* the server is shutting down                   */
+} bfs_status;
+
+/* Message for the last failed call made by this thread ("" if none). */
+BFS_API const char *bfs_last_error(void);
+
+/* Number of kernels this library has launched in this process so far. */
+BFS_API int64_t bfs_launch_count(void);
+
+/* ---------------------------------------------------------------------- */
+/* Graph generation (Sec. 6.2: Graph500 Kronecker graphs built on the      */
+/* R-MAT model with initiator A, B, C, D).                                 */
+/* ---------------------------------------------------------------------- */
+#define BFS_GEN_RMAT 0   /* R-MAT / Kronecker, initiator (a, b, c, 1-a-b-c) */
+#define BFS_GEN_ER 1     /* Erdos-Renyi control: uniform endpoints          */
+
+/* Writes the m = edgefactor * 2^scale generated edges (src[e], dst[e]) into
+ * caller-owned device arrays of m int32 each. scale in [1, 30].
+ * Edge e at bit level b draws the high 32 bits of SplitMix64 output
+ * e*scale + b of `seed` and picks a quadrant by comparing them with
+ * floor(a*2^32), floor((a+b)*2^32), floor((a+b+c)*2^32); the bits are then
+ * relabelled by a seeded bijection of [0, 2^scale). The ER control uses the
+ * top `scale` bits of outputs 2e and 2e+1. Stream-ordered; returns at once. */
+BFS_API bfs_status bfs_generate_edges(int32_t kind, int32_t scale, int32_t edgefactor,
+                                      uint64_t seed, double a, double b, double c,
+                                      int32_t *src, int32_t *dst, void *stream);
+
+/* Symmetric CSR from an edge list (Sec. 6.2: each edge is stored in both
+ * directions; Sec. 6.3: CSR). Self-loops are dropped, every row is sorted
+ * ascending and duplicates are removed.
+ *   src, dst    device, m int32 each, endpoints in [0, n)
+ *   offsets     device, caller-owned, n + 1 int64 (written)
+ *   indices     device, caller-owned, room for 2*m int32 (first nnz written)
+ *   nnz_out     host, receives nnz
+ * Temporary device memory (about 16*m bytes) is taken with cudaMallocAsync
+ * on `stream` and released before return. Synchronises `stream`.
+ * An endpoint outside [0, n) gives BFS_ERR_INVALID. */
+BFS_API bfs_status bfs_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                                 int64_t *offsets, int32_t *indices, int64_t *nnz_out,
+                                 void *stream);
+
+/* Seeded distinct roots of degree >= 1 (Sec. 6.3: 64 BFS executions from
+ * random starting vertices; degree-0 roots would report zero TEPS).
+ * Candidate j = SplitMix64 output j of `seed` modulo n; candidates are taken
+ * in order, skipping degree-0 vertices and repeats, until k are chosen or
+ * max_draws candidates were seen.
+ *   offsets     device, n + 1 int64
+ *   roots_out   device, k int32 (first *count_out written)
+ *   count_out   host, number of roots chosen (may be < k)
+ * k in [1, 4096]. Synchronises `stream`. */
+BFS_API bfs_status bfs_sample_roots(const int64_t *offsets, int64_t n, uint64_t seed, int32_t k,
+                                    int64_t max_draws, int32_t *roots_out, int32_t *count_out,
+                                    void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Graphs and the single-source hybrid BFS (Alg. 1-3, Sec. 5).             */
+/* ---------------------------------------------------------------------- */
+typedef struct bfs_graph bfs_graph;
+
+/* Direction policies for Alg. 3 (tests hold hysteresis: in top-down mode
+ * switch to bottom-up iff the f test passes; in bottom-up mode switch back
+ * iff the g test passes; layer 0 starts top-down).                        */
+#define BFS_POLICY_EDGE 0    /* f: e_f > e_u / alpha ; g: v_f < n / beta       */
+#define BFS_POLICY_VERTEX 1  /* f: v_f > n_u >> 10   ; g: v_f < n >> 6 (Table 2)*/
+#define BFS_POLICY_FORCED 2  /* layer d runs forced[min(d, forced_len-1)]      */
+
+typedef struct bfs_config {
+    int32_t policy;          /* BFS_POLICY_*                                  */
+    int32_t forced_len;      /* 1..64 entries used by BFS_POLICY_FORCED       */
+    uint8_t forced[64];      /* 0 = top-down, 1 = bottom-up                   */
+    double alpha;            /* edge policy, top-down -> bottom-up            */
+    double beta;             /* edge policy, bottom-up -> top-down            */
+    int32_t bu_probe;        /* neighbours a thread tests on its own in the
+                                bottom-up step before the warp-cooperative
+                                scan takes over (the MAX_POS of Sec. 5.2);
+                                1..64                                          */
+    int32_t td_warp_degree;  /* top-down: degree from which one warp expands
+                                a vertex (smaller ones share a warp)           */
+    int32_t td_grid_degree;  /* top-down: degree from which a vertex's edges
+                                are spread over the whole grid                 */
+    int32_t timing;          /* 1 = record CUDA events around each layer      */
+    int32_t reserved[8];
+} bfs_config;
+
+/* Fills `cfg` with the defaults (edge policy, alpha 14, beta 24, ...). */
+BFS_API void bfs_config_default(bfs_config *cfg);
+
+#define BFS_DEVICE_PTRS 1u  /* offsets / indices are device pointers           */
+#define BFS_BORROW 2u       /* keep the caller's device arrays (no copy); they
+                               must outlive the graph. Needs BFS_DEVICE_PTRS.  */
+#define BFS_VALIDATE 4u     /* check offsets[0]=0, monotone offsets,
+                               offsets[n]=nnz and indices in [0, n)            */
+
+/* Creates a graph from a symmetric CSR (layout above) and allocates its
+ * per-traversal scratch: three n-bit bitmaps (visited, frontier, next), two
+ * n-entry vertex queues and a small counter block, about 8.4*n bytes.
+ * Without BFS_BORROW the CSR is copied into library memory and the caller may
+ * free its arrays. cfg may be NULL (defaults). Synchronous. */
+BFS_API bfs_status bfs_graph_create(const int64_t *offsets, const int32_t *indices, int64_t n,
+                                    int64_t nnz, uint32_t flags, const bfs_config *cfg,
+                                    bfs_graph **out);
+
+/* Replaces the graph's configuration (cfg may be NULL for the defaults). */
+BFS_API bfs_status bfs_graph_set_config(bfs_graph *g, const bfs_config *cfg);
+
+/* Device pointers and sizes of the graph's CSR (library- or caller-owned). */
+BFS_API bfs_status bfs_graph_info(const bfs_graph *g, const int64_t **offsets,
+                                  const int32_t **indices, int64_t *n, int64_t *nnz);
+
+/* Frees everything the graph owns. NULL is accepted. */
+BFS_API bfs_status bfs_graph_destroy(bfs_graph *g);
+
+/* Hybrid BFS from `root` (Alg. 3). level_out / parent_out are n int32 each,
+ * caller-owned, either both device memory or both host memory (pageable or
+ * pinned); parent_out may be NULL. With host buffers the results are copied
+ * back before return. Work is ordered on `stream`; the host reads the layer
+ * counters after every layer to choose the next direction, so the call
+ * returns after the traversal has finished. Parents found by a bottom-up
+ * layer are the first frontier neighbour in CSR order (Alg. 2); parents found
+ * by a top-down layer are whichever frontier neighbour claimed the vertex
+ * first (any valid tree, Sec. 7.1). */
+BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level_out, int32_t *parent_out,
+                           void *stream);
+
+/* Per-layer record of the last bfs_run on this graph. Layer d is the
+ * frontier of the vertices at level d. Counters follow Sec. 4: v_f (n_f),
+ * e_f (m_f), and the unvisited vertex / edge counts n_u, m_u.             */
+typedef struct bfs_layer_stats {
+    int32_t direction;  /* 0 = top-down, 1 = bottom-up                          */
+    int32_t converted;  /* 1 = the frontier bitmap was turned into a queue     */
+    int64_t n_f;        /* vertices in the frontier                            */
+    int64_t m_f;        /* sum of their degrees                                */
+    int64_t n_u;        /* vertices not yet visited                            */
+    int64_t m_u;        /* sum of their degrees                                */
+    int64_t examined;   /* edges examined: all frontier edges top-down; up to
+                           and including the first hit (or the whole row)
+                           bottom-up                                           */
+    int64_t found;      /* vertices of the next layer                          */
+    float ms_total;     /* layer time, when cfg.timing = 1 (else 0)            */
+    float ms_main;      /* time of the layer's main step kernel                */
+} bfs_layer_stats;
+
+/* Copies up to `cap` layer records of the last run into `out`; *layers gets
+ * the number of layers, *component_edges the undirected edges inside the
+ * root's component (half the degree sum of the reached vertices: the TEPS
+ * numerator, Sec. 6.3). Any output pointer may be NULL. */
+BFS_API bfs_status bfs_last_run_stats(const bfs_graph *g, bfs_layer_stats *out, int32_t cap,
+                                      int32_t *layers, int64_t *component_edges);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_HYBRID_BFS_H */

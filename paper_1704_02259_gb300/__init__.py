@@ -1,0 +1,226 @@
+"""Python binding of the GB300 hybrid BFS library (include/bfs.h).
+
+Argument marshalling only: every step runs in the library's CUDA kernels.
+Tensors are passed as raw pointers, streams as ``torch.cuda.current_stream()``
+handles. If the shared library has not been built this module raises; there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import _build
+
+BFS_OK = 0
+STATUS = {0: "BFS_OK", 1: "BFS_ERR_INVALID", 2: "BFS_ERR_OOM", 3: "BFS_ERR_CUDA",
+          4: "BFS_ERR_TIMEOUT", 5: "BFS_ERR_DEPTH", 6: "BFS_ERR_BUSY", 7: "BFS_ERR_SHUTDOWN"}
+
+GEN_RMAT = 0
+GEN_ER = 1
+POLICY_EDGE = 0
+POLICY_VERTEX = 1
+POLICY_FORCED = 2
+DEVICE_PTRS = 1
+BORROW = 2
+VALIDATE = 4
+
+
+class BfsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("policy", ctypes.c_int32), ("forced_len", ctypes.c_int32),
+                ("forced", ctypes.c_uint8 * 64), ("alpha", ctypes.c_double),
+                ("beta", ctypes.c_double), ("bu_probe", ctypes.c_int32),
+                ("td_warp_degree", ctypes.c_int32), ("td_grid_degree", ctypes.c_int32),
+                ("timing", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8)]
+
+
+class LayerStats(ctypes.Structure):
+    _fields_ = [("direction", ctypes.c_int32), ("converted", ctypes.c_int32),
+                ("n_f", ctypes.c_int64), ("m_f", ctypes.c_int64), ("n_u", ctypes.c_int64),
+                ("m_u", ctypes.c_int64), ("examined", ctypes.c_int64), ("found", ctypes.c_int64),
+                ("ms_total", ctypes.c_float), ("ms_main", ctypes.c_float)]
+
+
+_lib = None
+P = ctypes.c_void_p
+I32, I64, U32, U64, DBL = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
+
+# name -> (restype, argtypes); exactly the entry points include/bfs.h declares
+SIGNATURES = {
+    "bfs_last_error": (ctypes.c_char_p, []),
+    "bfs_launch_count": (I64, []),
+    "bfs_generate_edges": (I32, [I32, I32, I32, U64, DBL, DBL, DBL, P, P, P]),
+    "bfs_build_csr": (I32, [I64, I64, P, P, P, P, P, P]),
+    "bfs_sample_roots": (I32, [P, I64, U64, I32, I64, P, P, P]),
+    "bfs_config_default": (None, [P]),
+    "bfs_graph_create": (I32, [P, P, I64, I64, U32, P, P]),
+    "bfs_graph_set_config": (I32, [P, P]),
+    "bfs_graph_info": (I32, [P, P, P, P, P]),
+    "bfs_graph_destroy": (I32, [P]),
+    "bfs_run": (I32, [P, I32, P, P, P]),
+    "bfs_last_run_stats": (I32, [P, P, I32, P, P]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load the built library; raises if it is missing (no fallback)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build the CUDA library first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def build(force: bool = False) -> str:
+    return _build.build(force=force)
+
+
+def _check(status: int):
+    if status != BFS_OK:
+        raise BfsError(status, lib().bfs_last_error().decode())
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None):
+    return ctypes.c_void_p(t.data_ptr() if t is not None else 0)
+
+
+def launch_count() -> int:
+    return int(lib().bfs_launch_count())
+
+
+def default_config() -> Config:
+    c = Config()
+    lib().bfs_config_default(ctypes.byref(c))
+    return c
+
+
+# ------------------------------------------------------------- graph input
+def generate_edges(kind: int, scale: int, edgefactor: int, seed: int,
+                   a: float = 0.57, b: float = 0.19, c: float = 0.19, device="cuda", stream=None):
+    m = edgefactor << scale
+    src = torch.empty(m, dtype=torch.int32, device=device)
+    dst = torch.empty(m, dtype=torch.int32, device=device)
+    _check(lib().bfs_generate_edges(kind, scale, edgefactor, seed, a, b, c, _ptr(src), _ptr(dst),
+                                    _stream(stream)))
+    return src, dst
+
+
+def build_csr(n: int, src: torch.Tensor, dst: torch.Tensor, stream=None):
+    m = src.numel()
+    dev = src.device
+    offsets = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    indices = torch.empty(max(2 * m, 1), dtype=torch.int32, device=dev)
+    nnz = ctypes.c_int64(0)
+    _check(lib().bfs_build_csr(n, m, _ptr(src if m else None), _ptr(dst if m else None),
+                               _ptr(offsets), _ptr(indices), ctypes.byref(nnz), _stream(stream)))
+    return offsets, indices[:nnz.value]
+
+
+def sample_roots(offsets: torch.Tensor, n: int, seed: int, k: int, max_draws: int = 1 << 24,
+                 stream=None):
+    roots = torch.empty(k, dtype=torch.int32, device=offsets.device)
+    got = ctypes.c_int32(0)
+    _check(lib().bfs_sample_roots(_ptr(offsets), n, seed, k, max_draws, _ptr(roots),
+                                  ctypes.byref(got), _stream(stream)))
+    return roots[:got.value]
+
+
+def rmat_graph(scale: int, edgefactor: int, seed: int, kind: int = GEN_RMAT, stream=None):
+    """Generate edges and build the symmetric CSR on the GPU."""
+    src, dst = generate_edges(kind, scale, edgefactor, seed, stream=stream)
+    off, idx = build_csr(1 << scale, src, dst, stream=stream)
+    del src, dst
+    return off, idx
+
+
+# --------------------------------------------------------------------- BFS
+@dataclass
+class RunStats:
+    layers: list
+    component_edges: int
+
+
+class Graph:
+    """A CSR graph resident on the GPU (bfs_graph)."""
+
+    def __init__(self, offsets: torch.Tensor, indices: torch.Tensor, config: Config | None = None,
+                 borrow: bool = True, validate: bool = False):
+        n = offsets.numel() - 1
+        nnz = indices.numel()
+        flags = 0
+        if offsets.is_cuda:
+            flags |= DEVICE_PTRS
+            if borrow:
+                flags |= BORROW
+                self._keep = (offsets, indices)
+        if validate:
+            flags |= VALIDATE
+        offsets = offsets.contiguous()
+        indices = indices.contiguous()
+        h = ctypes.c_void_p(0)
+        _check(lib().bfs_graph_create(_ptr(offsets), _ptr(indices if nnz else None), n, nnz, flags,
+                                      ctypes.byref(config) if config is not None else None,
+                                      ctypes.byref(h)))
+        self._h = h
+        self.n = n
+        self.nnz = nnz
+
+    def set_config(self, config: Config | None):
+        _check(lib().bfs_graph_set_config(self._h, ctypes.byref(config) if config else None))
+
+    def run(self, root: int, level: torch.Tensor | None = None, parent: torch.Tensor | None = None,
+            want_parent: bool = True, stream=None):
+        dev = "cuda"
+        if level is None:
+            level = torch.empty(self.n, dtype=torch.int32, device=dev)
+        if parent is None and want_parent:
+            parent = torch.empty(self.n, dtype=torch.int32, device=level.device)
+        _check(lib().bfs_run(self._h, int(root), _ptr(level), _ptr(parent), _stream(stream)))
+        return level, parent
+
+    def stats(self) -> RunStats:
+        L = ctypes.c_int32(0)
+        ce = ctypes.c_int64(0)
+        _check(lib().bfs_last_run_stats(self._h, None, 0, ctypes.byref(L), None))
+        arr = (LayerStats * max(L.value, 1))()
+        _check(lib().bfs_last_run_stats(self._h, arr, L.value, ctypes.byref(L), ctypes.byref(ce)))
+        layers = [{f: getattr(arr[i], f) for f, _ in LayerStats._fields_} for i in range(L.value)]
+        return RunStats(layers, ce.value)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().bfs_graph_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,810 @@
+// bfs.cu -- single-source hybrid BFS (Alg. 1-3, Sec. 5) on one GPU.
+//
+// Data on the device, per graph:
+//   off[n+1] int64, idx[nnz] int32            symmetric CSR, rows sorted
+//   visited, front, next : uint32[nw_pad]      n-bit bitmaps (Sec. 5.1 "vis",
+//                                              "in", "out"); words past n are
+//                                              marked visited
+//   q_a, q_b : int32[n]                        frontier queues for top-down
+//   big : int32[n]                             frontier vertices whose edges
+//                                              are spread over the whole grid
+//   trace : int64[kRing][8]                    per-layer counters (Sec. 4)
+//
+// One layer = one of
+//   top-down  (Alg. 1): td_kernel over the queue, vertices binned by degree
+//             (shared-warp gather below td_warp_degree, one warp per vertex
+//             below td_grid_degree), then td_big_kernel spreads the edges of
+//             the big vertices over the grid. A vertex is claimed by
+//             atomicCAS on its parent; the winner writes its level, sets its
+//             visited / next bits and appends it to the next queue.
+//   bottom-up (Alg. 2 / Sec. 5.1): bu_kernel, one warp per 32-vertex bitmap
+//             word, one lane per vertex. Each unvisited lane tests its first
+//             bu_probe neighbours itself (the MAX_POS probe of Sec. 5.2); the
+//             lanes still unresolved are then scanned by the whole warp, 32
+//             neighbours per step, __ballot_sync + __ffs picking the first
+//             frontier neighbour in CSR order. The warp owns the word, so the
+//             next / visited words are written without atomics.
+// and the switch counters v_f, e_f (plus edges examined) are reduced inside
+// the step kernels into the layer's trace slot. The host reads that slot after
+// each layer and applies the Alg. 3 switch.
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace gbfs {
+
+constexpr int kRing = 64;  // trace ring slots (layers)
+constexpr int kFields = 8;
+enum TraceField { T_NF = 0, T_MF = 1, T_EXAM = 2, T_CONV = 3, T_BIG = 4 };
+constexpr int kBlock = 256;
+constexpr int kBigBatch = 1024;
+
+}  // namespace gbfs
+
+struct bfs_graph {
+    int device = 0;
+    int64_t n = 0, nnz = 0, nw = 0, nw_pad = 0;
+    const int64_t *off = nullptr;
+    const int32_t *idx = nullptr;
+    int64_t *off_own = nullptr;
+    int32_t *idx_own = nullptr;
+    uint32_t *visited = nullptr, *bm_a = nullptr, *bm_b = nullptr;
+    int32_t *q_a = nullptr, *q_b = nullptr, *big = nullptr;
+    int32_t *parent_scratch = nullptr, *level_scratch = nullptr;
+    int64_t *trace = nullptr;
+    int64_t *h_slot = nullptr;  // pinned, kFields entries
+    bfs_config cfg;
+    std::vector<bfs_layer_stats> last;
+    int64_t last_component_edges = 0;
+    std::vector<cudaEvent_t> events;
+    int bu_blocks_per_sm = 1, td_blocks_per_sm = 1;
+};
+
+namespace gbfs {
+namespace {
+
+__device__ __forceinline__ int64_t deg_of(const int64_t *__restrict__ off, int32_t v) {
+    return off[v + 1] - off[v];
+}
+
+__global__ void init_kernel(int64_t n, int64_t nw, int64_t nw_pad, int32_t root,
+                            const int64_t *__restrict__ off, int32_t *__restrict__ level,
+                            int32_t *__restrict__ parent, uint32_t *__restrict__ visited,
+                            uint32_t *__restrict__ front, int32_t *__restrict__ queue,
+                            int64_t *__restrict__ trace) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (int64_t i = t0; i < n; i += stride) {
+        level[i] = (i == root) ? 0 : -1;
+        parent[i] = (i == root) ? root : -1;
+    }
+    const int64_t rw = root >> 5;
+    const uint32_t rbit = 1u << (root & 31);
+    for (int64_t w = t0; w < nw_pad; w += stride) {
+        uint32_t vis = 0;
+        if (w >= nw) {
+            vis = 0xffffffffu;
+        } else if (w == nw - 1 && (n & 31)) {
+            vis = ~((1u << (n & 31)) - 1u);  // bits past n count as visited
+        }
+        if (w == rw) vis |= rbit;
+        visited[w] = vis;
+        front[w] = (w == rw) ? rbit : 0u;
+    }
+    for (int64_t i = t0; i < kRing * kFields; i += stride) {
+        int64_t v = 0;
+        if (i == T_NF) v = 1;
+        if (i == T_MF) v = deg_of(off, root);
+        trace[i] = v;
+    }
+    if (t0 == 0) queue[0] = root;
+}
+
+__device__ __forceinline__ void block_add3(int64_t a, int64_t b, int64_t c,
+                                           unsigned long long *dst_a,
+                                           unsigned long long *dst_b,
+                                           unsigned long long *dst_c) {
+    __shared__ long long red[3][kBlock / 32];
+    a = warp_sum(a);
+    b = warp_sum(b);
+    c = warp_sum(c);
+    const unsigned lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][w] = a;
+        red[1][w] = b;
+        red[2][w] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long s0 = 0, s1 = 0, s2 = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            s0 += red[0][i];
+            s1 += red[1][i];
+            s2 += red[2][i];
+        }
+        if (dst_a && s0) atomicAdd(dst_a, (unsigned long long)s0);
+        if (dst_b && s1) atomicAdd(dst_b, (unsigned long long)s1);
+        if (dst_c && s2) atomicAdd(dst_c, (unsigned long long)s2);
+    }
+}
+
+// State shared by the top-down expansion paths.
+struct TdArgs {
+    const int64_t *__restrict__ off;
+    const int32_t *__restrict__ idx;
+    uint32_t *visited;
+    uint32_t *next_bm;
+    int32_t *parent;
+    int32_t *level;
+    int32_t *q_next;
+    unsigned long long *next_count;  // trace slot of the next layer, T_NF
+    int32_t new_level;
+};
+
+// Edge (u, v) of the top-down step (Alg. 1, lines 3-6). Called by all 32
+// lanes together; `valid` masks lanes without an edge. The visited bitmap
+// is read first (an L2-resident filter); the claim itself is the CAS on
+// parent[v]. Winners are appended to the next queue with one atomicAdd per
+// warp. Returns the degree of the vertex this lane claimed (0 if none).
+__device__ __forceinline__ int64_t td_visit(const TdArgs &a, bool valid, int32_t u, int32_t v) {
+    bool won = false;
+    int64_t dv = 0;
+    if (valid) {
+        const uint32_t bit = 1u << (v & 31);
+        if (!(__ldcg(a.visited + (v >> 5)) & bit)) {
+            if (atomicCAS(a.parent + v, -1, u) == -1) {
+                won = true;
+                a.level[v] = a.new_level;
+                atomicOr(a.visited + (v >> 5), bit);
+                atomicOr(a.next_bm + (v >> 5), bit);
+                dv = deg_of(a.off, v);
+            }
+        }
+    }
+    const unsigned wm = __ballot_sync(0xffffffffu, won);
+    if (wm) {
+        const int leader = __ffs(wm) - 1;
+        unsigned long long base = 0;
+        if ((int)lane_id() == leader) base = atomicAdd(a.next_count, (unsigned long long)__popc(wm));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (won) a.q_next[base + __popc(wm & lanemask_lt())] = v;
+    }
+    return dv;
+}
+
+// Top-down over the frontier queue: each warp takes 32 queue entries and
+// splits them by degree: >= grid_deg go to the big list (td_big_kernel),
+// >= warp_deg are expanded one at a time by the whole warp, the rest are
+// gathered together (a warp-wide exclusive scan of their degrees assigns
+// each of the 32 lanes one edge per round).
+__global__ void __launch_bounds__(kBlock) td_kernel(TdArgs a, const int32_t *__restrict__ q,
+                                                    int64_t qlen, int32_t *__restrict__ big,
+                                                    unsigned long long *big_count,
+                                                    unsigned long long *next_mf, int warp_deg,
+                                                    int64_t grid_deg, int64_t *zero_slot) {
+    if (blockIdx.x == 0 && threadIdx.x < kFields) zero_slot[threadIdx.x] = 0;
+    const unsigned lane = lane_id();
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t my_mf = 0;
+    for (int64_t base = gw * 32; base < qlen; base += tw * 32) {
+        const int64_t i = base + lane;
+        const bool have = i < qlen;
+        int32_t u = 0;
+        int64_t beg = 0, end = 0;
+        if (have) {
+            u = q[i];
+            beg = a.off[u];
+            end = a.off[u + 1];
+        }
+        const int64_t deg = end - beg;
+        const bool isbig = have && deg >= grid_deg;
+        const unsigned bm = __ballot_sync(0xffffffffu, isbig);
+        if (bm) {
+            const int leader = __ffs(bm) - 1;
+            unsigned long long b0 = 0;
+            if ((int)lane == leader) b0 = atomicAdd(big_count, (unsigned long long)__popc(bm));
+            b0 = __shfl_sync(0xffffffffu, b0, leader);
+            if (isbig) big[b0 + __popc(bm & lanemask_lt())] = u;
+        }
+        const bool isw = have && !isbig && deg >= warp_deg;
+        unsigned wm = __ballot_sync(0xffffffffu, isw);
+        while (wm) {
+            const int L = __ffs(wm) - 1;
+            wm &= wm - 1;
+            const int32_t lu = __shfl_sync(0xffffffffu, u, L);
+            const int64_t lb = __shfl_sync(0xffffffffu, beg, L);
+            const int64_t le = __shfl_sync(0xffffffffu, end, L);
+            for (int64_t e0 = lb; e0 < le; e0 += 32) {
+                const int64_t e = e0 + lane;
+                const bool ok = e < le;
+                const int32_t v = ok ? a.idx[e] : 0;
+                my_mf += td_visit(a, ok, lu, v);
+            }
+        }
+        const int sdeg = (have && !isbig && !isw) ? (int)deg : 0;
+        int total;
+        const int excl = warp_exclusive_scan(sdeg, &total);
+        for (int j0 = 0; j0 < total; j0 += 32) {
+            const int j = j0 + (int)lane;
+            // owner = the last lane whose exclusive prefix is <= j
+            int lo = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int ex = __shfl_sync(0xffffffffu, excl, lo + step);
+                if (ex <= j) lo += step;
+            }
+            const int32_t ou = __shfl_sync(0xffffffffu, u, lo);
+            const int64_t ob = __shfl_sync(0xffffffffu, beg, lo);
+            const int oex = __shfl_sync(0xffffffffu, excl, lo);
+            const bool ok = j < total;
+            const int32_t v = ok ? a.idx[ob + (j - oex)] : 0;
+            my_mf += td_visit(a, ok, ou, v);
+        }
+    }
+    block_add3(my_mf, 0, 0, next_mf, nullptr, nullptr);
+}
+
+// The edges of all big vertices, spread evenly over the whole grid: batches
+// of kBigBatch vertices, an exclusive scan of their degrees in shared memory,
+// then a grid-stride walk over the batch's edge range with a binary search
+// for the owning vertex.
+__global__ void __launch_bounds__(kBlock) td_big_kernel(TdArgs a, const int32_t *__restrict__ big,
+                                                        const unsigned long long *big_count,
+                                                        unsigned long long *next_mf) {
+    __shared__ long long pre[kBigBatch + 1];
+    __shared__ long long beg_s[kBigBatch];
+    __shared__ int32_t u_s[kBigBatch];
+    __shared__ long long wtot[kBlock / 32];
+    const int64_t cnt = (int64_t)*big_count;
+    const unsigned lane = lane_id(), w = threadIdx.x >> 5;
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    constexpr int per = kBigBatch / kBlock;
+    int64_t my_mf = 0;
+    for (int64_t b0 = 0; b0 < cnt; b0 += kBigBatch) {
+        const int nb = (int)(cnt - b0 < kBigBatch ? cnt - b0 : kBigBatch);
+        long long dsum = 0;
+        long long dloc[per];
+#pragma unroll
+        for (int k = 0; k < per; ++k) {
+            const int t = threadIdx.x * per + k;
+            long long d = 0;
+            if (t < nb) {
+                const int32_t u = big[b0 + t];
+                u_s[t] = u;
+                beg_s[t] = a.off[u];
+                d = a.off[u + 1] - beg_s[t];
+            }
+            dloc[k] = d;
+            dsum += d;
+        }
+        long long x = dsum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if ((int)lane >= o) x += y;
+        }
+        if (lane == 31) wtot[w] = x;
+        __syncthreads();
+        long long run = x - dsum;
+        for (unsigned i = 0; i < w; ++i) run += wtot[i];
+#pragma unroll
+        for (int k = 0; k < per; ++k) {
+            pre[threadIdx.x * per + k] = run;
+            run += dloc[k];
+        }
+        if (threadIdx.x == kBlock - 1) pre[kBigBatch] = run;
+        __syncthreads();
+        const long long total = pre[kBigBatch];
+        for (long long g0 = gw * 32; g0 < total; g0 += tw * 32) {
+            const long long g = g0 + lane;
+            const bool ok = g < total;
+            int32_t u = 0, v = 0;
+            if (ok) {
+                int lo = 0, hi = nb;  // last k in [0, nb) with pre[k] <= g
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (pre[mid] <= g) lo = mid;
+                    else hi = mid;
+                }
+                u = u_s[lo];
+                v = a.idx[beg_s[lo] + (g - pre[lo])];
+            }
+            my_mf += td_visit(a, ok, u, v);
+        }
+        __syncthreads();
+    }
+    block_add3(my_mf, 0, 0, next_mf, nullptr, nullptr);
+}
+
+// Bottom-up step (Alg. 2 with the Sec. 5.1 structure). Warp-per-word,
+// lane-per-vertex; a chunk is 32 consecutive words, whose visited words are
+// loaded together by the 32 lanes.
+__global__ void __launch_bounds__(kBlock) bu_kernel(
+    const int64_t *__restrict__ off, const int32_t *__restrict__ idx, int64_t n, int64_t nw_pad,
+    uint32_t *__restrict__ visited, const uint32_t *__restrict__ front,
+    uint32_t *__restrict__ next_bm, int32_t *__restrict__ parent, int32_t *__restrict__ level,
+    int32_t new_level, int probe, unsigned long long *slot_next, int64_t *zero_slot) {
+    if (blockIdx.x == 0 && threadIdx.x < kFields) zero_slot[threadIdx.x] = 0;
+    const unsigned lane = lane_id();
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nchunks = nw_pad >> 5;
+    int64_t my_nf = 0, my_mf = 0, my_ex = 0;
+    for (int64_t c = gw; c < nchunks; c += tw) {
+        const uint32_t vis_lane = visited[c * 32 + lane];
+        for (int j = 0; j < 32; ++j) {
+            const uint32_t vw = __shfl_sync(0xffffffffu, vis_lane, j);
+            const int64_t w = c * 32 + j;
+            if (vw == 0xffffffffu) {
+                if (lane == 0) next_bm[w] = 0u;
+                continue;
+            }
+            const int64_t v = w * 32 + lane;
+            const bool unvisited = !((vw >> lane) & 1u);  // bits past n are set
+            int64_t beg = 0, end = 0;
+            bool found = false;
+            int32_t p = -1;
+            int64_t ex = 0;
+            if (unvisited) {
+                beg = off[v];
+                end = off[v + 1];
+                // Probe the first `probe` neighbours, 8 independent loads at a time.
+                for (int k0 = 0; k0 < probe && !found; k0 += 8) {
+                    int32_t cand[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int64_t e = beg + k0 + k;
+                        cand[k] = (k0 + k < probe && e < end) ? __ldg(idx + e) : -1;
+                    }
+                    uint32_t fw[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        fw[k] = cand[k] >= 0 ? __ldg(front + (cand[k] >> 5)) : 0u;
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        if (!found && cand[k] >= 0) {
+                            ++ex;
+                            if ((fw[k] >> (cand[k] & 31)) & 1u) {
+                                found = true;
+                                p = cand[k];
+                            }
+                        }
+                    }
+                }
+            }
+            // Warp-cooperative scan of the rest of every unresolved row.
+            const int64_t rest = beg + probe;
+            unsigned pend = __ballot_sync(0xffffffffu, unvisited && !found && rest < end);
+            while (pend) {
+                const int L = __ffs(pend) - 1;
+                pend &= pend - 1;
+                const int64_t lb = __shfl_sync(0xffffffffu, rest, L);
+                const int64_t le = __shfl_sync(0xffffffffu, end, L);
+                bool hit_any = false;
+                for (int64_t e0 = lb; e0 < le; e0 += 32) {
+                    const int64_t e = e0 + lane;
+                    int32_t u = 0;
+                    bool hit = false;
+                    if (e < le) {
+                        u = __ldg(idx + e);
+                        hit = (__ldg(front + (u >> 5)) >> (u & 31)) & 1u;
+                    }
+                    const unsigned hb = __ballot_sync(0xffffffffu, hit);
+                    if (hb) {
+                        const int first = __ffs(hb) - 1;
+                        const int32_t pu = __shfl_sync(0xffffffffu, u, first);
+                        if ((int)lane == L) {
+                            found = true;
+                            p = pu;
+                            ex += (e0 - lb) + first + 1;
+                        }
+                        hit_any = true;
+                        break;
+                    }
+                }
+                if (!hit_any && (int)lane == L) ex += le - lb;
+            }
+            const unsigned fm = __ballot_sync(0xffffffffu, found);
+            if (found) {
+                parent[v] = p;
+                level[v] = new_level;
+                my_mf += end - beg;
+            }
+            my_ex += ex;
+            if (lane == 0) {
+                next_bm[w] = fm;
+                if (fm) visited[w] = vw | fm;
+                my_nf += __popc(fm);
+            }
+        }
+    }
+    block_add3(my_nf, my_mf, my_ex, slot_next + T_NF, slot_next + T_MF, slot_next + T_EXAM);
+}
+
+// Frontier bitmap -> queue: each thread takes 4 consecutive words, a block
+// scan orders the set bits, one atomicAdd per block reserves queue space.
+__global__ void __launch_bounds__(kBlock) b2q_kernel(const uint32_t *__restrict__ bm, int64_t nw,
+                                                     int32_t *__restrict__ q,
+                                                     unsigned long long *count) {
+    __shared__ int wtot[kBlock / 32];
+    __shared__ unsigned long long base_s;
+    const unsigned lane = lane_id(), w = threadIdx.x >> 5;
+    for (int64_t t0 = (int64_t)blockIdx.x * kBlock * 4; t0 < nw; t0 += (int64_t)gridDim.x * kBlock * 4) {
+        const int64_t w0 = t0 + threadIdx.x * 4;
+        uint32_t words[4];
+        int c = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            words[k] = (w0 + k < nw) ? bm[w0 + k] : 0u;
+            c += __popc(words[k]);
+        }
+        int tot;
+        int excl = warp_exclusive_scan(c, &tot);
+        if (lane == 31) wtot[w] = tot;
+        __syncthreads();
+        int before = 0, all = 0;
+        for (int i = 0; i < kBlock / 32; ++i) {
+            if (i < (int)w) before += wtot[i];
+            all += wtot[i];
+        }
+        if (threadIdx.x == 0) base_s = all ? atomicAdd(count, (unsigned long long)all) : 0ull;
+        __syncthreads();
+        unsigned long long pos = base_s + before + excl;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t x = words[k];
+            while (x) {
+                const int b = __ffs(x) - 1;
+                x &= x - 1;
+                q[pos++] = (int32_t)((w0 + k) * 32 + b);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void validate_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
+                                int64_t n, int64_t nnz, int *bad) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t0 == 0 && (off[0] != 0 || off[n] != nnz)) *bad = 1;
+    for (int64_t v = t0; v < n; v += stride)
+        if (off[v] > off[v + 1]) *bad = 1;
+    for (int64_t e = t0; e < nnz; e += stride)
+        if (idx[e] < 0 || idx[e] >= n) *bad = 1;
+}
+
+int grid_cap(int64_t work_items, int per_block, int blocks_per_sm) {
+    int64_t g = (work_items + per_block - 1) / per_block;
+    const int64_t cap = (int64_t)sm_count() * std::max(1, blocks_per_sm);
+    return (int)std::max<int64_t>(1, std::min(g, cap));
+}
+
+bool config_ok(const bfs_config &c) {
+    if (c.policy < 0 || c.policy > 2) return false;
+    if (c.policy == BFS_POLICY_FORCED && (c.forced_len < 1 || c.forced_len > 64)) return false;
+    if (!(c.alpha > 0) || !(c.beta > 0)) return false;
+    if (c.bu_probe < 1 || c.bu_probe > 64) return false;
+    if (c.td_warp_degree < 1 || c.td_grid_degree < c.td_warp_degree) return false;
+    return true;
+}
+
+// Alg. 3 switch, read as hysteresis (Table 2 layer 5 rules out the
+// state-free reading). Returns 1 for bottom-up.
+int decide(const bfs_config &c, int cur_bu, int d, int64_t n, int64_t n_f, int64_t m_f,
+           int64_t n_u, int64_t m_u) {
+    if (c.policy == BFS_POLICY_FORCED) return c.forced[std::min(d, c.forced_len - 1)] ? 1 : 0;
+    if (c.policy == BFS_POLICY_VERTEX) {
+        if (!cur_bu) return n_f > (n_u >> 10) ? 1 : 0;
+        return n_f < (n >> 6) ? 0 : 1;
+    }
+    if (!cur_bu) return ((double)m_f > (double)m_u / c.alpha) ? 1 : 0;
+    return ((double)n_f < (double)n / c.beta) ? 0 : 1;
+}
+
+bool is_host_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+void free_graph(bfs_graph *g) {
+    if (!g) return;
+    cudaFree(g->off_own);
+    cudaFree(g->idx_own);
+    cudaFree(g->visited);
+    cudaFree(g->bm_a);
+    cudaFree(g->bm_b);
+    cudaFree(g->q_a);
+    cudaFree(g->q_b);
+    cudaFree(g->big);
+    cudaFree(g->parent_scratch);
+    cudaFree(g->level_scratch);
+    cudaFree(g->trace);
+    if (g->h_slot) cudaFreeHost(g->h_slot);
+    for (cudaEvent_t e : g->events) cudaEventDestroy(e);
+    delete g;
+}
+
+}  // namespace
+}  // namespace gbfs
+
+using namespace gbfs;
+
+extern "C" BFS_API void bfs_config_default(bfs_config *c) {
+    if (!c) return;
+    memset(c, 0, sizeof *c);
+    c->policy = BFS_POLICY_EDGE;
+    c->forced_len = 1;
+    c->alpha = 14.0;
+    c->beta = 24.0;
+    c->bu_probe = 8;
+    c->td_warp_degree = 32;
+    c->td_grid_degree = 4096;
+    c->timing = 0;
+}
+
+extern "C" BFS_API bfs_status bfs_graph_create(const int64_t *offsets, const int32_t *indices,
+                                               int64_t n, int64_t nnz, uint32_t flags,
+                                               const bfs_config *cfg, bfs_graph **out) {
+    clear_error();
+    if (!out || !offsets || (nnz > 0 && !indices) || n < 1 || n >= (1ll << 31) || nnz < 0 ||
+        ((flags & BFS_BORROW) && !(flags & BFS_DEVICE_PTRS))) {
+        set_error("bfs_graph_create: need offsets/indices/out, 1 <= n < 2^31, nnz >= 0; "
+                  "BFS_BORROW needs BFS_DEVICE_PTRS");
+        return BFS_ERR_INVALID;
+    }
+    *out = nullptr;
+    bfs_config c;
+    if (cfg) c = *cfg;
+    else bfs_config_default(&c);
+    if (!config_ok(c)) {
+        set_error("bfs_graph_create: invalid bfs_config");
+        return BFS_ERR_INVALID;
+    }
+    bfs_graph *g = new bfs_graph();
+    g->cfg = c;
+    g->n = n;
+    g->nnz = nnz;
+    g->nw = (n + 31) / 32;
+    g->nw_pad = ((g->nw + 31) / 32) * 32;
+#define GB_CKG(call)                                                    \
+    do {                                                                \
+        cudaError_t _e = (call);                                        \
+        if (_e != cudaSuccess) {                                        \
+            bfs_status _s = cuda_status(_e, #call, __FILE__, __LINE__); \
+            free_graph(g);                                              \
+            return _s;                                                  \
+        }                                                               \
+    } while (0)
+    GB_CKG(cudaGetDevice(&g->device));
+    if ((flags & BFS_DEVICE_PTRS) && (flags & BFS_BORROW)) {
+        g->off = offsets;
+        g->idx = indices;
+    } else {
+        const cudaMemcpyKind kind =
+            (flags & BFS_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        GB_CKG(cudaMalloc(&g->off_own, (size_t)(n + 1) * 8));
+        GB_CKG(cudaMalloc(&g->idx_own, (size_t)std::max<int64_t>(nnz, 1) * 4));
+        GB_CKG(cudaMemcpy(g->off_own, offsets, (size_t)(n + 1) * 8, kind));
+        if (nnz) GB_CKG(cudaMemcpy(g->idx_own, indices, (size_t)nnz * 4, kind));
+        g->off = g->off_own;
+        g->idx = g->idx_own;
+    }
+    const size_t bmb = (size_t)g->nw_pad * 4;
+    GB_CKG(cudaMalloc(&g->visited, bmb));
+    GB_CKG(cudaMalloc(&g->bm_a, bmb));
+    GB_CKG(cudaMalloc(&g->bm_b, bmb));
+    GB_CKG(cudaMalloc(&g->q_a, (size_t)n * 4));
+    GB_CKG(cudaMalloc(&g->q_b, (size_t)n * 4));
+    GB_CKG(cudaMalloc(&g->big, (size_t)n * 4));
+    GB_CKG(cudaMalloc(&g->trace, (size_t)kRing * kFields * 8));
+    GB_CKG(cudaMallocHost(&g->h_slot, kFields * 8));
+    if (flags & BFS_VALIDATE) {
+        int *bad = nullptr, hbad = 0;
+        GB_CKG(cudaMalloc(&bad, sizeof(int)));
+        cudaMemset(bad, 0, sizeof(int));
+        validate_kernel<<<grid_cap(std::max(n, nnz), kBlock, 8), kBlock>>>(g->off, g->idx, n, nnz,
+                                                                           bad);
+        count_launch();
+        cudaError_t e = cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost);
+        cudaFree(bad);
+        GB_CKG(e);
+        if (hbad) {
+            free_graph(g);
+            set_error("bfs_graph_create: CSR failed validation (offsets or indices out of range)");
+            return BFS_ERR_INVALID;
+        }
+    }
+    GB_CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->bu_blocks_per_sm, bu_kernel, kBlock, 0));
+    GB_CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->td_blocks_per_sm, td_kernel, kBlock, 0));
+#undef GB_CKG
+    *out = g;
+    return BFS_OK;
+}
+
+extern "C" BFS_API bfs_status bfs_graph_set_config(bfs_graph *g, const bfs_config *cfg) {
+    clear_error();
+    if (!g) {
+        set_error("bfs_graph_set_config: null graph");
+        return BFS_ERR_INVALID;
+    }
+    bfs_config c;
+    if (cfg) c = *cfg;
+    else bfs_config_default(&c);
+    if (!config_ok(c)) {
+        set_error("bfs_graph_set_config: invalid bfs_config");
+        return BFS_ERR_INVALID;
+    }
+    g->cfg = c;
+    return BFS_OK;
+}
+
+extern "C" BFS_API bfs_status bfs_graph_info(const bfs_graph *g, const int64_t **offsets,
+                                             const int32_t **indices, int64_t *n, int64_t *nnz) {
+    clear_error();
+    if (!g) {
+        set_error("bfs_graph_info: null graph");
+        return BFS_ERR_INVALID;
+    }
+    if (offsets) *offsets = g->off;
+    if (indices) *indices = g->idx;
+    if (n) *n = g->n;
+    if (nnz) *nnz = g->nnz;
+    return BFS_OK;
+}
+
+extern "C" BFS_API bfs_status bfs_graph_destroy(bfs_graph *g) {
+    clear_error();
+    free_graph(g);
+    return BFS_OK;
+}
+
+extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level_out,
+                                      int32_t *parent_out, void *stream) {
+    clear_error();
+    if (!g || !level_out || root < 0 || root >= g->n) {
+        set_error("bfs_run: need a graph, level_out and 0 <= root < n");
+        return BFS_ERR_INVALID;
+    }
+    cudaStream_t st = as_stream(stream);
+    const int64_t n = g->n;
+    const bool host_out = is_host_ptr(level_out);
+    if (parent_out && is_host_ptr(parent_out) != host_out) {
+        set_error("bfs_run: level_out and parent_out must both be host or both be device memory");
+        return BFS_ERR_INVALID;
+    }
+    int32_t *level = level_out, *parent = parent_out;
+    if (host_out) {
+        if (!g->level_scratch) GB_CK(cudaMalloc(&g->level_scratch, (size_t)n * 4));
+        level = g->level_scratch;
+        parent = nullptr;
+    }
+    if (!parent) {
+        if (!g->parent_scratch) GB_CK(cudaMalloc(&g->parent_scratch, (size_t)n * 4));
+        parent = g->parent_scratch;
+    }
+    const bfs_config &cfg = g->cfg;
+    const bool timing = cfg.timing != 0;
+    auto event = [&](size_t i) -> cudaEvent_t {
+        while (g->events.size() <= i) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            g->events.push_back(e);
+        }
+        return g->events[i];
+    };
+
+    g->last.clear();
+    uint32_t *front = g->bm_a, *next = g->bm_b;
+    int32_t *q_cur = g->q_a, *q_next = g->q_b;
+    GB_LAUNCH(init_kernel, grid_cap(std::max(n, g->nw_pad), kBlock, 8), kBlock, 0, st, n, g->nw,
+              g->nw_pad, root, g->off, level, parent, g->visited, front, q_cur, g->trace);
+    GB_CK(cudaMemcpyAsync(g->h_slot, g->trace, kFields * 8, cudaMemcpyDeviceToHost, st));
+    GB_CK(cudaStreamSynchronize(st));
+    int64_t n_f = 1, m_f = g->h_slot[T_MF];
+    int64_t n_u = n - 1, m_u = g->nnz - m_f;
+    int cur_bu = 0;
+    bool have_queue = true;
+    int64_t degree_sum = 0;
+    const int bu_grid = (int)std::max<int64_t>(
+        1, std::min<int64_t>(g->nw_pad / 32 / (kBlock / 32) + 1,
+                             (int64_t)sm_count() * g->bu_blocks_per_sm));
+    for (int d = 0; n_f > 0; ++d) {
+        if (d > n) {  // a BFS has at most n layers: the counters are inconsistent
+            set_error("bfs_run: traversal did not terminate after %lld layers", (long long)n);
+            return BFS_ERR_CUDA;
+        }
+        cur_bu = decide(cfg, cur_bu, d, n, n_f, m_f, n_u, m_u);
+        bfs_layer_stats ls;
+        memset(&ls, 0, sizeof ls);
+        ls.direction = cur_bu;
+        ls.n_f = n_f;
+        ls.m_f = m_f;
+        ls.n_u = n_u;
+        ls.m_u = m_u;
+        degree_sum += m_f;
+        int64_t *slot_cur = g->trace + (d % kRing) * kFields;
+        int64_t *slot_next = g->trace + ((d + 1) % kRing) * kFields;
+        int64_t *slot_zero = g->trace + ((d + 2) % kRing) * kFields;
+        const size_t e0 = (size_t)d * 3;
+        if (timing) GB_CK(cudaEventRecord(event(e0), st));
+        if (!cur_bu) {
+            if (!have_queue) {
+                GB_LAUNCH(b2q_kernel, grid_cap(g->nw, kBlock * 4, 8), kBlock, 0, st, front, g->nw,
+                          q_cur, (unsigned long long *)(slot_cur + T_CONV));
+                ls.converted = 1;
+            }
+            GB_CK(cudaMemsetAsync(next, 0, (size_t)g->nw_pad * 4, st));
+            TdArgs a{g->off, g->idx, g->visited, next, parent, level, q_next,
+                     (unsigned long long *)(slot_next + T_NF), d + 1};
+            if (timing) GB_CK(cudaEventRecord(event(e0 + 1), st));
+            GB_LAUNCH(td_kernel, grid_cap(n_f, kBlock, g->td_blocks_per_sm), kBlock, 0, st, a,
+                      q_cur, n_f, g->big, (unsigned long long *)(slot_cur + T_BIG),
+                      (unsigned long long *)(slot_next + T_MF), cfg.td_warp_degree,
+                      (int64_t)cfg.td_grid_degree, slot_zero);
+            if (m_f >= cfg.td_grid_degree)
+                GB_LAUNCH(td_big_kernel, sm_count() * g->td_blocks_per_sm, kBlock, 0, st, a,
+                          g->big, (const unsigned long long *)(slot_cur + T_BIG),
+                          (unsigned long long *)(slot_next + T_MF));
+            have_queue = true;
+        } else {
+            if (timing) GB_CK(cudaEventRecord(event(e0 + 1), st));
+            GB_LAUNCH(bu_kernel, bu_grid, kBlock, 0, st, g->off, g->idx, n, g->nw_pad, g->visited,
+                      front, next, parent, level, d + 1, cfg.bu_probe,
+                      (unsigned long long *)slot_next, slot_zero);
+            have_queue = false;
+        }
+        if (timing) GB_CK(cudaEventRecord(event(e0 + 2), st));
+        GB_CK(cudaMemcpyAsync(g->h_slot, slot_next, kFields * 8, cudaMemcpyDeviceToHost, st));
+        GB_CK(cudaStreamSynchronize(st));
+        const int64_t found = g->h_slot[T_NF], m_new = g->h_slot[T_MF];
+        ls.examined = cur_bu ? g->h_slot[T_EXAM] : m_f;
+        ls.found = found;
+        g->last.push_back(ls);
+        n_u -= found;
+        m_u -= m_new;
+        n_f = found;
+        m_f = m_new;
+        std::swap(front, next);
+        std::swap(q_cur, q_next);
+    }
+    g->last_component_edges = degree_sum / 2;
+    if (timing) {
+        for (size_t d = 0; d < g->last.size(); ++d) {
+            float t0 = 0, t1 = 0;
+            cudaEventElapsedTime(&t0, g->events[3 * d], g->events[3 * d + 2]);
+            cudaEventElapsedTime(&t1, g->events[3 * d + 1], g->events[3 * d + 2]);
+            g->last[d].ms_total = t0;
+            g->last[d].ms_main = t1;
+        }
+    }
+    if (host_out) {
+        GB_CK(cudaMemcpyAsync(level_out, level, (size_t)n * 4, cudaMemcpyDeviceToHost, st));
+        if (parent_out)
+            GB_CK(cudaMemcpyAsync(parent_out, parent, (size_t)n * 4, cudaMemcpyDeviceToHost, st));
+        GB_CK(cudaStreamSynchronize(st));
+    }
+    return BFS_OK;
+}
+
+extern "C" BFS_API bfs_status bfs_last_run_stats(const bfs_graph *g, bfs_layer_stats *out,
+                                                 int32_t cap, int32_t *layers,
+                                                 int64_t *component_edges) {
+    clear_error();
+    if (!g || cap < 0 || (cap > 0 && !out)) {
+        set_error("bfs_last_run_stats: null graph or output");
+        return BFS_ERR_INVALID;
+    }
+    const int32_t L = (int32_t)g->last.size();
+    for (int32_t i = 0; i < std::min(cap, L); ++i) out[i] = g->last[i];
+    if (layers) *layers = L;
+    if (component_edges) *component_edges = g->last_component_edges;
+    return BFS_OK;
+}

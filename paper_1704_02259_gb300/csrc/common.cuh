@@ -1,0 +1,81 @@
+// common.cuh -- internal helpers shared by the library's translation units:
+// error reporting behind the C ABI, kernel launch accounting, warp helpers
+// and the device-side SplitMix64 stream.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+
+#include "bfs.h"
+
+namespace gbfs {
+
+// Thread-local message behind bfs_last_error().
+void set_error(const char *fmt, ...);
+void clear_error();
+
+// Launch accounting behind bfs_launch_count().
+extern std::atomic<int64_t> g_launches;
+inline void count_launch(int k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Returns BFS_OK or records the CUDA error and returns BFS_ERR_CUDA / OOM.
+bfs_status cuda_status(cudaError_t e, const char *what, const char *file, int line);
+
+#define GB_CK(call)                                                                  \
+    do {                                                                             \
+        cudaError_t _e = (call);                                                     \
+        if (_e != cudaSuccess) return ::gbfs::cuda_status(_e, #call, __FILE__, __LINE__); \
+    } while (0)
+
+// Launch with accounting; checks the launch error.
+#define GB_LAUNCH(kernel, grid, block, smem, stream, ...)                            \
+    do {                                                                             \
+        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                  \
+        ::gbfs::count_launch();                                                      \
+        GB_CK(cudaGetLastError());                                                   \
+    } while (0)
+
+// Number of SMs of the current device (cached per device).
+int sm_count();
+
+// SplitMix64 (Steele, Lea, Flood 2014): output i of the stream seeded with s
+// is the mix13 finaliser applied to s + (i + 1) * 0x9E3779B97F4A7C15.
+__host__ __device__ __forceinline__ uint64_t sm64_at(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Exclusive prefix sum across the warp; *total receives the warp sum.
+__device__ __forceinline__ int warp_exclusive_scan(int v, int *total) {
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if ((int)lane_id() >= o) x += y;
+    }
+    *total = __shfl_sync(0xffffffffu, x, 31);
+    return x - v;
+}
+
+}  // namespace gbfs

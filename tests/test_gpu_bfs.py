@@ -1,0 +1,225 @@
+"""GPU parity for the single-source hybrid BFS: levels bit-exact against the
+oracle, parents by the tree invariants, bottom-up parents and per-layer
+counters exact against the oracle's run of Alg. 3 under the same policy."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1704_02259_gb300 as gb
+from tests import inputs
+from tests.gpu_common import both_csr, config, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def check_run(o_off, o_idx, graph, root, policy=None, forced=None, alpha=14.0, beta=24.0):
+    """Runs the GPU BFS and compares it with the oracle's Alg. 3 run."""
+    lv, pa = run_gpu(graph, root)
+    ref, _ = oracle.bfs(o_off, o_idx, root)
+    assert np.array_equal(lv, ref), "levels differ from the oracle"
+    assert oracle.check_parents(o_off, o_idx, root, lv, pa) == 0
+    if policy is None:
+        policy = oracle.POLICY_FORCED if forced is not None else oracle.POLICY_EDGE
+    h_lv, h_pa, dirs, tr = oracle.hybrid_bfs(o_off, o_idx, root, policy, alpha, beta,
+                                             forced=forced)
+    st = graph.stats()
+    L = st.layers
+    assert [x["direction"] for x in L] == dirs.tolist()
+    for d, x in enumerate(L):
+        assert (x["n_f"], x["m_f"], x["n_u"], x["m_u"], x["examined"], x["found"]) == \
+            tuple(int(t) for t in tr[d]), f"layer {d}"
+        if x["direction"] == 1:
+            nxt = ref == d + 1
+            assert np.array_equal(pa[nxt], h_pa[nxt]), f"bottom-up parents, layer {d}"
+    assert st.component_edges == oracle.component_edges(o_off, ref)
+    return lv, pa
+
+
+def make(n, s, d, **cfg):
+    o_off, o_idx, g_off, g_idx = both_csr(n, s, d)
+    g = gb.Graph(g_off, g_idx, config(**cfg) if cfg else None, validate=True)
+    return o_off, o_idx, g
+
+
+FORCED = {"td": [0], "bu": [1], "alt": [0, 1] * 32, "alt2": [1, 0] * 32,
+          "late_bu": [0, 0, 1], "rand": [1, 0, 0, 1, 1, 0, 1, 0, 0, 0, 1, 1, 1, 0, 1, 1]}
+
+
+@pytest.mark.parametrize("name", ["path", "cycle", "star", "grid", "hypercube", "complete",
+                                  "union", "single", "ragged"])
+@pytest.mark.parametrize("pat", list(FORCED))
+def test_closed_form_graphs_forced_directions(name, pat):
+    if name == "path":
+        n, (s, d) = 77, inputs.path_edges(77)
+    elif name == "cycle":
+        n, (s, d) = 65, inputs.cycle_edges(65)
+    elif name == "star":
+        n, (s, d) = 100, inputs.star_edges(100, centre=3)
+    elif name == "grid":
+        n, (s, d) = 15 * 17, inputs.grid_edges(15, 17)
+    elif name == "hypercube":
+        n, (s, d) = 256, inputs.hypercube_edges(8)
+    elif name == "complete":
+        n, (s, d) = 40, inputs.complete_edges(40)
+    elif name == "union":
+        n, s, d = inputs.union((30, *inputs.path_edges(30)), (9, *inputs.cycle_edges(9)),
+                               (5, [], []))
+    elif name == "single":
+        n, s, d = 1, np.zeros(0, np.int32), np.zeros(0, np.int32)
+    else:
+        n = 1000 + 13
+        s, d = inputs.random_edges(n, 3 * n, 5)
+    forced = FORCED[pat]
+    o_off, o_idx, g = make(n, s, d, forced=forced)
+    for r in sorted({0, n // 2, n - 1}):
+        check_run(o_off, o_idx, g, r, forced=forced)
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("policy", [gb.POLICY_EDGE, gb.POLICY_VERTEX])
+def test_policies_on_skewed_graphs(seed, policy):
+    n = [300, 2049, 5000, 10007, 40000, 65536][seed]
+    if seed % 2:
+        s, d = inputs.powerlaw_edges(n, 8 * n, seed, hubs=5)
+    else:
+        s, d = oracle.gen_edges(oracle.RMAT, 12 + seed // 2, 8, seed)
+        n = 1 << (12 + seed // 2)
+    o_off, o_idx, g = make(n, s, d, policy=policy)
+    for r in oracle.sample_roots(o_off, n, seed, 4):
+        check_run(o_off, o_idx, g, int(r), policy=policy)
+
+
+@pytest.mark.parametrize("deg", [1, 7, 8, 9, 31, 32, 33, 63, 64, 65, 1023, 1024, 1025,
+                                 4095, 4096, 4097])
+@pytest.mark.parametrize("pat", ["td", "bu"])
+def test_degree_bin_boundaries(deg, pat):
+    # hub 0 with `deg` leaves, each leaf also on a path, plus a second hub
+    n = deg + 200
+    hs, hd = inputs.star_edges(deg + 1, centre=0)
+    ps, pd = inputs.path_edges(n)
+    s = np.concatenate([hs, ps, np.full(50, 5, np.int32)]).astype(np.int32)
+    d = np.concatenate([hd, pd, np.arange(100, 150, dtype=np.int32)]).astype(np.int32)
+    forced = FORCED[pat]
+    for cfg in [dict(forced=forced), dict(forced=forced, td_warp_degree=8, td_grid_degree=64),
+                dict(forced=forced, bu_probe=1), dict(forced=forced, bu_probe=33)]:
+        o_off, o_idx, g = make(n, s, d, **cfg)
+        for r in [0, 1, n - 1, deg // 2]:
+            check_run(o_off, o_idx, g, r, forced=forced)
+
+
+def test_vertex_adjacent_to_all():
+    n = 5000
+    s, d = inputs.star_edges(n, centre=4321)
+    s2, d2 = inputs.random_edges(n, n, 3)
+    s = np.concatenate([s, s2]); d = np.concatenate([d, d2])
+    for pat in ["td", "bu", "alt"]:
+        o_off, o_idx, g = make(n, s, d, forced=FORCED[pat], td_grid_degree=256)
+        for r in [4321, 0, 17]:
+            check_run(o_off, o_idx, g, r, forced=FORCED[pat])
+
+
+def _rmat_both(scale, ef, seed, kind=oracle.RMAT):
+    n = 1 << scale
+    s, d = gb.generate_edges(kind, scale, ef, seed)
+    g_off, g_idx = gb.build_csr(n, s, d)
+    os_, od = oracle.gen_edges(kind, scale, ef, seed)
+    o_off, o_idx = oracle.build_csr(n, os_, od)
+    assert np.array_equal(g_off.cpu().numpy(), o_off)
+    assert np.array_equal(g_idx.cpu().numpy(), o_idx)
+    return n, o_off, o_idx, g_off, g_idx
+
+
+def test_rmat_scale16_all_64_roots():
+    # R-MAT scale 16, edgefactor 16, graph seed 1, 64 roots from seed 2
+    n, o_off, o_idx, g_off, g_idx = _rmat_both(16, 16, 1)
+    g = gb.Graph(g_off, g_idx)
+    roots = gb.sample_roots(g_off, n, 2, 64).cpu().numpy()
+    assert np.array_equal(roots, oracle.sample_roots(o_off, n, 2, 64))
+    for r in roots:
+        check_run(o_off, o_idx, g, int(r))
+
+
+@pytest.mark.parametrize("kind,seed", [(oracle.RMAT, 1), (oracle.ER, 3)])
+def test_scale20_all_64_roots(kind, seed):
+    # R-MAT scale 20 (the paper's one-million-vertex size) and its ER control
+    n, o_off, o_idx, g_off, g_idx = _rmat_both(20, 16, seed, kind)
+    g = gb.Graph(g_off, g_idx)
+    roots = gb.sample_roots(g_off, n, 2, 64).cpu().numpy()
+    for i, r in enumerate(roots):
+        lv, pa = run_gpu(g, int(r))
+        ref, _ = oracle.bfs(o_off, o_idx, int(r))
+        assert np.array_equal(lv, ref)
+        assert oracle.check_parents(o_off, o_idx, int(r), lv, pa) == 0
+        if i < 4:
+            check_run(o_off, o_idx, g, int(r))
+
+
+def test_host_output_buffers_match_device():
+    n, o_off, o_idx, g_off, g_idx = _rmat_both(14, 16, 1)
+    g = gb.Graph(g_off, g_idx)
+    r = int(oracle.sample_roots(o_off, n, 2, 1)[0])
+    lv_d, _ = run_gpu(g, r)
+    lv_h = torch.empty(n, dtype=torch.int32).pin_memory()
+    pa_h = torch.empty(n, dtype=torch.int32)
+    g.run(r, lv_h, pa_h)
+    assert np.array_equal(lv_h.numpy(), lv_d)
+    assert oracle.check_parents(o_off, o_idx, r, lv_h.numpy(), pa_h.numpy()) == 0
+
+
+def test_run_rejects_bad_root():
+    n, o_off, o_idx, g = None, *make(10, *inputs.path_edges(10))[:2], None
+    o_off, o_idx, g = make(10, *inputs.path_edges(10))
+    with pytest.raises(gb.BfsError):
+        g.run(10)
+    with pytest.raises(gb.BfsError):
+        g.run(-1)
+
+
+def test_validate_rejects_bad_csr():
+    off = torch.tensor([0, 1, 2], dtype=torch.int64, device="cuda")
+    idx = torch.tensor([1, 5], dtype=torch.int32, device="cuda")
+    with pytest.raises(gb.BfsError):
+        gb.Graph(off, idx, validate=True)
+    off = torch.tensor([0, 2, 1], dtype=torch.int64, device="cuda")
+    with pytest.raises(gb.BfsError):
+        gb.Graph(off, idx, validate=True)
+
+
+def test_scale26_sampled_levels():
+    """Full-size workload in the benchmark's launch configuration: for every
+    sampled vertex the level must satisfy the local BFS characterisation
+    (root 0; reached v: some neighbour one level up and none more than one
+    level away; unreached: all neighbours unreached), checked on 4 roots with
+    2,000 sampled vertices each, and the component edge count must equal
+    half the degree sum over reached vertices."""
+    scale = 26
+    n = 1 << scale
+    off, idx = gb.rmat_graph(scale, 16, 1)
+    g = gb.Graph(off, idx)
+    roots = gb.sample_roots(off, n, 2, 64)
+    rng = np.random.default_rng(1)
+    level = torch.empty(n, dtype=torch.int32, device="cuda")
+    parent = torch.empty(n, dtype=torch.int32, device="cuda")
+    for r in roots[:4].tolist():
+        g.run(r, level, parent)
+        torch.cuda.synchronize()
+        assert level[r].item() == 0 and parent[r].item() == r
+        degs = (off[1:] - off[:-1])
+        ce = int(degs[level >= 0].sum().item()) // 2
+        assert g.stats().component_edges == ce
+        for v in rng.choice(n, 2000, replace=False).tolist():
+            a, b = off[v].item(), off[v + 1].item()
+            nb = idx[a:b]
+            lv = level[v].item()
+            nl = level[nb.long()] if b > a else torch.empty(0, dtype=torch.int32, device="cuda")
+            if lv < 0:
+                assert bool((nl < 0).all()) and parent[v].item() == -1
+            elif v != r:
+                assert bool((nl >= 0).all())
+                assert int((nl - lv).abs().max().item()) <= 1
+                assert bool((nl == lv - 1).any())
+                p = parent[v].item()
+                assert level[p].item() == lv - 1 and bool((nb == p).any())
