@@ -125,10 +125,15 @@ typedef struct bfs_config {
                                 1..64                                          */
     int32_t td_warp_degree;  /* top-down: degree from which one warp expands
                                 a vertex (smaller ones share a warp)           */
-    int32_t td_grid_degree;  /* top-down: degree from which a vertex's edges
-                                are spread over the whole grid                 */
+    int32_t td_grid_degree;  /* top-down: largest degree threshold above which
+                                a vertex's edges are spread over the whole
+                                grid (the threshold used per layer is the
+                                frontier's edges per resident warp, clamped to
+                                [4*td_warp_degree, td_grid_degree])            */
     int32_t timing;          /* 1 = record CUDA events around each layer      */
-    int32_t reserved[8];
+    int32_t bu_words;        /* bottom-up: bitmap words a warp keeps in
+                                flight (1 or 2)                                */
+    int32_t reserved[7];
 } bfs_config;
 
 /* Fills `cfg` with the defaults (edge policy, alpha 14, beta 24, ...). */

@@ -40,7 +40,8 @@ class Config(ctypes.Structure):
                 ("forced", ctypes.c_uint8 * 64), ("alpha", ctypes.c_double),
                 ("beta", ctypes.c_double), ("bu_probe", ctypes.c_int32),
                 ("td_warp_degree", ctypes.c_int32), ("td_grid_degree", ctypes.c_int32),
-                ("timing", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8)]
+                ("timing", ctypes.c_int32), ("bu_words", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
 
 
 class LayerStats(ctypes.Structure):

@@ -39,6 +39,7 @@ constexpr int kFields = 8;
 enum TraceField { T_NF = 0, T_MF = 1, T_EXAM = 2, T_CONV = 3, T_BIG = 4 };
 constexpr int kBlock = 256;
 constexpr int kBigBatch = 1024;
+constexpr int64_t kQueueModeMaxEdges = 1 << 18;
 
 }  // namespace gbfs
 
@@ -50,6 +51,8 @@ struct bfs_graph {
     int64_t *off_own = nullptr;
     int32_t *idx_own = nullptr;
     uint32_t *visited = nullptr, *bm_a = nullptr, *bm_b = nullptr;
+    uint32_t *base_vis = nullptr;  // bits that start every traversal visited:
+                                   // degree-0 vertices and ids past n
     int32_t *q_a = nullptr, *q_b = nullptr, *big = nullptr;
     int32_t *parent_scratch = nullptr, *level_scratch = nullptr;
     int64_t *trace = nullptr;
@@ -58,7 +61,8 @@ struct bfs_graph {
     std::vector<bfs_layer_stats> last;
     int64_t last_component_edges = 0;
     std::vector<cudaEvent_t> events;
-    int bu_blocks_per_sm = 1, td_blocks_per_sm = 1;
+    int bu_blocks_per_sm[2] = {1, 1};
+    int td_blocks_per_sm = 1;
 };
 
 namespace gbfs {
@@ -68,11 +72,26 @@ __device__ __forceinline__ int64_t deg_of(const int64_t *__restrict__ off, int32
     return off[v + 1] - off[v];
 }
 
-__global__ void init_kernel(int64_t n, int64_t nw, int64_t nw_pad, int32_t root,
-                            const int64_t *__restrict__ off, int32_t *__restrict__ level,
-                            int32_t *__restrict__ parent, uint32_t *__restrict__ visited,
-                            uint32_t *__restrict__ front, int32_t *__restrict__ queue,
-                            int64_t *__restrict__ trace) {
+// Marks, per bitmap word, the vertices no traversal can reach from another
+// vertex: degree 0 (no edge leads to them) and ids past n (padding).
+__global__ void base_vis_kernel(const int64_t *__restrict__ off, int64_t n, int64_t nw_pad,
+                                uint32_t *__restrict__ base) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nw_pad; w += stride) {
+        uint32_t bits = 0;
+        for (int b = 0; b < 32; ++b) {
+            const int64_t v = w * 32 + b;
+            if (v >= n || off[v + 1] == off[v]) bits |= 1u << b;
+        }
+        base[w] = bits;
+    }
+}
+
+__global__ void init_kernel(int64_t n, int64_t nw_pad, int32_t root,
+                            const int64_t *__restrict__ off, const uint32_t *__restrict__ base,
+                            int32_t *__restrict__ level, int32_t *__restrict__ parent,
+                            uint32_t *__restrict__ visited, uint32_t *__restrict__ front,
+                            int32_t *__restrict__ queue, int64_t *__restrict__ trace) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     for (int64_t i = t0; i < n; i += stride) {
@@ -82,14 +101,7 @@ __global__ void init_kernel(int64_t n, int64_t nw, int64_t nw_pad, int32_t root,
     const int64_t rw = root >> 5;
     const uint32_t rbit = 1u << (root & 31);
     for (int64_t w = t0; w < nw_pad; w += stride) {
-        uint32_t vis = 0;
-        if (w >= nw) {
-            vis = 0xffffffffu;
-        } else if (w == nw - 1 && (n & 31)) {
-            vis = ~((1u << (n & 31)) - 1u);  // bits past n count as visited
-        }
-        if (w == rw) vis |= rbit;
-        visited[w] = vis;
+        visited[w] = base[w] | (w == rw ? rbit : 0u);
         front[w] = (w == rw) ? rbit : 0u;
     }
     for (int64_t i = t0; i < kRing * kFields; i += stride) {
@@ -140,46 +152,66 @@ struct TdArgs {
     int32_t *q_next;
     unsigned long long *next_count;  // trace slot of the next layer, T_NF
     int32_t new_level;
+    int queue_mode;  // 1: append winners to q_next; 0: next bitmap only
 };
 
-// Edge (u, v) of the top-down step (Alg. 1, lines 3-6). Called by all 32
-// lanes together; `valid` masks lanes without an edge. The visited bitmap
-// is read first (an L2-resident filter); the claim itself is the CAS on
-// parent[v]. Winners are appended to the next queue with one atomicAdd per
-// warp. Returns the degree of the vertex this lane claimed (0 if none).
-__device__ __forceinline__ int64_t td_visit(const TdArgs &a, bool valid, int32_t u, int32_t v) {
-    bool won = false;
-    int64_t dv = 0;
-    if (valid) {
-        const uint32_t bit = 1u << (v & 31);
-        if (!(__ldcg(a.visited + (v >> 5)) & bit)) {
-            if (atomicCAS(a.parent + v, -1, u) == -1) {
-                won = true;
-                a.level[v] = a.new_level;
-                atomicOr(a.visited + (v >> 5), bit);
-                atomicOr(a.next_bm + (v >> 5), bit);
-                dv = deg_of(a.off, v);
+// K edges (u[k], v[k]) per lane of the top-down step (Alg. 1, lines 3-6),
+// called by all 32 lanes together; valid[k] masks missing edges. The visited
+// bitmap (L2-resident) filters first; the claim itself is the CAS on
+// parent[v]. The K loads and the K CASes of a lane are issued back to back.
+// A winner writes its level, sets its visited and next bits, and adds its
+// degree to *mf (and 1 to *nf). In queue mode winners are appended to the
+// next queue with one atomicAdd per warp and edge slot.
+template <int K>
+__device__ __forceinline__ void td_visit(const TdArgs &a, const bool (&valid)[K],
+                                         const int32_t (&u)[K], const int32_t (&v)[K],
+                                         int64_t &mf, int64_t &nf) {
+    uint32_t vw[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) vw[k] = valid[k] ? __ldcg(a.visited + (v[k] >> 5)) : 0xffffffffu;
+    int old[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const bool cand = valid[k] && !((vw[k] >> (v[k] & 31)) & 1u);
+        old[k] = cand ? atomicCAS(a.parent + v[k], -1, u[k]) : 0;
+    }
+    bool won[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        won[k] = valid[k] && old[k] == -1 && !((vw[k] >> (v[k] & 31)) & 1u);
+        if (won[k]) {
+            const uint32_t bit = 1u << (v[k] & 31);
+            a.level[v[k]] = a.new_level;
+            atomicOr(a.visited + (v[k] >> 5), bit);
+            atomicOr(a.next_bm + (v[k] >> 5), bit);
+            mf += deg_of(a.off, v[k]);
+            nf += 1;
+        }
+    }
+    if (a.queue_mode) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const unsigned wm = __ballot_sync(0xffffffffu, won[k]);
+            if (wm) {
+                const int leader = __ffs(wm) - 1;
+                unsigned long long base = 0;
+                if ((int)lane_id() == leader)
+                    base = atomicAdd(a.next_count, (unsigned long long)__popc(wm));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (won[k]) a.q_next[base + __popc(wm & lanemask_lt())] = v[k];
             }
         }
     }
-    const unsigned wm = __ballot_sync(0xffffffffu, won);
-    if (wm) {
-        const int leader = __ffs(wm) - 1;
-        unsigned long long base = 0;
-        if ((int)lane_id() == leader) base = atomicAdd(a.next_count, (unsigned long long)__popc(wm));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (won) a.q_next[base + __popc(wm & lanemask_lt())] = v;
-    }
-    return dv;
 }
 
-// Top-down over the frontier queue: each warp takes 32 queue entries and
-// splits them by degree: >= grid_deg go to the big list (td_big_kernel),
-// >= warp_deg are expanded one at a time by the whole warp, the rest are
-// gathered together (a warp-wide exclusive scan of their degrees assigns
-// each of the 32 lanes one edge per round).
+// Top-down over the frontier queue. A warp takes `per_warp` (1..32) queue
+// entries, one per lane, and splits them by degree: >= grid_deg go to the big
+// list (td_big_kernel), >= warp_deg are expanded one at a time by the whole
+// warp (64 edges per round), the rest are gathered together: a warp-wide
+// exclusive scan of their degrees gives each lane two edges per round.
 __global__ void __launch_bounds__(kBlock) td_kernel(TdArgs a, const int32_t *__restrict__ q,
-                                                    int64_t qlen, int32_t *__restrict__ big,
+                                                    int64_t qlen, int per_warp,
+                                                    int32_t *__restrict__ big,
                                                     unsigned long long *big_count,
                                                     unsigned long long *next_mf, int warp_deg,
                                                     int64_t grid_deg, int64_t *zero_slot) {
@@ -187,10 +219,10 @@ __global__ void __launch_bounds__(kBlock) td_kernel(TdArgs a, const int32_t *__r
     const unsigned lane = lane_id();
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    int64_t my_mf = 0;
-    for (int64_t base = gw * 32; base < qlen; base += tw * 32) {
+    int64_t my_mf = 0, my_nf = 0;
+    for (int64_t base = gw * per_warp; base < qlen; base += tw * per_warp) {
         const int64_t i = base + lane;
-        const bool have = i < qlen;
+        const bool have = (int)lane < per_warp && i < qlen;
         int32_t u = 0;
         int64_t beg = 0, end = 0;
         if (have) {
@@ -216,40 +248,51 @@ __global__ void __launch_bounds__(kBlock) td_kernel(TdArgs a, const int32_t *__r
             const int32_t lu = __shfl_sync(0xffffffffu, u, L);
             const int64_t lb = __shfl_sync(0xffffffffu, beg, L);
             const int64_t le = __shfl_sync(0xffffffffu, end, L);
-            for (int64_t e0 = lb; e0 < le; e0 += 32) {
-                const int64_t e = e0 + lane;
-                const bool ok = e < le;
-                const int32_t v = ok ? a.idx[e] : 0;
-                my_mf += td_visit(a, ok, lu, v);
+            for (int64_t e0 = lb; e0 < le; e0 += 64) {
+                bool ok[2];
+                int32_t uu[2], vv[2];
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int64_t e = e0 + 32 * k + lane;
+                    ok[k] = e < le;
+                    uu[k] = lu;
+                    vv[k] = ok[k] ? a.idx[e] : 0;
+                }
+                td_visit<2>(a, ok, uu, vv, my_mf, my_nf);
             }
         }
         const int sdeg = (have && !isbig && !isw) ? (int)deg : 0;
         int total;
         const int excl = warp_exclusive_scan(sdeg, &total);
-        for (int j0 = 0; j0 < total; j0 += 32) {
-            const int j = j0 + (int)lane;
-            // owner = the last lane whose exclusive prefix is <= j
-            int lo = 0;
+        for (int j0 = 0; j0 < total; j0 += 64) {
+            bool ok[2];
+            int32_t uu[2], vv[2];
 #pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const int ex = __shfl_sync(0xffffffffu, excl, lo + step);
-                if (ex <= j) lo += step;
+            for (int k = 0; k < 2; ++k) {
+                const int j = j0 + 32 * k + (int)lane;
+                // owner = the last lane whose exclusive prefix is <= j
+                int lo = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int ex = __shfl_sync(0xffffffffu, excl, lo + step);
+                    if (ex <= j) lo += step;
+                }
+                uu[k] = __shfl_sync(0xffffffffu, u, lo);
+                const int64_t ob = __shfl_sync(0xffffffffu, beg, lo);
+                const int oex = __shfl_sync(0xffffffffu, excl, lo);
+                ok[k] = j < total;
+                vv[k] = ok[k] ? a.idx[ob + (j - oex)] : 0;
             }
-            const int32_t ou = __shfl_sync(0xffffffffu, u, lo);
-            const int64_t ob = __shfl_sync(0xffffffffu, beg, lo);
-            const int oex = __shfl_sync(0xffffffffu, excl, lo);
-            const bool ok = j < total;
-            const int32_t v = ok ? a.idx[ob + (j - oex)] : 0;
-            my_mf += td_visit(a, ok, ou, v);
+            td_visit<2>(a, ok, uu, vv, my_mf, my_nf);
         }
     }
-    block_add3(my_mf, 0, 0, next_mf, nullptr, nullptr);
+    block_add3(my_mf, a.queue_mode ? 0 : my_nf, 0, next_mf, a.next_count, nullptr);
 }
 
-// The edges of all big vertices, spread evenly over the whole grid: batches
-// of kBigBatch vertices, an exclusive scan of their degrees in shared memory,
-// then a grid-stride walk over the batch's edge range with a binary search
-// for the owning vertex.
+// The edges of all big vertices, spread evenly over the grid: batches of
+// kBigBatch vertices, an exclusive scan of their degrees in shared memory,
+// then a grid-stride walk over the batch's edge range (64 edges per warp and
+// round) with a binary search for the owning vertex.
 __global__ void __launch_bounds__(kBlock) td_big_kernel(TdArgs a, const int32_t *__restrict__ big,
                                                         const unsigned long long *big_count,
                                                         unsigned long long *next_mf) {
@@ -262,7 +305,7 @@ __global__ void __launch_bounds__(kBlock) td_big_kernel(TdArgs a, const int32_t 
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     constexpr int per = kBigBatch / kBlock;
-    int64_t my_mf = 0;
+    int64_t my_mf = 0, my_nf = 0;
     for (int64_t b0 = 0; b0 < cnt; b0 += kBigBatch) {
         const int nb = (int)(cnt - b0 < kBigBatch ? cnt - b0 : kBigBatch);
         long long dsum = 0;
@@ -298,32 +341,48 @@ __global__ void __launch_bounds__(kBlock) td_big_kernel(TdArgs a, const int32_t 
         if (threadIdx.x == kBlock - 1) pre[kBigBatch] = run;
         __syncthreads();
         const long long total = pre[kBigBatch];
-        for (long long g0 = gw * 32; g0 < total; g0 += tw * 32) {
-            const long long g = g0 + lane;
-            const bool ok = g < total;
-            int32_t u = 0, v = 0;
-            if (ok) {
-                int lo = 0, hi = nb;  // last k in [0, nb) with pre[k] <= g
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (pre[mid] <= g) lo = mid;
-                    else hi = mid;
+        for (long long g0 = gw * 64; g0 < total; g0 += tw * 64) {
+            bool ok[2];
+            int32_t uu[2], vv[2];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const long long g = g0 + 32 * k + lane;
+                ok[k] = g < total;
+                uu[k] = 0;
+                vv[k] = 0;
+                if (ok[k]) {
+                    int lo = 0, hi = nb;  // last j in [0, nb) with pre[j] <= g
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (pre[mid] <= g) lo = mid;
+                        else hi = mid;
+                    }
+                    uu[k] = u_s[lo];
+                    vv[k] = a.idx[beg_s[lo] + (g - pre[lo])];
                 }
-                u = u_s[lo];
-                v = a.idx[beg_s[lo] + (g - pre[lo])];
             }
-            my_mf += td_visit(a, ok, u, v);
+            td_visit<2>(a, ok, uu, vv, my_mf, my_nf);
         }
         __syncthreads();
     }
-    block_add3(my_mf, 0, 0, next_mf, nullptr, nullptr);
+    block_add3(my_mf, a.queue_mode ? 0 : my_nf, 0, next_mf, a.next_count, nullptr);
 }
 
-// Bottom-up step (Alg. 2 with the Sec. 5.1 structure). Warp-per-word,
-// lane-per-vertex; a chunk is 32 consecutive words, whose visited words are
-// loaded together by the 32 lanes.
+// Bottom-up step (Alg. 2 with the Sec. 5.1 structure). Lane-per-vertex,
+// warp-per-word: a warp takes a chunk of 32 consecutive bitmap words (their
+// visited words loaded together) and walks it W words at a time, so W
+// independent word-tasks are in flight per warp. Per word and lane:
+//   1. the lane's own probe of its first `probe` neighbours, 4 independent
+//      index loads then 4 frontier-bit loads per round (the MAX_POS probe of
+//      Sec. 5.2, the 16-lane gather of Alg. 5 recast for 32 lanes);
+//   2. the rows still unresolved are scanned by the whole warp, 64
+//      neighbours per round, __ballot_sync + __ffs selecting the first
+//      frontier neighbour in CSR order (Alg. 2 stops at the first hit);
+//   3. the ballot of found lanes is the next word and is ORed into the
+//      visited word by the owning warp, without atomics.
+template <int W>
 __global__ void __launch_bounds__(kBlock) bu_kernel(
-    const int64_t *__restrict__ off, const int32_t *__restrict__ idx, int64_t n, int64_t nw_pad,
+    const int64_t *__restrict__ off, const int32_t *__restrict__ idx, int64_t nw_pad,
     uint32_t *__restrict__ visited, const uint32_t *__restrict__ front,
     uint32_t *__restrict__ next_bm, int32_t *__restrict__ parent, int32_t *__restrict__ level,
     int32_t new_level, int probe, unsigned long long *slot_next, int64_t *zero_slot) {
@@ -335,89 +394,120 @@ __global__ void __launch_bounds__(kBlock) bu_kernel(
     int64_t my_nf = 0, my_mf = 0, my_ex = 0;
     for (int64_t c = gw; c < nchunks; c += tw) {
         const uint32_t vis_lane = visited[c * 32 + lane];
-        for (int j = 0; j < 32; ++j) {
-            const uint32_t vw = __shfl_sync(0xffffffffu, vis_lane, j);
-            const int64_t w = c * 32 + j;
-            if (vw == 0xffffffffu) {
-                if (lane == 0) next_bm[w] = 0u;
+        for (int j = 0; j < 32; j += W) {
+            uint32_t vw[W];
+            bool all = true;
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                vw[k] = __shfl_sync(0xffffffffu, vis_lane, j + k);
+                all = all && vw[k] == 0xffffffffu;
+            }
+            if (all) {
+                if ((int)lane < W) next_bm[c * 32 + j + lane] = 0u;
                 continue;
             }
-            const int64_t v = w * 32 + lane;
-            const bool unvisited = !((vw >> lane) & 1u);  // bits past n are set
-            int64_t beg = 0, end = 0;
-            bool found = false;
-            int32_t p = -1;
-            int64_t ex = 0;
-            if (unvisited) {
-                beg = off[v];
-                end = off[v + 1];
-                // Probe the first `probe` neighbours, 8 independent loads at a time.
-                for (int k0 = 0; k0 < probe && !found; k0 += 8) {
-                    int32_t cand[8];
+            bool unv[W], found[W];
+            int64_t beg[W], end[W], ex[W];
+            int32_t p[W];
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        const int64_t e = beg + k0 + k;
-                        cand[k] = (k0 + k < probe && e < end) ? __ldg(idx + e) : -1;
+            for (int k = 0; k < W; ++k) {
+                const int64_t v = (c * 32 + j + k) * 32 + lane;
+                unv[k] = !((vw[k] >> lane) & 1u);  // bits past n are set
+                found[k] = false;
+                p[k] = -1;
+                ex[k] = 0;
+                beg[k] = unv[k] ? off[v] : 0;
+                end[k] = unv[k] ? off[v + 1] : 0;
+            }
+            for (int p0 = 0; p0 < probe; p0 += 4) {
+                int32_t cand[W][4];
+                bool any = false;
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int64_t e = beg[k] + p0 + t;
+                        const bool ok = unv[k] && !found[k] && p0 + t < probe && e < end[k];
+                        cand[k][t] = ok ? __ldg(idx + e) : -1;
+                        any = any || ok;
                     }
-                    uint32_t fw[8];
+                }
+                if (!any) break;
+                uint32_t fw[W][4];
 #pragma unroll
-                    for (int k = 0; k < 8; ++k)
-                        fw[k] = cand[k] >= 0 ? __ldg(front + (cand[k] >> 5)) : 0u;
+                for (int k = 0; k < W; ++k)
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        if (!found && cand[k] >= 0) {
-                            ++ex;
-                            if ((fw[k] >> (cand[k] & 31)) & 1u) {
-                                found = true;
-                                p = cand[k];
+                    for (int t = 0; t < 4; ++t)
+                        fw[k][t] = cand[k][t] >= 0 ? __ldg(front + (cand[k][t] >> 5)) : 0u;
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        if (!found[k] && cand[k][t] >= 0) {
+                            ++ex[k];
+                            if ((fw[k][t] >> (cand[k][t] & 31)) & 1u) {
+                                found[k] = true;
+                                p[k] = cand[k][t];
                             }
                         }
                     }
                 }
             }
-            // Warp-cooperative scan of the rest of every unresolved row.
-            const int64_t rest = beg + probe;
-            unsigned pend = __ballot_sync(0xffffffffu, unvisited && !found && rest < end);
-            while (pend) {
-                const int L = __ffs(pend) - 1;
-                pend &= pend - 1;
-                const int64_t lb = __shfl_sync(0xffffffffu, rest, L);
-                const int64_t le = __shfl_sync(0xffffffffu, end, L);
-                bool hit_any = false;
-                for (int64_t e0 = lb; e0 < le; e0 += 32) {
-                    const int64_t e = e0 + lane;
-                    int32_t u = 0;
-                    bool hit = false;
-                    if (e < le) {
-                        u = __ldg(idx + e);
-                        hit = (__ldg(front + (u >> 5)) >> (u & 31)) & 1u;
-                    }
-                    const unsigned hb = __ballot_sync(0xffffffffu, hit);
-                    if (hb) {
-                        const int first = __ffs(hb) - 1;
-                        const int32_t pu = __shfl_sync(0xffffffffu, u, first);
-                        if ((int)lane == L) {
-                            found = true;
-                            p = pu;
-                            ex += (e0 - lb) + first + 1;
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                const int64_t rest = beg[k] + probe;
+                unsigned pend = __ballot_sync(0xffffffffu, unv[k] && !found[k] && rest < end[k]);
+                while (pend) {
+                    const int L = __ffs(pend) - 1;
+                    pend &= pend - 1;
+                    const int64_t lb = __shfl_sync(0xffffffffu, rest, L);
+                    const int64_t le = __shfl_sync(0xffffffffu, end[k], L);
+                    bool hit_any = false;
+                    for (int64_t e0 = lb; e0 < le; e0 += 64) {
+                        int32_t uu[2];
+                        bool hit[2];
+#pragma unroll
+                        for (int t = 0; t < 2; ++t) {
+                            const int64_t e = e0 + 32 * t + lane;
+                            uu[t] = e < le ? __ldg(idx + e) : -1;
                         }
-                        hit_any = true;
-                        break;
+#pragma unroll
+                        for (int t = 0; t < 2; ++t)
+                            hit[t] = uu[t] >= 0 && ((__ldg(front + (uu[t] >> 5)) >> (uu[t] & 31)) & 1u);
+                        const unsigned h0 = __ballot_sync(0xffffffffu, hit[0]);
+                        const unsigned h1 = __ballot_sync(0xffffffffu, hit[1]);
+                        if (h0 | h1) {
+                            const int t = h0 ? 0 : 1;
+                            const int first = __ffs(h0 ? h0 : h1) - 1;
+                            const int32_t pu = __shfl_sync(0xffffffffu, t ? uu[1] : uu[0], first);
+                            if ((int)lane == L) {
+                                found[k] = true;
+                                p[k] = pu;
+                                ex[k] += (e0 - lb) + 32 * t + first + 1;
+                            }
+                            hit_any = true;
+                            break;
+                        }
                     }
+                    if (!hit_any && (int)lane == L) ex[k] += le - lb;
                 }
-                if (!hit_any && (int)lane == L) ex += le - lb;
             }
-            const unsigned fm = __ballot_sync(0xffffffffu, found);
-            if (found) {
-                parent[v] = p;
-                level[v] = new_level;
-                my_mf += end - beg;
-            }
-            my_ex += ex;
-            if (lane == 0) {
-                next_bm[w] = fm;
-                if (fm) visited[w] = vw | fm;
-                my_nf += __popc(fm);
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                const int64_t w = c * 32 + j + k;
+                const int64_t v = w * 32 + lane;
+                const unsigned fm = __ballot_sync(0xffffffffu, found[k]);
+                if (found[k]) {
+                    parent[v] = p[k];
+                    level[v] = new_level;
+                    my_mf += end[k] - beg[k];
+                }
+                my_ex += ex[k];
+                if (lane == 0) {
+                    next_bm[w] = fm;
+                    if (fm) visited[w] = vw[k] | fm;
+                    my_nf += __popc(fm);
+                }
             }
         }
     }
@@ -489,6 +579,7 @@ bool config_ok(const bfs_config &c) {
     if (!(c.alpha > 0) || !(c.beta > 0)) return false;
     if (c.bu_probe < 1 || c.bu_probe > 64) return false;
     if (c.td_warp_degree < 1 || c.td_grid_degree < c.td_warp_degree) return false;
+    if (c.bu_words != 1 && c.bu_words != 2) return false;
     return true;
 }
 
@@ -519,6 +610,7 @@ void free_graph(bfs_graph *g) {
     cudaFree(g->off_own);
     cudaFree(g->idx_own);
     cudaFree(g->visited);
+    cudaFree(g->base_vis);
     cudaFree(g->bm_a);
     cudaFree(g->bm_b);
     cudaFree(g->q_a);
@@ -546,8 +638,9 @@ extern "C" BFS_API void bfs_config_default(bfs_config *c) {
     c->beta = 24.0;
     c->bu_probe = 8;
     c->td_warp_degree = 32;
-    c->td_grid_degree = 4096;
+    c->td_grid_degree = 1024;
     c->timing = 0;
+    c->bu_words = 2;
 }
 
 extern "C" BFS_API bfs_status bfs_graph_create(const int64_t *offsets, const int32_t *indices,
@@ -599,6 +692,7 @@ extern "C" BFS_API bfs_status bfs_graph_create(const int64_t *offsets, const int
     }
     const size_t bmb = (size_t)g->nw_pad * 4;
     GB_CKG(cudaMalloc(&g->visited, bmb));
+    GB_CKG(cudaMalloc(&g->base_vis, bmb));
     GB_CKG(cudaMalloc(&g->bm_a, bmb));
     GB_CKG(cudaMalloc(&g->bm_b, bmb));
     GB_CKG(cudaMalloc(&g->q_a, (size_t)n * 4));
@@ -622,7 +716,14 @@ extern "C" BFS_API bfs_status bfs_graph_create(const int64_t *offsets, const int
             return BFS_ERR_INVALID;
         }
     }
-    GB_CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->bu_blocks_per_sm, bu_kernel, kBlock, 0));
+    base_vis_kernel<<<grid_cap(g->nw_pad, kBlock, 8), kBlock>>>(g->off, n, g->nw_pad, g->base_vis);
+    count_launch();
+    GB_CKG(cudaGetLastError());
+    GB_CKG(cudaDeviceSynchronize());
+    GB_CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->bu_blocks_per_sm[0], bu_kernel<1>,
+                                                         kBlock, 0));
+    GB_CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->bu_blocks_per_sm[1], bu_kernel<2>,
+                                                         kBlock, 0));
     GB_CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->td_blocks_per_sm, td_kernel, kBlock, 0));
 #undef GB_CKG
     *out = g;
@@ -704,8 +805,9 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
     g->last.clear();
     uint32_t *front = g->bm_a, *next = g->bm_b;
     int32_t *q_cur = g->q_a, *q_next = g->q_b;
-    GB_LAUNCH(init_kernel, grid_cap(std::max(n, g->nw_pad), kBlock, 8), kBlock, 0, st, n, g->nw,
-              g->nw_pad, root, g->off, level, parent, g->visited, front, q_cur, g->trace);
+    GB_LAUNCH(init_kernel, grid_cap(std::max(n, g->nw_pad), kBlock, 8), kBlock, 0, st, n,
+              g->nw_pad, root, g->off, g->base_vis, level, parent, g->visited, front, q_cur,
+              g->trace);
     GB_CK(cudaMemcpyAsync(g->h_slot, g->trace, kFields * 8, cudaMemcpyDeviceToHost, st));
     GB_CK(cudaStreamSynchronize(st));
     int64_t n_f = 1, m_f = g->h_slot[T_MF];
@@ -713,9 +815,11 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
     int cur_bu = 0;
     bool have_queue = true;
     int64_t degree_sum = 0;
+    const int bw = cfg.bu_words;
     const int bu_grid = (int)std::max<int64_t>(
         1, std::min<int64_t>(g->nw_pad / 32 / (kBlock / 32) + 1,
-                             (int64_t)sm_count() * g->bu_blocks_per_sm));
+                             (int64_t)sm_count() * g->bu_blocks_per_sm[bw - 1]));
+    const int64_t td_warps = (int64_t)sm_count() * g->td_blocks_per_sm * (kBlock / 32);
     for (int d = 0; n_f > 0; ++d) {
         if (d > n) {  // a BFS has at most n layers: the counters are inconsistent
             set_error("bfs_run: traversal did not terminate after %lld layers", (long long)n);
@@ -742,23 +846,44 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                 ls.converted = 1;
             }
             GB_CK(cudaMemsetAsync(next, 0, (size_t)g->nw_pad * 4, st));
+            // Queue output only while the layer is small enough that one
+            // atomicAdd per warp and round on the queue tail does not
+            // serialise; a large layer leaves only the next bitmap, and the
+            // queue is rebuilt by b2q if the next layer is top-down too.
+            const int queue_mode = m_f <= kQueueModeMaxEdges ? 1 : 0;
             TdArgs a{g->off, g->idx, g->visited, next, parent, level, q_next,
-                     (unsigned long long *)(slot_next + T_NF), d + 1};
+                     (unsigned long long *)(slot_next + T_NF), d + 1, queue_mode};
+            // Entries per warp so that a small frontier still covers the GPU,
+            // and the grid-spread threshold at the frontier's edges per warp.
+            const int per_warp = (int)std::min<int64_t>(32, std::max<int64_t>(1, (n_f + td_warps - 1) / td_warps));
+            const int64_t grid_deg = std::min<int64_t>(
+                cfg.td_grid_degree,
+                std::max<int64_t>(4 * (int64_t)cfg.td_warp_degree, m_f / td_warps));
+            const int td_grid = grid_cap((n_f + per_warp - 1) / per_warp, kBlock / 32,
+                                         g->td_blocks_per_sm);
             if (timing) GB_CK(cudaEventRecord(event(e0 + 1), st));
-            GB_LAUNCH(td_kernel, grid_cap(n_f, kBlock, g->td_blocks_per_sm), kBlock, 0, st, a,
-                      q_cur, n_f, g->big, (unsigned long long *)(slot_cur + T_BIG),
-                      (unsigned long long *)(slot_next + T_MF), cfg.td_warp_degree,
-                      (int64_t)cfg.td_grid_degree, slot_zero);
-            if (m_f >= cfg.td_grid_degree)
-                GB_LAUNCH(td_big_kernel, sm_count() * g->td_blocks_per_sm, kBlock, 0, st, a,
-                          g->big, (const unsigned long long *)(slot_cur + T_BIG),
+            GB_LAUNCH(td_kernel, td_grid, kBlock, 0, st, a, q_cur, n_f, per_warp, g->big,
+                      (unsigned long long *)(slot_cur + T_BIG),
+                      (unsigned long long *)(slot_next + T_MF), cfg.td_warp_degree, grid_deg,
+                      slot_zero);
+            if (m_f >= grid_deg) {
+                const int big_grid = (int)std::max<int64_t>(
+                    1, std::min<int64_t>(m_f / 4096 + 1, (int64_t)sm_count() * g->td_blocks_per_sm));
+                GB_LAUNCH(td_big_kernel, big_grid, kBlock, 0, st, a, g->big,
+                          (const unsigned long long *)(slot_cur + T_BIG),
                           (unsigned long long *)(slot_next + T_MF));
-            have_queue = true;
+            }
+            have_queue = queue_mode != 0;
         } else {
             if (timing) GB_CK(cudaEventRecord(event(e0 + 1), st));
-            GB_LAUNCH(bu_kernel, bu_grid, kBlock, 0, st, g->off, g->idx, n, g->nw_pad, g->visited,
-                      front, next, parent, level, d + 1, cfg.bu_probe,
-                      (unsigned long long *)slot_next, slot_zero);
+            if (bw == 1)
+                GB_LAUNCH(bu_kernel<1>, bu_grid, kBlock, 0, st, g->off, g->idx, g->nw_pad,
+                          g->visited, front, next, parent, level, d + 1, cfg.bu_probe,
+                          (unsigned long long *)slot_next, slot_zero);
+            else
+                GB_LAUNCH(bu_kernel<2>, bu_grid, kBlock, 0, st, g->off, g->idx, g->nw_pad,
+                          g->visited, front, next, parent, level, d + 1, cfg.bu_probe,
+                          (unsigned long long *)slot_next, slot_zero);
             have_queue = false;
         }
         if (timing) GB_CK(cudaEventRecord(event(e0 + 2), st));

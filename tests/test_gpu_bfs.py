@@ -92,7 +92,7 @@ def test_policies_on_skewed_graphs(seed, policy):
         check_run(o_off, o_idx, g, int(r), policy=policy)
 
 
-@pytest.mark.parametrize("deg", [1, 7, 8, 9, 31, 32, 33, 63, 64, 65, 1023, 1024, 1025,
+@pytest.mark.parametrize("deg", [1, 7, 8, 9, 31, 32, 33, 63, 64, 65, 127, 128, 129, 1023, 1024, 1025,
                                  4095, 4096, 4097])
 @pytest.mark.parametrize("pat", ["td", "bu"])
 def test_degree_bin_boundaries(deg, pat):
@@ -104,7 +104,8 @@ def test_degree_bin_boundaries(deg, pat):
     d = np.concatenate([hd, pd, np.arange(100, 150, dtype=np.int32)]).astype(np.int32)
     forced = FORCED[pat]
     for cfg in [dict(forced=forced), dict(forced=forced, td_warp_degree=8, td_grid_degree=64),
-                dict(forced=forced, bu_probe=1), dict(forced=forced, bu_probe=33)]:
+                dict(forced=forced, bu_probe=1), dict(forced=forced, bu_probe=33),
+                dict(forced=forced, bu_words=1, bu_probe=5)]:
         o_off, o_idx, g = make(n, s, d, **cfg)
         for r in [0, 1, n - 1, deg // 2]:
             check_run(o_off, o_idx, g, r, forced=forced)
@@ -170,7 +171,6 @@ def test_host_output_buffers_match_device():
 
 
 def test_run_rejects_bad_root():
-    n, o_off, o_idx, g = None, *make(10, *inputs.path_edges(10))[:2], None
     o_off, o_idx, g = make(10, *inputs.path_edges(10))
     with pytest.raises(gb.BfsError):
         g.run(10)
