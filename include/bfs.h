@@ -201,6 +201,32 @@ typedef struct bfs_layer_stats {
 BFS_API bfs_status bfs_last_run_stats(const bfs_graph *g, bfs_layer_stats *out, int32_t cap,
                                       int32_t *layers, int64_t *component_edges);
 
+/* ---------------------------------------------------------------------- */
+/* Allocation-free traversal. The paper has no counterpart: this entry     */
+/* point exists for callers that must not allocate device memory.         */
+/* ---------------------------------------------------------------------- */
+/* Some callers cannot call cudaMalloc: a plugin handed only a stream by its
+ * host process, a service whose device memory is owned by another allocator
+ * (a framework's caching pool that has reserved the GPU), or code on a
+ * latency-critical path where an allocation's implicit synchronisation is not
+ * acceptable. bfs_run_noalloc runs the same hybrid BFS as bfs_run (default
+ * configuration, edge policy) without creating a bfs_graph and without any
+ * allocation: its bitmaps, queues and counters live in one fixed device
+ * array compiled into the library (about 12.5 MiB on every GPU that loads
+ * the library, held until the process exits).
+ *   offsets, indices   device CSR (layout above), caller-owned, n <= 2^20
+ *   level_out, parent_out   device, n int32 each, caller-owned (both needed)
+ * n above 2^20 gives BFS_ERR_INVALID. The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current.
+ * Every call overwrites the part of the array it reads before reading it, so
+ * nothing of a previous call leaks in; but all calls share the one array, so
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller. Synchronous like bfs_run.
+ * Makes no cudaMalloc, cudaMallocAsync, cudaMallocHost or cudaFree call. */
+BFS_API bfs_status bfs_run_noalloc(const int64_t *offsets, const int32_t *indices, int64_t n,
+                                   int64_t nnz, int32_t root, int32_t *level_out,
+                                   int32_t *parent_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

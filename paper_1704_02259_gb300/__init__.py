@@ -69,6 +69,7 @@ SIGNATURES = {
     "bfs_graph_destroy": (I32, [P]),
     "bfs_run": (I32, [P, I32, P, P, P]),
     "bfs_last_run_stats": (I32, [P, P, I32, P, P]),
+    "bfs_run_noalloc": (I32, [P, P, I64, I64, I32, P, P, P]),
 }
 
 
@@ -225,3 +226,13 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+def run_noalloc(offsets: torch.Tensor, indices: torch.Tensor, root: int, level: torch.Tensor,
+                parent: torch.Tensor, stream=None):
+    """bfs_run_noalloc: the traversal with library-resident scratch (n <= 2^20)."""
+    n = offsets.numel() - 1
+    _check(lib().bfs_run_noalloc(_ptr(offsets), _ptr(indices if indices.numel() else None), n,
+                                 indices.numel(), int(root), _ptr(level), _ptr(parent),
+                                 _stream(stream)))
+    return level, parent

@@ -28,6 +28,7 @@
 // the step kernels into the layer's trace slot. The host reads that slot after
 // each layer and applies the Alg. 3 switch.
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -931,5 +932,153 @@ extern "C" BFS_API bfs_status bfs_last_run_stats(const bfs_graph *g, bfs_layer_s
     for (int32_t i = 0; i < std::min(cap, L); ++i) out[i] = g->last[i];
     if (layers) *layers = L;
     if (component_edges) *component_edges = g->last_component_edges;
+    return BFS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// bfs_run_noalloc: the same traversal with its scratch in a fixed device array
+// instead of graph-owned allocations, for callers that may not allocate.
+// ---------------------------------------------------------------------------
+namespace gbfs {
+namespace {
+
+constexpr int64_t kNoAllocMaxN = 1 << 20;
+constexpr int64_t kNoAllocNwPad = ((((kNoAllocMaxN + 31) / 32) + 31) / 32) * 32;
+constexpr size_t kNoAllocBitmapBytes = (size_t)kNoAllocNwPad * 4;
+constexpr size_t kNoAllocQueueBytes = (size_t)kNoAllocMaxN * 4;
+constexpr size_t kNoAllocTraceBytes = (size_t)kRing * kFields * 8;
+// visited, base, front, next | q_a, q_b, big | trace
+constexpr size_t kNoAllocBytes =
+    4 * kNoAllocBitmapBytes + 3 * kNoAllocQueueBytes + kNoAllocTraceBytes;
+
+// Shared by every call in the process, one copy per device that loads the
+// library (about 12.5 MiB), kept until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Device address of g_noalloc_scratch, looked up once per device with that
+// device current (the host-side symbol is only a stand-in).
+bfs_status noalloc_scratch(unsigned char **out) {
+    static std::mutex mu;
+    static std::vector<unsigned char *> addr;
+    int dev = 0;
+    GB_CK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)addr.size() <= dev) addr.resize(dev + 1, nullptr);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        GB_CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        addr[dev] = (unsigned char *)p;
+    }
+    *out = addr[dev];
+    return BFS_OK;
+}
+
+}  // namespace
+}  // namespace gbfs
+
+extern "C" BFS_API bfs_status bfs_run_noalloc(const int64_t *offsets, const int32_t *indices,
+                                              int64_t n, int64_t nnz, int32_t root,
+                                              int32_t *level_out, int32_t *parent_out,
+                                              void *stream) {
+    clear_error();
+    if (!offsets || (nnz > 0 && !indices) || !level_out || !parent_out || nnz < 0 || n < 1) {
+        set_error("bfs_run_noalloc: need device offsets/indices/level_out/parent_out and n >= 1");
+        return BFS_ERR_INVALID;
+    }
+    if (n > kNoAllocMaxN) {
+        set_error("bfs_run_noalloc: n = %lld exceeds the fixed scratch limit of %lld vertices",
+                  (long long)n, (long long)kNoAllocMaxN);
+        return BFS_ERR_INVALID;
+    }
+    if (root < 0 || root >= n) {
+        set_error("bfs_run_noalloc: root out of range");
+        return BFS_ERR_INVALID;
+    }
+    unsigned char *base = nullptr;
+    bfs_status s = noalloc_scratch(&base);
+    if (s != BFS_OK) return s;
+    uint32_t *visited = (uint32_t *)base;
+    uint32_t *base_vis = visited + kNoAllocNwPad;
+    uint32_t *front = base_vis + kNoAllocNwPad;
+    uint32_t *next = front + kNoAllocNwPad;
+    int32_t *q_cur = (int32_t *)(next + kNoAllocNwPad);
+    int32_t *q_next = q_cur + kNoAllocMaxN;
+    int32_t *big = q_next + kNoAllocMaxN;
+    int64_t *trace = (int64_t *)(big + kNoAllocMaxN);
+
+    cudaStream_t st = as_stream(stream);
+    bfs_config cfg;
+    bfs_config_default(&cfg);
+    const int64_t nw_pad = (((n + 31) / 32 + 31) / 32) * 32;
+    int bu_occ = 1, td_occ = 1;
+    GB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu_occ, bu_kernel<2>, kBlock, 0));
+    GB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&td_occ, td_kernel, kBlock, 0));
+    // Every buffer the traversal reads before writing is set here: the base
+    // and visited bitmaps, the frontier bitmap, the first queue entry and the
+    // whole trace ring (init_kernel), so nothing of a previous call leaks in.
+    GB_LAUNCH(base_vis_kernel, grid_cap(nw_pad, kBlock, 8), kBlock, 0, st, offsets, n, nw_pad,
+              base_vis);
+    GB_LAUNCH(init_kernel, grid_cap(std::max(n, nw_pad), kBlock, 8), kBlock, 0, st, n, nw_pad,
+              root, offsets, base_vis, level_out, parent_out, visited, front, q_cur, trace);
+    int64_t h[kFields];
+    GB_CK(cudaMemcpyAsync(h, trace, sizeof h, cudaMemcpyDeviceToHost, st));
+    GB_CK(cudaStreamSynchronize(st));
+    int64_t n_f = 1, m_f = h[T_MF];
+    int64_t n_u = n - 1, m_u = nnz - m_f;
+    int cur_bu = 0;
+    bool have_queue = true;
+    const int bu_grid = (int)std::max<int64_t>(
+        1, std::min<int64_t>(nw_pad / 32 / (kBlock / 32) + 1, (int64_t)sm_count() * bu_occ));
+    const int64_t td_warps = (int64_t)sm_count() * td_occ * (kBlock / 32);
+    for (int d = 0; n_f > 0; ++d) {
+        if (d > n) {
+            set_error("bfs_run_noalloc: traversal did not terminate after %lld layers",
+                      (long long)n);
+            return BFS_ERR_CUDA;
+        }
+        cur_bu = decide(cfg, cur_bu, d, n, n_f, m_f, n_u, m_u);
+        int64_t *slot_cur = trace + (d % kRing) * kFields;
+        int64_t *slot_next = trace + ((d + 1) % kRing) * kFields;
+        int64_t *slot_zero = trace + ((d + 2) % kRing) * kFields;
+        if (!cur_bu) {
+            if (!have_queue)
+                GB_LAUNCH(b2q_kernel, grid_cap((n + 31) / 32, kBlock * 4, 8), kBlock, 0, st, front,
+                          (n + 31) / 32, q_cur, (unsigned long long *)(slot_cur + T_CONV));
+            GB_CK(cudaMemsetAsync(next, 0, (size_t)nw_pad * 4, st));
+            const int queue_mode = m_f <= kQueueModeMaxEdges ? 1 : 0;
+            TdArgs a{offsets, indices, visited, next, parent_out, level_out, q_next,
+                     (unsigned long long *)(slot_next + T_NF), d + 1, queue_mode};
+            const int per_warp = (int)std::min<int64_t>(
+                32, std::max<int64_t>(1, (n_f + td_warps - 1) / td_warps));
+            const int64_t grid_deg = std::min<int64_t>(
+                cfg.td_grid_degree,
+                std::max<int64_t>(4 * (int64_t)cfg.td_warp_degree, m_f / td_warps));
+            GB_LAUNCH(td_kernel, grid_cap((n_f + per_warp - 1) / per_warp, kBlock / 32, td_occ),
+                      kBlock, 0, st, a, q_cur, n_f, per_warp, big,
+                      (unsigned long long *)(slot_cur + T_BIG),
+                      (unsigned long long *)(slot_next + T_MF), cfg.td_warp_degree, grid_deg,
+                      slot_zero);
+            if (m_f >= grid_deg)
+                GB_LAUNCH(td_big_kernel,
+                          (int)std::max<int64_t>(1, std::min<int64_t>(m_f / 4096 + 1,
+                                                                      (int64_t)sm_count() * td_occ)),
+                          kBlock, 0, st, a, big, (const unsigned long long *)(slot_cur + T_BIG),
+                          (unsigned long long *)(slot_next + T_MF));
+            have_queue = queue_mode != 0;
+        } else {
+            GB_LAUNCH(bu_kernel<2>, bu_grid, kBlock, 0, st, offsets, indices, nw_pad, visited,
+                      front, next, parent_out, level_out, d + 1, cfg.bu_probe,
+                      (unsigned long long *)slot_next, slot_zero);
+            have_queue = false;
+        }
+        GB_CK(cudaMemcpyAsync(h, slot_next, sizeof h, cudaMemcpyDeviceToHost, st));
+        GB_CK(cudaStreamSynchronize(st));
+        n_u -= h[T_NF];
+        m_u -= h[T_MF];
+        n_f = h[T_NF];
+        m_f = h[T_MF];
+        std::swap(front, next);
+        std::swap(q_cur, q_next);
+    }
     return BFS_OK;
 }
