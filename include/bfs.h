@@ -132,8 +132,16 @@ typedef struct bfs_config {
                                 [4*td_warp_degree, td_grid_degree])            */
     int32_t timing;          /* 1 = record CUDA events around each layer      */
     int32_t bu_words;        /* bottom-up: bitmap words a warp keeps in
-                                flight (1 or 2)                                */
-    int32_t reserved[7];
+                                flight (1, 2 or 4)                             */
+    int32_t td_claim;        /* top-down claim of a vertex: 0 = atomicCAS on
+                                parent[v] (-1 -> u); 1 = atomicOr on the
+                                visited bitmap word, then plain parent store  */
+    int32_t bu_head;         /* 1 = the bottom-up probe reads a 16-byte record
+                                per vertex {first three neighbours, degree}
+                                built at graph creation (16*n bytes), one
+                                coalesced load instead of a row-bound pair
+                                and a random index sector; 0 = read the CSR  */
+    int32_t reserved[5];
 } bfs_config;
 
 /* Fills `cfg` with the defaults (edge policy, alpha 14, beta 24, ...). */

@@ -41,7 +41,8 @@ class Config(ctypes.Structure):
                 ("beta", ctypes.c_double), ("bu_probe", ctypes.c_int32),
                 ("td_warp_degree", ctypes.c_int32), ("td_grid_degree", ctypes.c_int32),
                 ("timing", ctypes.c_int32), ("bu_words", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("td_claim", ctypes.c_int32), ("bu_head", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class LayerStats(ctypes.Structure):

@@ -52,6 +52,7 @@ struct bfs_graph {
     int64_t *off_own = nullptr;
     int32_t *idx_own = nullptr;
     uint32_t *visited = nullptr, *bm_a = nullptr, *bm_b = nullptr;
+    int4 *head = nullptr;          // {first three neighbours (-1 if none), degree}
     uint32_t *base_vis = nullptr;  // bits that start every traversal visited:
                                    // degree-0 vertices and ids past n
     int32_t *q_a = nullptr, *q_b = nullptr, *big = nullptr;
@@ -62,7 +63,7 @@ struct bfs_graph {
     std::vector<bfs_layer_stats> last;
     int64_t last_component_edges = 0;
     std::vector<cudaEvent_t> events;
-    int bu_blocks_per_sm[2] = {1, 1};
+    int bu_blocks_per_sm[6] = {1, 1, 1, 1, 1, 1};  // BU1, BU2, BU4, BU1H, BU2H, BU4H
     int td_blocks_per_sm = 1;
 };
 
@@ -85,6 +86,18 @@ __global__ void base_vis_kernel(const int64_t *__restrict__ off, int64_t n, int6
             if (v >= n || off[v + 1] == off[v]) bits |= 1u << b;
         }
         base[w] = bits;
+    }
+}
+
+// Per-vertex head record for the bottom-up probe: the first three entries of
+// the vertex's CSR row (-1 past its degree) and the degree.
+__global__ void head_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
+                            int64_t n, int4 *__restrict__ head) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += stride) {
+        const int64_t b = off[v];
+        const int d = (int)(off[v + 1] - b);
+        head[v] = make_int4(d > 0 ? idx[b] : -1, d > 1 ? idx[b + 1] : -1, d > 2 ? idx[b + 2] : -1, d);
     }
 }
 
@@ -154,15 +167,19 @@ struct TdArgs {
     unsigned long long *next_count;  // trace slot of the next layer, T_NF
     int32_t new_level;
     int queue_mode;  // 1: append winners to q_next; 0: next bitmap only
+    int claim;       // 0: atomicCAS on parent; 1: atomicOr on the visited word
 };
 
 // K edges (u[k], v[k]) per lane of the top-down step (Alg. 1, lines 3-6),
 // called by all 32 lanes together; valid[k] masks missing edges. The visited
-// bitmap (L2-resident) filters first; the claim itself is the CAS on
-// parent[v]. The K loads and the K CASes of a lane are issued back to back.
-// A winner writes its level, sets its visited and next bits, and adds its
-// degree to *mf (and 1 to *nf). In queue mode winners are appended to the
-// next queue with one atomicAdd per warp and edge slot.
+// bitmap (L2-resident) filters first. The claim is either the CAS of
+// parent[v] from -1 to u (claim 0), or a fetch-or of v's bit into its
+// visited word (claim 1: an L2 atomic instead of a read-modify-write of the
+// parent array in HBM), after which the winner stores parent[v] = u. The K
+// loads and the K atomics of a lane are issued back to back. A winner writes
+// its level, sets its visited and next bits, and adds its degree to mf and 1
+// to nf. In queue mode winners are appended to the next queue with one
+// atomicAdd per warp and edge slot.
 template <int K>
 __device__ __forceinline__ void td_visit(const TdArgs &a, const bool (&valid)[K],
                                          const int32_t (&u)[K], const int32_t (&v)[K],
@@ -170,21 +187,36 @@ __device__ __forceinline__ void td_visit(const TdArgs &a, const bool (&valid)[K]
     uint32_t vw[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) vw[k] = valid[k] ? __ldcg(a.visited + (v[k] >> 5)) : 0xffffffffu;
-    int old[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const bool cand = valid[k] && !((vw[k] >> (v[k] & 31)) & 1u);
-        old[k] = cand ? atomicCAS(a.parent + v[k], -1, u[k]) : 0;
-    }
     bool won[K];
+    if (a.claim == 0) {
+        int old[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const bool cand = valid[k] && !((vw[k] >> (v[k] & 31)) & 1u);
+            old[k] = cand ? atomicCAS(a.parent + v[k], -1, u[k]) : 0;
+            won[k] = cand && old[k] == -1;
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (won[k]) atomicOr(a.visited + (v[k] >> 5), 1u << (v[k] & 31));
+    } else {
+        uint32_t old[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const uint32_t bit = 1u << (v[k] & 31);
+            const bool cand = valid[k] && !(vw[k] & bit);
+            old[k] = cand ? atomicOr(a.visited + (v[k] >> 5), bit) : 0xffffffffu;
+            won[k] = cand && !(old[k] & bit);
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (won[k]) a.parent[v[k]] = u[k];
+    }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        won[k] = valid[k] && old[k] == -1 && !((vw[k] >> (v[k] & 31)) & 1u);
         if (won[k]) {
-            const uint32_t bit = 1u << (v[k] & 31);
             a.level[v[k]] = a.new_level;
-            atomicOr(a.visited + (v[k] >> 5), bit);
-            atomicOr(a.next_bm + (v[k] >> 5), bit);
+            atomicOr(a.next_bm + (v[k] >> 5), 1u << (v[k] & 31));
             mf += deg_of(a.off, v[k]);
             nf += 1;
         }
@@ -373,17 +405,22 @@ __global__ void __launch_bounds__(kBlock) td_big_kernel(TdArgs a, const int32_t 
 // warp-per-word: a warp takes a chunk of 32 consecutive bitmap words (their
 // visited words loaded together) and walks it W words at a time, so W
 // independent word-tasks are in flight per warp. Per word and lane:
-//   1. the lane's own probe of its first `probe` neighbours, 4 independent
-//      index loads then 4 frontier-bit loads per round (the MAX_POS probe of
-//      Sec. 5.2, the 16-lane gather of Alg. 5 recast for 32 lanes);
+//   1. the lane's own probe of its first `probe` neighbours, CH independent
+//      index loads then CH frontier-bit loads per round (the MAX_POS probe of
+//      Sec. 5.2; the 16-lane gather of Alg. 5 recast for 32 lanes);
 //   2. the rows still unresolved are scanned by the whole warp, 64
 //      neighbours per round, __ballot_sync + __ffs selecting the first
 //      frontier neighbour in CSR order (Alg. 2 stops at the first hit);
 //   3. the ballot of found lanes is the next word and is ORed into the
 //      visited word by the owning warp, without atomics.
-template <int W>
+// Row positions are 32-bit offsets from a per-lane row pointer. With HEAD the
+// first three positions and the degree come from the vertex's 16-byte head
+// record (one coalesced load per lane); the row bounds are read only for
+// rows longer than three that found no parent there.
+template <int W, int CH, bool HEAD>
 __global__ void __launch_bounds__(kBlock) bu_kernel(
-    const int64_t *__restrict__ off, const int32_t *__restrict__ idx, int64_t nw_pad,
+    const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
+    const int4 *__restrict__ head, int64_t nw_pad,
     uint32_t *__restrict__ visited, const uint32_t *__restrict__ front,
     uint32_t *__restrict__ next_bm, int32_t *__restrict__ parent, int32_t *__restrict__ level,
     int32_t new_level, int probe, unsigned long long *slot_next, int64_t *zero_slot) {
@@ -395,6 +432,9 @@ __global__ void __launch_bounds__(kBlock) bu_kernel(
     int64_t my_nf = 0, my_mf = 0, my_ex = 0;
     for (int64_t c = gw; c < nchunks; c += tw) {
         const uint32_t vis_lane = visited[c * 32 + lane];
+        uint32_t *const next_c = next_bm + c * 32;
+        uint32_t *const vis_c = visited + c * 32;
+        const int64_t v_c = c * 1024 + lane;
         for (int j = 0; j < 32; j += W) {
             uint32_t vw[W];
             bool all = true;
@@ -404,46 +444,92 @@ __global__ void __launch_bounds__(kBlock) bu_kernel(
                 all = all && vw[k] == 0xffffffffu;
             }
             if (all) {
-                if ((int)lane < W) next_bm[c * 32 + j + lane] = 0u;
+                if ((int)lane < W) next_c[j + lane] = 0u;
                 continue;
             }
             bool unv[W], found[W];
-            int64_t beg[W], end[W], ex[W];
+            const int32_t *row[W];
+            int deg[W], ex[W];
             int32_t p[W];
+            // positions [0, lane_lim) are tested by the lane itself
+            const int lane_lim = HEAD ? (probe > 3 ? probe : 3) : probe;
+            if (HEAD) {
+                int4 h[W];
 #pragma unroll
-            for (int k = 0; k < W; ++k) {
-                const int64_t v = (c * 32 + j + k) * 32 + lane;
-                unv[k] = !((vw[k] >> lane) & 1u);  // bits past n are set
-                found[k] = false;
-                p[k] = -1;
-                ex[k] = 0;
-                beg[k] = unv[k] ? off[v] : 0;
-                end[k] = unv[k] ? off[v + 1] : 0;
+                for (int k = 0; k < W; ++k) {
+                    const int64_t v = v_c + (j + k) * 32;
+                    unv[k] = !((vw[k] >> lane) & 1u);  // bits past n are set
+                    found[k] = false;
+                    p[k] = -1;
+                    ex[k] = 0;
+                    h[k] = unv[k] ? __ldg(head + v) : make_int4(-1, -1, -1, 0);
+                    deg[k] = h[k].w;
+                    row[k] = idx;
+                }
+                uint32_t fw[W][3];
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    fw[k][0] = h[k].x >= 0 ? __ldg(front + (h[k].x >> 5)) : 0u;
+                    fw[k][1] = h[k].y >= 0 ? __ldg(front + (h[k].y >> 5)) : 0u;
+                    fw[k][2] = h[k].z >= 0 ? __ldg(front + (h[k].z >> 5)) : 0u;
+                }
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    const int32_t c3[3] = {h[k].x, h[k].y, h[k].z};
+#pragma unroll
+                    for (int t = 0; t < 3; ++t) {
+                        if (!found[k] && c3[t] >= 0) {
+                            ++ex[k];
+                            if ((fw[k][t] >> (c3[t] & 31)) & 1u) {
+                                found[k] = true;
+                                p[k] = c3[t];
+                            }
+                        }
+                    }
+                    if (unv[k] && !found[k] && deg[k] > 3)
+                        row[k] = idx + off[v_c + (j + k) * 32];
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    const int64_t v = v_c + (j + k) * 32;
+                    unv[k] = !((vw[k] >> lane) & 1u);  // bits past n are set
+                    found[k] = false;
+                    p[k] = -1;
+                    ex[k] = 0;
+                    int64_t b = 0, e = 0;
+                    if (unv[k]) {
+                        b = off[v];
+                        e = off[v + 1];
+                    }
+                    row[k] = idx + b;
+                    deg[k] = (int)(e - b);
+                }
             }
-            for (int p0 = 0; p0 < probe; p0 += 4) {
-                int32_t cand[W][4];
+            for (int p0 = HEAD ? 3 : 0; p0 < lane_lim; p0 += CH) {
+                int32_t cand[W][CH];
                 bool any = false;
 #pragma unroll
                 for (int k = 0; k < W; ++k) {
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        const int64_t e = beg[k] + p0 + t;
-                        const bool ok = unv[k] && !found[k] && p0 + t < probe && e < end[k];
-                        cand[k][t] = ok ? __ldg(idx + e) : -1;
+                    for (int t = 0; t < CH; ++t) {
+                        const int q = p0 + t;
+                        const bool ok = unv[k] && !found[k] && q < lane_lim && q < deg[k];
+                        cand[k][t] = ok ? __ldg(row[k] + q) : -1;
                         any = any || ok;
                     }
                 }
                 if (!any) break;
-                uint32_t fw[W][4];
+                uint32_t fw[W][CH];
 #pragma unroll
                 for (int k = 0; k < W; ++k)
 #pragma unroll
-                    for (int t = 0; t < 4; ++t)
+                    for (int t = 0; t < CH; ++t)
                         fw[k][t] = cand[k][t] >= 0 ? __ldg(front + (cand[k][t] >> 5)) : 0u;
 #pragma unroll
                 for (int k = 0; k < W; ++k) {
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) {
+                    for (int t = 0; t < CH; ++t) {
                         if (!found[k] && cand[k][t] >= 0) {
                             ++ex[k];
                             if ((fw[k][t] >> (cand[k][t] & 31)) & 1u) {
@@ -456,21 +542,21 @@ __global__ void __launch_bounds__(kBlock) bu_kernel(
             }
 #pragma unroll
             for (int k = 0; k < W; ++k) {
-                const int64_t rest = beg[k] + probe;
-                unsigned pend = __ballot_sync(0xffffffffu, unv[k] && !found[k] && rest < end[k]);
+                unsigned pend = __ballot_sync(0xffffffffu, unv[k] && !found[k] && lane_lim < deg[k]);
                 while (pend) {
                     const int L = __ffs(pend) - 1;
                     pend &= pend - 1;
-                    const int64_t lb = __shfl_sync(0xffffffffu, rest, L);
-                    const int64_t le = __shfl_sync(0xffffffffu, end[k], L);
+                    const int32_t *lrow = (const int32_t *)__shfl_sync(
+                        0xffffffffu, (unsigned long long)row[k], L);
+                    const int ld = __shfl_sync(0xffffffffu, deg[k], L);
                     bool hit_any = false;
-                    for (int64_t e0 = lb; e0 < le; e0 += 64) {
+                    for (int q0 = lane_lim; q0 < ld; q0 += 64) {
                         int32_t uu[2];
                         bool hit[2];
 #pragma unroll
                         for (int t = 0; t < 2; ++t) {
-                            const int64_t e = e0 + 32 * t + lane;
-                            uu[t] = e < le ? __ldg(idx + e) : -1;
+                            const int q = q0 + 32 * t + (int)lane;
+                            uu[t] = q < ld ? __ldg(lrow + q) : -1;
                         }
 #pragma unroll
                         for (int t = 0; t < 2; ++t)
@@ -484,29 +570,28 @@ __global__ void __launch_bounds__(kBlock) bu_kernel(
                             if ((int)lane == L) {
                                 found[k] = true;
                                 p[k] = pu;
-                                ex[k] += (e0 - lb) + 32 * t + first + 1;
+                                ex[k] += (q0 - lane_lim) + 32 * t + first + 1;
                             }
                             hit_any = true;
                             break;
                         }
                     }
-                    if (!hit_any && (int)lane == L) ex[k] += le - lb;
+                    if (!hit_any && (int)lane == L) ex[k] += ld - lane_lim;
                 }
             }
 #pragma unroll
             for (int k = 0; k < W; ++k) {
-                const int64_t w = c * 32 + j + k;
-                const int64_t v = w * 32 + lane;
+                const int64_t v = v_c + (j + k) * 32;
                 const unsigned fm = __ballot_sync(0xffffffffu, found[k]);
                 if (found[k]) {
                     parent[v] = p[k];
                     level[v] = new_level;
-                    my_mf += end[k] - beg[k];
+                    my_mf += deg[k];
                 }
                 my_ex += ex[k];
                 if (lane == 0) {
-                    next_bm[w] = fm;
-                    if (fm) visited[w] = vw[k] | fm;
+                    next_c[j + k] = fm;
+                    if (fm) vis_c[j + k] = vw[k] | fm;
                     my_nf += __popc(fm);
                 }
             }
@@ -514,6 +599,13 @@ __global__ void __launch_bounds__(kBlock) bu_kernel(
     }
     block_add3(my_nf, my_mf, my_ex, slot_next + T_NF, slot_next + T_MF, slot_next + T_EXAM);
 }
+
+constexpr auto BU1 = bu_kernel<1, 4, false>;
+constexpr auto BU2 = bu_kernel<2, 4, false>;
+constexpr auto BU4 = bu_kernel<4, 2, false>;
+constexpr auto BU1H = bu_kernel<1, 4, true>;
+constexpr auto BU2H = bu_kernel<2, 4, true>;
+constexpr auto BU4H = bu_kernel<4, 2, true>;
 
 // Frontier bitmap -> queue: each thread takes 4 consecutive words, a block
 // scan orders the set bits, one atomicAdd per block reserves queue space.
@@ -580,7 +672,9 @@ bool config_ok(const bfs_config &c) {
     if (!(c.alpha > 0) || !(c.beta > 0)) return false;
     if (c.bu_probe < 1 || c.bu_probe > 64) return false;
     if (c.td_warp_degree < 1 || c.td_grid_degree < c.td_warp_degree) return false;
-    if (c.bu_words != 1 && c.bu_words != 2) return false;
+    if (c.bu_words != 1 && c.bu_words != 2 && c.bu_words != 4) return false;
+    if (c.td_claim != 0 && c.td_claim != 1) return false;
+    if (c.bu_head != 0 && c.bu_head != 1) return false;
     return true;
 }
 
@@ -612,6 +706,7 @@ void free_graph(bfs_graph *g) {
     cudaFree(g->idx_own);
     cudaFree(g->visited);
     cudaFree(g->base_vis);
+    cudaFree(g->head);
     cudaFree(g->bm_a);
     cudaFree(g->bm_b);
     cudaFree(g->q_a);
@@ -641,7 +736,8 @@ extern "C" BFS_API void bfs_config_default(bfs_config *c) {
     c->td_warp_degree = 32;
     c->td_grid_degree = 1024;
     c->timing = 0;
-    c->bu_words = 2;
+    c->bu_words = 4;
+    c->bu_head = 0;
 }
 
 extern "C" BFS_API bfs_status bfs_graph_create(const int64_t *offsets, const int32_t *indices,
@@ -721,10 +817,12 @@ extern "C" BFS_API bfs_status bfs_graph_create(const int64_t *offsets, const int
     count_launch();
     GB_CKG(cudaGetLastError());
     GB_CKG(cudaDeviceSynchronize());
-    GB_CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->bu_blocks_per_sm[0], bu_kernel<1>,
-                                                         kBlock, 0));
-    GB_CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->bu_blocks_per_sm[1], bu_kernel<2>,
-                                                         kBlock, 0));
+    GB_CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->bu_blocks_per_sm[0], BU1, kBlock, 0));
+    GB_CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->bu_blocks_per_sm[1], BU2, kBlock, 0));
+    GB_CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->bu_blocks_per_sm[2], BU4, kBlock, 0));
+    GB_CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->bu_blocks_per_sm[3], BU1H, kBlock, 0));
+    GB_CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->bu_blocks_per_sm[4], BU2H, kBlock, 0));
+    GB_CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->bu_blocks_per_sm[5], BU4H, kBlock, 0));
     GB_CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->td_blocks_per_sm, td_kernel, kBlock, 0));
 #undef GB_CKG
     *out = g;
@@ -803,6 +901,10 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
         return g->events[i];
     };
 
+    if (cfg.bu_head && !g->head) {  // head records are built on first use
+        GB_CK(cudaMalloc(&g->head, (size_t)n * sizeof(int4)));
+        GB_LAUNCH(head_kernel, grid_cap(n, kBlock, 8), kBlock, 0, st, g->off, g->idx, n, g->head);
+    }
     g->last.clear();
     uint32_t *front = g->bm_a, *next = g->bm_b;
     int32_t *q_cur = g->q_a, *q_next = g->q_b;
@@ -817,9 +919,10 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
     bool have_queue = true;
     int64_t degree_sum = 0;
     const int bw = cfg.bu_words;
+    const int bsel = (bw == 4 ? 2 : bw - 1) + (cfg.bu_head ? 3 : 0);
     const int bu_grid = (int)std::max<int64_t>(
         1, std::min<int64_t>(g->nw_pad / 32 / (kBlock / 32) + 1,
-                             (int64_t)sm_count() * g->bu_blocks_per_sm[bw - 1]));
+                             (int64_t)sm_count() * g->bu_blocks_per_sm[bsel]));
     const int64_t td_warps = (int64_t)sm_count() * g->td_blocks_per_sm * (kBlock / 32);
     for (int d = 0; n_f > 0; ++d) {
         if (d > n) {  // a BFS has at most n layers: the counters are inconsistent
@@ -853,7 +956,7 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
             // queue is rebuilt by b2q if the next layer is top-down too.
             const int queue_mode = m_f <= kQueueModeMaxEdges ? 1 : 0;
             TdArgs a{g->off, g->idx, g->visited, next, parent, level, q_next,
-                     (unsigned long long *)(slot_next + T_NF), d + 1, queue_mode};
+                     (unsigned long long *)(slot_next + T_NF), d + 1, queue_mode, cfg.td_claim};
             // Entries per warp so that a small frontier still covers the GPU,
             // and the grid-spread threshold at the frontier's edges per warp.
             const int per_warp = (int)std::min<int64_t>(32, std::max<int64_t>(1, (n_f + td_warps - 1) / td_warps));
@@ -877,14 +980,11 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
             have_queue = queue_mode != 0;
         } else {
             if (timing) GB_CK(cudaEventRecord(event(e0 + 1), st));
-            if (bw == 1)
-                GB_LAUNCH(bu_kernel<1>, bu_grid, kBlock, 0, st, g->off, g->idx, g->nw_pad,
-                          g->visited, front, next, parent, level, d + 1, cfg.bu_probe,
-                          (unsigned long long *)slot_next, slot_zero);
-            else
-                GB_LAUNCH(bu_kernel<2>, bu_grid, kBlock, 0, st, g->off, g->idx, g->nw_pad,
-                          g->visited, front, next, parent, level, d + 1, cfg.bu_probe,
-                          (unsigned long long *)slot_next, slot_zero);
+            decltype(BU1) const kernels[6] = {BU1, BU2, BU4, BU1H, BU2H, BU4H};
+            auto bu = kernels[bsel];
+            GB_LAUNCH(bu, bu_grid, kBlock, 0, st, g->off, g->idx, g->head, g->nw_pad, g->visited, front,
+                      next, parent, level, d + 1, cfg.bu_probe, (unsigned long long *)slot_next,
+                      slot_zero);
             have_queue = false;
         }
         if (timing) GB_CK(cudaEventRecord(event(e0 + 2), st));
@@ -1011,7 +1111,7 @@ extern "C" BFS_API bfs_status bfs_run_noalloc(const int64_t *offsets, const int3
     bfs_config_default(&cfg);
     const int64_t nw_pad = (((n + 31) / 32 + 31) / 32) * 32;
     int bu_occ = 1, td_occ = 1;
-    GB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu_occ, bu_kernel<2>, kBlock, 0));
+    GB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu_occ, BU2, kBlock, 0));
     GB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&td_occ, td_kernel, kBlock, 0));
     // Every buffer the traversal reads before writing is set here: the base
     // and visited bitmaps, the frontier bitmap, the first queue entry and the
@@ -1047,7 +1147,7 @@ extern "C" BFS_API bfs_status bfs_run_noalloc(const int64_t *offsets, const int3
             GB_CK(cudaMemsetAsync(next, 0, (size_t)nw_pad * 4, st));
             const int queue_mode = m_f <= kQueueModeMaxEdges ? 1 : 0;
             TdArgs a{offsets, indices, visited, next, parent_out, level_out, q_next,
-                     (unsigned long long *)(slot_next + T_NF), d + 1, queue_mode};
+                     (unsigned long long *)(slot_next + T_NF), d + 1, queue_mode, cfg.td_claim};
             const int per_warp = (int)std::min<int64_t>(
                 32, std::max<int64_t>(1, (n_f + td_warps - 1) / td_warps));
             const int64_t grid_deg = std::min<int64_t>(
@@ -1066,7 +1166,7 @@ extern "C" BFS_API bfs_status bfs_run_noalloc(const int64_t *offsets, const int3
                           (unsigned long long *)(slot_next + T_MF));
             have_queue = queue_mode != 0;
         } else {
-            GB_LAUNCH(bu_kernel<2>, bu_grid, kBlock, 0, st, offsets, indices, nw_pad, visited,
+            GB_LAUNCH(BU2, bu_grid, kBlock, 0, st, offsets, indices, nullptr, nw_pad, visited,
                       front, next, parent_out, level_out, d + 1, cfg.bu_probe,
                       (unsigned long long *)slot_next, slot_zero);
             have_queue = false;

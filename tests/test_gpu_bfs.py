@@ -80,14 +80,16 @@ def test_closed_form_graphs_forced_directions(name, pat):
 
 @pytest.mark.parametrize("seed", range(6))
 @pytest.mark.parametrize("policy", [gb.POLICY_EDGE, gb.POLICY_VERTEX])
-def test_policies_on_skewed_graphs(seed, policy):
+@pytest.mark.parametrize("claim", [0, 1])
+def test_policies_on_skewed_graphs(seed, policy, claim):
     n = [300, 2049, 5000, 10007, 40000, 65536][seed]
     if seed % 2:
         s, d = inputs.powerlaw_edges(n, 8 * n, seed, hubs=5)
     else:
         s, d = oracle.gen_edges(oracle.RMAT, 12 + seed // 2, 8, seed)
         n = 1 << (12 + seed // 2)
-    o_off, o_idx, g = make(n, s, d, policy=policy)
+    o_off, o_idx, g = make(n, s, d, policy=policy, td_claim=claim, bu_words=[1, 2, 4][seed % 3],
+                           bu_head=(seed // 3 + claim) % 2)
     for r in oracle.sample_roots(o_off, n, seed, 4):
         check_run(o_off, o_idx, g, int(r), policy=policy)
 
@@ -105,7 +107,10 @@ def test_degree_bin_boundaries(deg, pat):
     forced = FORCED[pat]
     for cfg in [dict(forced=forced), dict(forced=forced, td_warp_degree=8, td_grid_degree=64),
                 dict(forced=forced, bu_probe=1), dict(forced=forced, bu_probe=33),
-                dict(forced=forced, bu_words=1, bu_probe=5)]:
+                dict(forced=forced, bu_words=1, bu_probe=5),
+                dict(forced=forced, bu_words=4, bu_probe=7, td_claim=1),
+                dict(forced=forced, bu_head=0), dict(forced=forced, bu_head=1, bu_probe=2),
+                dict(forced=forced, bu_head=1, bu_probe=4, bu_words=2)]:
         o_off, o_idx, g = make(n, s, d, **cfg)
         for r in [0, 1, n - 1, deg // 2]:
             check_run(o_off, o_idx, g, r, forced=forced)
