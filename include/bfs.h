@@ -138,7 +138,7 @@ typedef struct bfs_config {
                                 visited bitmap word, then plain parent store  */
     int32_t bu_head;         /* 1 = the bottom-up probe reads a 16-byte record
                                 per vertex {first three neighbours, degree}
-                                built at graph creation (16*n bytes), one
+                                built on first use (16*n bytes), one
                                 coalesced load instead of a row-bound pair
                                 and a random index sector; 0 = read the CSR  */
     int32_t reserved[5];
@@ -154,8 +154,11 @@ BFS_API void bfs_config_default(bfs_config *cfg);
                                offsets[n]=nnz and indices in [0, n)            */
 
 /* Creates a graph from a symmetric CSR (layout above) and allocates its
- * per-traversal scratch: three n-bit bitmaps (visited, frontier, next), two
- * n-entry vertex queues and a small counter block, about 8.4*n bytes.
+ * per-traversal scratch: four n-bit bitmaps (visited, frontier, next, and
+ * the degree-0 mask), three n-entry vertex lists (two queues and the list of
+ * grid-spread vertices) and a small counter block: about 12.5*n bytes. The
+ * 16-byte head records (cfg.bu_head) are built by the first bfs_run that
+ * asks for them.
  * Without BFS_BORROW the CSR is copied into library memory and the caller may
  * free its arrays. cfg may be NULL (defaults). Synchronous. */
 BFS_API bfs_status bfs_graph_create(const int64_t *offsets, const int32_t *indices, int64_t n,
