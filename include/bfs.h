@@ -213,6 +213,71 @@ BFS_API bfs_status bfs_last_run_stats(const bfs_graph *g, bfs_layer_stats *out, 
                                       int32_t *layers, int64_t *component_edges);
 
 /* ---------------------------------------------------------------------- */
+/* Batched multi-source BFS. The paper runs its 64 roots one after another */
+/* (Sec. 6.3); here up to 512 roots share one traversal: root i is bit i of */
+/* a per-vertex bitset, so one sweep of a vertex's row serves every root.  */
+/* Each layer is the bottom-up step of Alg. 2 generalised to bit lanes (a  */
+/* vertex ORs its neighbours' frontier words and stops once every lane it  */
+/* still lacks is found: the paper's early exit, per lane set) or the      */
+/* top-down step of Alg. 1 (frontier words ORed into neighbours' next      */
+/* words), chosen per layer by the edge form of the Alg. 3 switch.         */
+/* ---------------------------------------------------------------------- */
+typedef struct bfs_batch_config {
+    double alpha;         /* top-down -> bottom-up iff e_f > e_u / alpha, where
+                             e_f = degree sum of vertices with a frontier bit
+                             and e_u = degree sum of vertices still lacking
+                             some root's bit                                  */
+    double beta;          /* bottom-up -> top-down iff v_f < n / beta         */
+    int32_t lane_probe;   /* bottom-up: neighbours a lane scans alone before
+                             the warp-cooperative OR-reduction takes over     */
+    int32_t big_degree;   /* top-down: degree from which a vertex's edges are
+                             spread over the grid                             */
+    int32_t use_graph;    /* 1 = run the layers as one CUDA graph with a
+                             device-side loop (no per-layer host round trip) */
+    int32_t timing;       /* 1 = record CUDA events per layer                 */
+    int32_t reserved[8];
+} bfs_batch_config;
+
+BFS_API void bfs_batch_config_default(bfs_batch_config *cfg);
+BFS_API bfs_status bfs_graph_set_batch_config(bfs_graph *g, const bfs_batch_config *cfg);
+BFS_API bfs_status bfs_graph_get_batch_config(const bfs_graph *g, bfs_batch_config *cfg);
+
+/* BFS from k roots at once (1 <= k <= 512; repeats allowed).
+ *   roots        k int32 vertex ids, host or device memory
+ *   levels_out   device, caller-owned, k*n int8, row i = levels from roots[i]
+ *                (level[v] = hop distance, -1 when unreachable)
+ * A level above 127 does not fit: the traversal stops after writing level
+ * 127 and returns BFS_ERR_DEPTH (no value wraps). The bitsets (three arrays
+ * of n * ceil(k/64 rounded to 1, 2, 4 or 8) 64-bit words) are allocated on
+ * first use and kept by the graph. Synchronous, like bfs_run. */
+BFS_API bfs_status bfs_run_batch(bfs_graph *g, const int32_t *roots, int32_t k,
+                                 int8_t *levels_out, void *stream);
+
+/* Per-layer record of the last bfs_run_batch. */
+typedef struct bfs_batch_layer_stats {
+    int32_t direction;   /* 0 = top-down, 1 = bottom-up                       */
+    int32_t pad;
+    int64_t v_f;         /* vertices holding at least one frontier bit        */
+    int64_t e_f;         /* their degree sum                                  */
+    int64_t pairs;       /* (root, vertex) pairs in the frontier              */
+    int64_t v_u;         /* vertices still lacking some root's bit            */
+    int64_t e_u;         /* their degree sum                                  */
+    float ms;            /* layer time when cfg.timing = 1                    */
+    float pad2;
+} bfs_batch_layer_stats;
+
+BFS_API bfs_status bfs_last_batch_stats(const bfs_graph *g, bfs_batch_layer_stats *out,
+                                        int32_t cap, int32_t *layers, int64_t *pairs_reached);
+
+/* Autotuner: runs the batch from `roots` under a small grid of switch
+ * thresholds (alpha, beta) and lane-probe lengths, keeps the fastest in the
+ * graph's batch configuration and copies it to *best (may be NULL).
+ * levels_scratch is a device k*n int8 buffer it may overwrite. */
+BFS_API bfs_status bfs_batch_autotune(bfs_graph *g, const int32_t *roots, int32_t k,
+                                      int8_t *levels_scratch, bfs_batch_config *best,
+                                      void *stream);
+
+/* ---------------------------------------------------------------------- */
 /* Allocation-free traversal. The paper has no counterpart: this entry     */
 /* point exists for callers that must not allocate device memory.         */
 /* ---------------------------------------------------------------------- */

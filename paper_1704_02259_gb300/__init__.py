@@ -52,6 +52,20 @@ class LayerStats(ctypes.Structure):
                 ("ms_total", ctypes.c_float), ("ms_main", ctypes.c_float)]
 
 
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+                ("lane_probe", ctypes.c_int32), ("big_degree", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32), ("timing", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 8)]
+
+
+class BatchLayerStats(ctypes.Structure):
+    _fields_ = [("direction", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("v_f", ctypes.c_int64), ("e_f", ctypes.c_int64), ("pairs", ctypes.c_int64),
+                ("v_u", ctypes.c_int64), ("e_u", ctypes.c_int64), ("ms", ctypes.c_float),
+                ("pad2", ctypes.c_float)]
+
+
 _lib = None
 P = ctypes.c_void_p
 I32, I64, U32, U64, DBL = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
@@ -71,6 +85,12 @@ SIGNATURES = {
     "bfs_run": (I32, [P, I32, P, P, P]),
     "bfs_last_run_stats": (I32, [P, P, I32, P, P]),
     "bfs_run_noalloc": (I32, [P, P, I64, I64, I32, P, P, P]),
+    "bfs_batch_config_default": (None, [P]),
+    "bfs_graph_set_batch_config": (I32, [P, P]),
+    "bfs_graph_get_batch_config": (I32, [P, P]),
+    "bfs_run_batch": (I32, [P, P, I32, P, P]),
+    "bfs_last_batch_stats": (I32, [P, P, I32, P, P]),
+    "bfs_batch_autotune": (I32, [P, P, I32, P, P, P]),
 }
 
 
@@ -116,6 +136,12 @@ def _ptr(t: torch.Tensor | None):
 
 def launch_count() -> int:
     return int(lib().bfs_launch_count())
+
+
+def default_batch_config() -> BatchConfig:
+    c = BatchConfig()
+    lib().bfs_batch_config_default(ctypes.byref(c))
+    return c
 
 
 def default_config() -> Config:
@@ -216,6 +242,48 @@ class Graph:
         _check(lib().bfs_last_run_stats(self._h, arr, L.value, ctypes.byref(L), ctypes.byref(ce)))
         layers = [{f: getattr(arr[i], f) for f, _ in LayerStats._fields_} for i in range(L.value)]
         return RunStats(layers, ce.value)
+
+    # ---------------------------------------------------------- batched BFS
+    def batch_config(self) -> BatchConfig:
+        c = BatchConfig()
+        _check(lib().bfs_graph_get_batch_config(self._h, ctypes.byref(c)))
+        return c
+
+    def set_batch_config(self, config: BatchConfig | None):
+        _check(lib().bfs_graph_set_batch_config(self._h, ctypes.byref(config) if config else None))
+
+    def run_batch(self, roots, levels: torch.Tensor | None = None, stream=None):
+        """Levels from every root at once: int8 [k, n] (row i = roots[i])."""
+        if not isinstance(roots, torch.Tensor):
+            roots = torch.tensor(list(roots), dtype=torch.int32)
+        roots = roots.to(torch.int32).contiguous()
+        k = roots.numel()
+        if levels is None:
+            levels = torch.empty((k, self.n), dtype=torch.int8, device="cuda")
+        _check(lib().bfs_run_batch(self._h, _ptr(roots), k, _ptr(levels), _stream(stream)))
+        return levels
+
+    def batch_stats(self):
+        L = ctypes.c_int32(0)
+        pairs = ctypes.c_int64(0)
+        _check(lib().bfs_last_batch_stats(self._h, None, 0, ctypes.byref(L), None))
+        arr = (BatchLayerStats * max(L.value, 1))()
+        _check(lib().bfs_last_batch_stats(self._h, arr, L.value, ctypes.byref(L),
+                                          ctypes.byref(pairs)))
+        layers = [{f: getattr(arr[i], f) for f, _ in BatchLayerStats._fields_}
+                  for i in range(L.value)]
+        return layers, pairs.value
+
+    def autotune_batch(self, roots, stream=None) -> BatchConfig:
+        if not isinstance(roots, torch.Tensor):
+            roots = torch.tensor(list(roots), dtype=torch.int32)
+        roots = roots.to(torch.int32).contiguous()
+        k = roots.numel()
+        scratch = torch.empty((k, self.n), dtype=torch.int8, device="cuda")
+        best = BatchConfig()
+        _check(lib().bfs_batch_autotune(self._h, _ptr(roots), k, _ptr(scratch), ctypes.byref(best),
+                                        _stream(stream)))
+        return best
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

@@ -33,39 +33,7 @@
 
 #include "common.cuh"
 
-namespace gbfs {
-
-constexpr int kRing = 64;  // trace ring slots (layers)
-constexpr int kFields = 8;
-enum TraceField { T_NF = 0, T_MF = 1, T_EXAM = 2, T_CONV = 3, T_BIG = 4 };
-constexpr int kBlock = 256;
-constexpr int kBigBatch = 1024;
-constexpr int64_t kQueueModeMaxEdges = 1 << 18;
-
-}  // namespace gbfs
-
-struct bfs_graph {
-    int device = 0;
-    int64_t n = 0, nnz = 0, nw = 0, nw_pad = 0;
-    const int64_t *off = nullptr;
-    const int32_t *idx = nullptr;
-    int64_t *off_own = nullptr;
-    int32_t *idx_own = nullptr;
-    uint32_t *visited = nullptr, *bm_a = nullptr, *bm_b = nullptr;
-    int4 *head = nullptr;          // {first three neighbours (-1 if none), degree}
-    uint32_t *base_vis = nullptr;  // bits that start every traversal visited:
-                                   // degree-0 vertices and ids past n
-    int32_t *q_a = nullptr, *q_b = nullptr, *big = nullptr;
-    int32_t *parent_scratch = nullptr, *level_scratch = nullptr;
-    int64_t *trace = nullptr;
-    int64_t *h_slot = nullptr;  // pinned, kFields entries
-    bfs_config cfg;
-    std::vector<bfs_layer_stats> last;
-    int64_t last_component_edges = 0;
-    std::vector<cudaEvent_t> events;
-    int bu_blocks_per_sm[6] = {1, 1, 1, 1, 1, 1};  // BU1, BU2, BU4, BU1H, BU2H, BU4H
-    int td_blocks_per_sm = 1;
-};
+#include "graph.cuh"
 
 namespace gbfs {
 namespace {
@@ -660,11 +628,6 @@ __global__ void validate_kernel(const int64_t *__restrict__ off, const int32_t *
         if (idx[e] < 0 || idx[e] >= n) *bad = 1;
 }
 
-int grid_cap(int64_t work_items, int per_block, int blocks_per_sm) {
-    int64_t g = (work_items + per_block - 1) / per_block;
-    const int64_t cap = (int64_t)sm_count() * std::max(1, blocks_per_sm);
-    return (int)std::max<int64_t>(1, std::min(g, cap));
-}
 
 bool config_ok(const bfs_config &c) {
     if (c.policy < 0 || c.policy > 2) return false;
@@ -702,6 +665,7 @@ bool is_host_ptr(const void *p) {
 
 void free_graph(bfs_graph *g) {
     if (!g) return;
+    free_ms_state(g);
     cudaFree(g->off_own);
     cudaFree(g->idx_own);
     cudaFree(g->visited);

@@ -1,0 +1,57 @@
+// graph.cuh -- the bfs_graph object shared by the single-source and the
+// batched traversal, and small host helpers used by both.
+#pragma once
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace gbfs {
+
+constexpr int kRing = 64;  // trace ring slots (layers)
+constexpr int kFields = 8;
+enum TraceField { T_NF = 0, T_MF = 1, T_EXAM = 2, T_CONV = 3, T_BIG = 4 };
+constexpr int kBlock = 256;
+constexpr int kBigBatch = 1024;
+constexpr int64_t kQueueModeMaxEdges = 1 << 18;
+
+}  // namespace gbfs
+
+struct MsState;  // batched-traversal buffers (msbfs.cu), allocated on first use
+
+struct bfs_graph {
+    int device = 0;
+    int64_t n = 0, nnz = 0, nw = 0, nw_pad = 0;
+    const int64_t *off = nullptr;
+    const int32_t *idx = nullptr;
+    int64_t *off_own = nullptr;
+    int32_t *idx_own = nullptr;
+    uint32_t *visited = nullptr, *bm_a = nullptr, *bm_b = nullptr;
+    int4 *head = nullptr;          // {first three neighbours (-1 if none), degree}
+    uint32_t *base_vis = nullptr;  // bits that start every traversal visited:
+                                   // degree-0 vertices and ids past n
+    int32_t *q_a = nullptr, *q_b = nullptr, *big = nullptr;
+    int32_t *parent_scratch = nullptr, *level_scratch = nullptr;
+    int64_t *trace = nullptr;
+    int64_t *h_slot = nullptr;  // pinned, kFields entries
+    bfs_config cfg;
+    std::vector<bfs_layer_stats> last;
+    int64_t last_component_edges = 0;
+    std::vector<cudaEvent_t> events;
+    int bu_blocks_per_sm[6] = {1, 1, 1, 1, 1, 1};  // BU1, BU2, BU4, BU1H, BU2H, BU4H
+    int td_blocks_per_sm = 1;
+    MsState *ms = nullptr;
+};
+
+namespace gbfs {
+
+inline int grid_cap(int64_t work_items, int per_block, int blocks_per_sm) {
+    int64_t g = (work_items + per_block - 1) / per_block;
+    const int64_t cap = (int64_t)sm_count() * std::max(1, blocks_per_sm);
+    return (int)std::max<int64_t>(1, std::min(g, cap));
+}
+
+void free_ms_state(bfs_graph *g);  // msbfs.cu
+
+}  // namespace gbfs

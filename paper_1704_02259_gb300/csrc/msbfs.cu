@@ -1,0 +1,852 @@
+// msbfs.cu -- batched multi-source BFS: up to 512 roots share one traversal.
+//
+// Root i owns bit i of a per-vertex bitset of W 64-bit words (W = 1, 2, 4 or
+// 8): seen[v] (roots that reached v), cur[v] (roots whose frontier holds v)
+// and nxt[v] (roots reaching v in this layer). A layer is
+//   bottom-up (Alg. 2 on bit lanes): every vertex still lacking some roots
+//     ORs the frontier words of its neighbours, in CSR order, and stops as
+//     soon as every lacking root is found -- the paper's early exit, taken
+//     per lane set. A lane scans `lane_probe` neighbours alone; longer rows
+//     are finished by the warp with a 64-bit OR reduction over 32 neighbours
+//     per round. The vertex's own thread then updates seen, nxt and the int8
+//     level rows, so no separate pass is needed;
+//   top-down (Alg. 1 on bit lanes): the vertices holding frontier bits are
+//     compacted into a list (heavy ones into a grid-spread list), their
+//     frontier words are ORed into each neighbour's nxt with 64-bit
+//     atomicOr, and a dense pass keeps the bits not yet seen.
+// The direction is the edge form of the Alg. 3 switch over vertex counts:
+// e_f is the degree sum of vertices holding a frontier bit, e_u that of
+// vertices still lacking some root.
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "graph.cuh"
+
+struct MsState {
+    int W = 0;
+    int64_t n = 0;
+    unsigned long long *seen = nullptr, *cur = nullptr, *nxt = nullptr;
+    int32_t *list = nullptr, *big = nullptr, *roots = nullptr;
+    int64_t *trace = nullptr;
+    int64_t *h_slot = nullptr;  // pinned
+    bfs_batch_config cfg;
+    std::vector<bfs_batch_layer_stats> last;
+    int64_t last_pairs = 0;
+    std::vector<cudaEvent_t> events;
+};
+
+namespace gbfs {
+
+void free_ms_state(bfs_graph *g) {
+    if (!g || !g->ms) return;
+    MsState *m = g->ms;
+    cudaFree(m->seen);
+    cudaFree(m->cur);
+    cudaFree(m->nxt);
+    cudaFree(m->list);
+    cudaFree(m->big);
+    cudaFree(m->roots);
+    cudaFree(m->trace);
+    if (m->h_slot) cudaFreeHost(m->h_slot);
+    for (cudaEvent_t e : m->events) cudaEventDestroy(e);
+    delete m;
+    g->ms = nullptr;
+}
+
+namespace {
+
+// Trace slot fields; the step kernels add fields 0-5 with one block_add.
+enum MsField { M_NV = 0, M_MF = 1, M_PAIRS = 2, M_FULLN = 3, M_FULLDEG = 4, M_EXAM = 5,
+               M_LIST = 6, M_BIG = 7 };
+constexpr int kMsBlock = 256;
+constexpr int kMsBigBatch = 1024;
+constexpr int kMaxRoots = 512;
+
+template <int W>
+struct Lanes {
+    unsigned long long w[W];
+};
+
+template <int W>
+__device__ __forceinline__ void load_lanes(const unsigned long long *p,
+                                           unsigned long long (&x)[W]) {
+    if constexpr (W == 1) {
+        x[0] = __ldg(p);
+    } else {
+#pragma unroll
+        for (int i = 0; i < W; i += 2) {
+            const ulonglong2 t = __ldg(reinterpret_cast<const ulonglong2 *>(p) + i / 2);
+            x[i] = t.x;
+            x[i + 1] = t.y;
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned long long warp_or64(unsigned long long x) {
+    const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)x);
+    const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(x >> 32));
+    return ((unsigned long long)hi << 32) | lo;
+}
+
+// Sums NV counters over the block and adds them to dst[0..NV) with one
+// atomic each.
+template <int NV>
+__device__ __forceinline__ void block_add(int64_t (&v)[NV], unsigned long long *dst) {
+    __shared__ long long red[NV][kMsBlock / 32];
+    const unsigned lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        const int64_t s = warp_sum(v[i]);
+        if (lane == 0) red[i][w] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        long long s = 0;
+        for (int j = 0; j < (int)(blockDim.x >> 5); ++j) s += red[threadIdx.x][j];
+        if (s) atomicAdd(dst + threadIdx.x, (unsigned long long)s);
+    }
+}
+
+// levels = -1 (16-byte stores when aligned), seen = cur = 0.
+__global__ void ms_fill_kernel(int8_t *__restrict__ levels, int64_t total, int aligned,
+                               unsigned long long *__restrict__ seen,
+                               unsigned long long *__restrict__ cur, int64_t nwords) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (aligned) {
+        const int64_t nv = total / 16;
+        int4 *l4 = reinterpret_cast<int4 *>(levels);
+        for (int64_t i = t0; i < nv; i += stride) l4[i] = make_int4(-1, -1, -1, -1);
+        for (int64_t i = nv * 16 + t0; i < total; i += stride) levels[i] = -1;
+    } else {
+        for (int64_t i = t0; i < total; i += stride) levels[i] = -1;
+    }
+    for (int64_t i = t0; i < nwords; i += stride) {
+        seen[i] = 0ull;
+        cur[i] = 0ull;
+    }
+}
+
+// Roots: lane l sets bit l of its root's seen and cur words and level 0.
+// Slot 0 of the trace gets the first frontier's counters (distinct root
+// vertices, their degrees, pairs = k, roots that are already complete).
+template <int W>
+__global__ void __launch_bounds__(kMaxRoots) ms_roots_kernel(
+    const int32_t *__restrict__ roots, int k, int64_t n, const int64_t *__restrict__ off,
+    Lanes<W> act, unsigned long long *__restrict__ seen, unsigned long long *__restrict__ cur,
+    int8_t *__restrict__ levels, int64_t *__restrict__ trace) {
+    __shared__ long long red[5][kMaxRoots / 32];
+    const int l = threadIdx.x;
+    if (l < k) {
+        const int64_t v = roots[l];
+        atomicOr(seen + v * W + (l >> 6), 1ull << (l & 63));
+        atomicOr(cur + v * W + (l >> 6), 1ull << (l & 63));
+        levels[(int64_t)l * n + v] = 0;
+    }
+    __syncthreads();
+    int64_t c[5] = {0, 0, 0, 0, 0};
+    if (l < k) {
+        const int32_t v = roots[l];
+        bool first = true;
+        for (int j = 0; j < l; ++j) first = first && roots[j] != v;
+        if (first) {
+            const int64_t d = off[v + 1] - off[v];
+            c[0] = 1;
+            c[1] = d;
+            bool full = true;
+#pragma unroll
+            for (int i = 0; i < W; ++i) full = full && seen[(int64_t)v * W + i] == act.w[i];
+            if (full) {
+                c[3] = 1;
+                c[4] = d;
+            }
+        }
+    }
+    const unsigned lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const int64_t s = warp_sum(c[i]);
+        if (lane == 0) red[i][w] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        long long s = 0;
+        for (int j = 0; j < (int)(blockDim.x >> 5); ++j) s += red[threadIdx.x][j];
+        trace[threadIdx.x] = threadIdx.x == M_PAIRS ? k : s;
+    }
+}
+
+// Writes the newly reached bits `nw` of vertex v: seen, level rows, counters.
+template <int W>
+__device__ __forceinline__ void ms_commit(int64_t v, int64_t n, int64_t deg,
+                                          const unsigned long long (&s)[W],
+                                          const unsigned long long (&nw)[W], const Lanes<W> &act,
+                                          unsigned long long *__restrict__ seen,
+                                          int8_t *__restrict__ levels, int8_t new_level,
+                                          int64_t (&c)[6]) {
+    bool any = false, full = true;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        any = any || nw[i] != 0ull;
+        full = full && (s[i] | nw[i]) == act.w[i];
+    }
+    if (!any) return;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        if (!nw[i]) continue;
+        seen[v * W + i] = s[i] | nw[i];
+        unsigned long long x = nw[i];
+        c[2] += __popcll(x);
+        while (x) {
+            const int b = __ffsll((long long)x) - 1;
+            x &= x - 1;
+            levels[(int64_t)(i * 64 + b) * n + v] = new_level;
+        }
+    }
+    c[0] += 1;
+    c[1] += deg;
+    if (full) {
+        c[3] += 1;
+        c[4] += deg;
+    }
+}
+
+// Bottom-up layer on bit lanes. Warp per 32 consecutive vertices, lane per
+// vertex. need = roots this vertex still lacks; acc = OR of the neighbours'
+// frontier words restricted to need, in CSR order, stopping once acc = need.
+template <int W>
+__global__ void __launch_bounds__(kMsBlock) ms_bu_kernel(
+    const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
+    const uint32_t *__restrict__ base_vis, int64_t n, Lanes<W> act,
+    unsigned long long *__restrict__ seen, const unsigned long long *__restrict__ cur,
+    unsigned long long *__restrict__ nxt, int8_t *__restrict__ levels, int8_t new_level,
+    int probe, unsigned long long *slot_next, int64_t *zero_slot) {
+    if (blockIdx.x == 0 && threadIdx.x < 8) zero_slot[threadIdx.x] = 0;
+    const unsigned lane = lane_id();
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nwords = (n + 31) / 32;
+    int64_t c[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t w = gw; w < nwords; w += tw) {
+        const int64_t v = w * 32 + lane;
+        const bool inb = v < n;
+        const uint32_t bw = base_vis[w];
+        const bool skip = !inb || ((bw >> lane) & 1u);  // degree 0 or past n
+        unsigned long long s[W], need[W], acc[W];
+        bool anyneed = false;
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            s[i] = skip ? 0ull : seen[v * W + i];
+            need[i] = skip ? 0ull : (act.w[i] & ~s[i]);
+            acc[i] = 0ull;
+            anyneed = anyneed || need[i] != 0ull;
+        }
+        int64_t beg = 0, end = 0;
+        bool done = !anyneed;
+        int64_t ex = 0;
+        if (!done) {
+            beg = off[v];
+            end = off[v + 1];
+            const int64_t lim = min(end - beg, (int64_t)probe);
+            for (int64_t q = 0; q < lim; ++q) {
+                const int64_t u = __ldg(idx + beg + q);
+                unsigned long long x[W];
+                load_lanes<W>(cur + u * W, x);
+                ++ex;
+                bool comp = true;
+#pragma unroll
+                for (int i = 0; i < W; ++i) {
+                    acc[i] |= x[i] & need[i];
+                    comp = comp && acc[i] == need[i];
+                }
+                if (comp) {
+                    done = true;
+                    break;
+                }
+            }
+        }
+        unsigned pend = __ballot_sync(0xffffffffu, !done && end - beg > probe);
+        while (pend) {
+            const int L = __ffs(pend) - 1;
+            pend &= pend - 1;
+            const int64_t lb = __shfl_sync(0xffffffffu, beg + probe, L);
+            const int64_t le = __shfl_sync(0xffffffffu, end, L);
+            unsigned long long nL[W], aL[W];
+#pragma unroll
+            for (int i = 0; i < W; ++i) {
+                nL[i] = __shfl_sync(0xffffffffu, need[i], L);
+                aL[i] = __shfl_sync(0xffffffffu, acc[i], L);
+            }
+            int64_t exL = 0;
+            for (int64_t e0 = lb; e0 < le; e0 += 32) {
+                const int64_t e = e0 + lane;
+                unsigned long long x[W];
+                if (e < le) {
+                    const int64_t u = __ldg(idx + e);
+                    load_lanes<W>(cur + u * W, x);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < W; ++i) x[i] = 0ull;
+                }
+                bool comp = true;
+#pragma unroll
+                for (int i = 0; i < W; ++i) {
+                    aL[i] |= warp_or64(x[i] & nL[i]);
+                    comp = comp && aL[i] == nL[i];
+                }
+                exL += min((int64_t)32, le - e0);
+                if (comp) break;
+            }
+            if ((int)lane == L) {
+#pragma unroll
+                for (int i = 0; i < W; ++i) acc[i] = aL[i];
+                ex += exL;
+            }
+        }
+        if (inb) {
+#pragma unroll
+            for (int i = 0; i < W; ++i) nxt[v * W + i] = acc[i];
+            ms_commit<W>(v, n, end - beg, s, acc, act, seen, levels, new_level, c);
+        }
+        c[5] += ex;
+    }
+    block_add<6>(c, slot_next);
+}
+
+// Vertices holding a frontier bit -> list (block scan, one atomic per
+// block); those of degree >= big_deg -> the grid-spread list instead.
+template <int W>
+__global__ void __launch_bounds__(kMsBlock) ms_compact_kernel(
+    const unsigned long long *__restrict__ cur, int64_t n, const int64_t *__restrict__ off,
+    int64_t big_deg, int32_t *__restrict__ list, int32_t *__restrict__ big,
+    unsigned long long *slot_cur) {
+    __shared__ int wtot[kMsBlock / 32];
+    __shared__ unsigned long long base_s;
+    const unsigned lane = lane_id(), w = threadIdx.x >> 5;
+    constexpr int per = 4;
+    for (int64_t t0 = (int64_t)blockIdx.x * kMsBlock * per; t0 < n;
+         t0 += (int64_t)gridDim.x * kMsBlock * per) {
+        const int64_t v0 = t0 + (int64_t)threadIdx.x * per;
+        bool small[per];
+        int cnt = 0;
+#pragma unroll
+        for (int k = 0; k < per; ++k) {
+            const int64_t v = v0 + k;
+            bool active = false, isbig = false;
+            if (v < n) {
+#pragma unroll
+                for (int i = 0; i < W; ++i) active = active || cur[v * W + i] != 0ull;
+                if (active) isbig = off[v + 1] - off[v] >= big_deg;
+            }
+            small[k] = active && !isbig;
+            cnt += small[k];
+            const unsigned bm = __ballot_sync(0xffffffffu, isbig);
+            if (bm) {
+                const int leader = __ffs(bm) - 1;
+                unsigned long long b0 = 0;
+                if ((int)lane == leader) b0 = atomicAdd(slot_cur + M_BIG, (unsigned long long)__popc(bm));
+                b0 = __shfl_sync(0xffffffffu, b0, leader);
+                if (isbig) big[b0 + __popc(bm & lanemask_lt())] = (int32_t)v;
+            }
+        }
+        int tot;
+        const int excl = warp_exclusive_scan(cnt, &tot);
+        if (lane == 31) wtot[w] = tot;
+        __syncthreads();
+        int before = 0, all = 0;
+        for (int i = 0; i < kMsBlock / 32; ++i) {
+            if (i < (int)w) before += wtot[i];
+            all += wtot[i];
+        }
+        if (threadIdx.x == 0) base_s = all ? atomicAdd(slot_cur + M_LIST, (unsigned long long)all) : 0ull;
+        __syncthreads();
+        unsigned long long pos = base_s + before + excl;
+#pragma unroll
+        for (int k = 0; k < per; ++k)
+            if (small[k]) list[pos++] = (int32_t)(v0 + k);
+        __syncthreads();
+    }
+}
+
+// OR the frontier words `cu` of u into neighbour v's next words, only the
+// bits v has not seen.
+template <int W>
+__device__ __forceinline__ void ms_push(const unsigned long long (&cu)[W], int64_t v,
+                                        const unsigned long long *__restrict__ seen,
+                                        unsigned long long *__restrict__ nxt) {
+    unsigned long long sv[W];
+    load_lanes<W>(seen + v * W, sv);
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        const unsigned long long add = cu[i] & ~sv[i];
+        if (add) atomicOr(nxt + v * W + i, add);
+    }
+}
+
+// Top-down layer on bit lanes over the compacted list: a warp takes 32
+// entries; rows shorter than 32 are walked by their own lane, longer ones
+// by the whole warp.
+template <int W>
+__global__ void __launch_bounds__(kMsBlock) ms_td_kernel(
+    const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
+    const int32_t *__restrict__ list, const unsigned long long *slot_cur,
+    const unsigned long long *__restrict__ cur, const unsigned long long *__restrict__ seen,
+    unsigned long long *__restrict__ nxt) {
+    const int64_t cnt = (int64_t)slot_cur[M_LIST];
+    const unsigned lane = lane_id();
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = gw * 32; base < cnt; base += tw * 32) {
+        const int64_t i = base + lane;
+        int64_t u = 0, beg = 0, end = 0;
+        unsigned long long cu[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) cu[j] = 0ull;
+        if (i < cnt) {
+            u = list[i];
+            beg = off[u];
+            end = off[u + 1];
+            load_lanes<W>(cur + u * W, cu);
+        }
+        const bool wide = end - beg >= 32;
+        if (!wide)
+            for (int64_t e = beg; e < end; ++e) ms_push<W>(cu, __ldg(idx + e), seen, nxt);
+        unsigned wm = __ballot_sync(0xffffffffu, wide);
+        while (wm) {
+            const int L = __ffs(wm) - 1;
+            wm &= wm - 1;
+            const int64_t lb = __shfl_sync(0xffffffffu, beg, L);
+            const int64_t le = __shfl_sync(0xffffffffu, end, L);
+            unsigned long long cL[W];
+#pragma unroll
+            for (int j = 0; j < W; ++j) cL[j] = __shfl_sync(0xffffffffu, cu[j], L);
+            for (int64_t e = lb + lane; e < le; e += 32) ms_push<W>(cL, __ldg(idx + e), seen, nxt);
+        }
+    }
+}
+
+// The grid-spread list: batches of kMsBigBatch vertices, degree prefix in
+// shared memory, grid-stride over the batch's edges.
+template <int W>
+__global__ void __launch_bounds__(kMsBlock) ms_td_big_kernel(
+    const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
+    const int32_t *__restrict__ big, const unsigned long long *slot_cur,
+    const unsigned long long *__restrict__ cur, const unsigned long long *__restrict__ seen,
+    unsigned long long *__restrict__ nxt) {
+    __shared__ long long pre[kMsBigBatch + 1];
+    __shared__ long long beg_s[kMsBigBatch];
+    __shared__ int32_t u_s[kMsBigBatch];
+    __shared__ long long wtot[kMsBlock / 32];
+    const int64_t cnt = (int64_t)slot_cur[M_BIG];
+    const unsigned lane = lane_id(), w = threadIdx.x >> 5;
+    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t tt = (int64_t)gridDim.x * blockDim.x;
+    constexpr int per = kMsBigBatch / kMsBlock;
+    for (int64_t b0 = 0; b0 < cnt; b0 += kMsBigBatch) {
+        const int nb = (int)(cnt - b0 < kMsBigBatch ? cnt - b0 : kMsBigBatch);
+        long long dsum = 0, dloc[per];
+#pragma unroll
+        for (int k = 0; k < per; ++k) {
+            const int t = threadIdx.x * per + k;
+            long long d = 0;
+            if (t < nb) {
+                const int32_t u = big[b0 + t];
+                u_s[t] = u;
+                beg_s[t] = off[u];
+                d = off[u + 1] - beg_s[t];
+            }
+            dloc[k] = d;
+            dsum += d;
+        }
+        long long x = dsum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if ((int)lane >= o) x += y;
+        }
+        if (lane == 31) wtot[w] = x;
+        __syncthreads();
+        long long run = x - dsum;
+        for (unsigned i = 0; i < w; ++i) run += wtot[i];
+#pragma unroll
+        for (int k = 0; k < per; ++k) {
+            pre[threadIdx.x * per + k] = run;
+            run += dloc[k];
+        }
+        if (threadIdx.x == kMsBlock - 1) pre[kMsBigBatch] = run;
+        __syncthreads();
+        const long long total = pre[kMsBigBatch];
+        for (long long g = gt; g < total; g += tt) {
+            int lo = 0, hi = nb;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (pre[mid] <= g) lo = mid;
+                else hi = mid;
+            }
+            unsigned long long cu[W];
+            load_lanes<W>(cur + (int64_t)u_s[lo] * W, cu);
+            ms_push<W>(cu, __ldg(idx + beg_s[lo] + (g - pre[lo])), seen, nxt);
+        }
+        __syncthreads();
+    }
+}
+
+// After a top-down layer: keep the bits of nxt not yet seen (they become the
+// next frontier), update seen and the level rows, count.
+template <int W>
+__global__ void __launch_bounds__(kMsBlock) ms_finalize_kernel(
+    const int64_t *__restrict__ off, int64_t n, Lanes<W> act,
+    unsigned long long *__restrict__ seen, unsigned long long *__restrict__ nxt,
+    int8_t *__restrict__ levels, int8_t new_level, int64_t td_edges,
+    unsigned long long *slot_next, int64_t *zero_slot) {
+    if (blockIdx.x == 0 && threadIdx.x < 8) zero_slot[threadIdx.x] = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t c[6] = {0, 0, 0, 0, 0, 0};
+    if (blockIdx.x == 0 && threadIdx.x == 0) c[5] = td_edges;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += stride) {
+        unsigned long long x[W], s[W], nw[W];
+        bool any = false;
+        load_lanes<W>(nxt + v * W, x);
+        if constexpr (W == 1) {
+            any = x[0] != 0ull;
+        } else {
+#pragma unroll
+            for (int i = 0; i < W; ++i) any = any || x[i] != 0ull;
+        }
+        if (!any) continue;
+        load_lanes<W>(seen + v * W, s);
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            nw[i] = x[i] & ~s[i] & act.w[i];
+            nxt[v * W + i] = nw[i];
+        }
+        ms_commit<W>(v, n, off[v + 1] - off[v], s, nw, act, seen, levels, new_level, c);
+    }
+    block_add<6>(c, slot_next);
+}
+
+}  // namespace
+}  // namespace gbfs
+
+namespace gbfs {
+namespace {
+
+constexpr int kMsRing = 64;
+constexpr int kMsFields = 8;
+
+bool batch_cfg_ok(const bfs_batch_config &c) {
+    return c.alpha > 0 && c.beta > 0 && c.lane_probe >= 0 && c.lane_probe <= 4096 &&
+           c.big_degree >= 32 && (c.use_graph == 0 || c.use_graph == 1);
+}
+
+bfs_status ensure_ms(bfs_graph *g, int W) {
+    if (!g->ms) {
+        g->ms = new MsState();
+        bfs_batch_config_default(&g->ms->cfg);
+        g->ms->n = g->n;
+    }
+    MsState *m = g->ms;
+    if (!m->list) {
+        GB_CK(cudaMalloc(&m->list, (size_t)g->n * 4));
+        GB_CK(cudaMalloc(&m->big, (size_t)g->n * 4));
+        GB_CK(cudaMalloc(&m->roots, kMaxRoots * 4));
+        GB_CK(cudaMalloc(&m->trace, (size_t)kMsRing * kMsFields * 8));
+        GB_CK(cudaMallocHost(&m->h_slot, kMsFields * 8));
+    }
+    if (m->W < W) {
+        cudaFree(m->seen);
+        cudaFree(m->cur);
+        cudaFree(m->nxt);
+        m->seen = m->cur = m->nxt = nullptr;
+        m->W = 0;
+        const size_t bytes = (size_t)g->n * W * 8;
+        GB_CK(cudaMalloc(&m->seen, bytes));
+        GB_CK(cudaMalloc(&m->cur, bytes));
+        GB_CK(cudaMalloc(&m->nxt, bytes));
+        m->W = W;
+    }
+    return BFS_OK;
+}
+
+template <int W>
+Lanes<W> active_lanes(int k) {
+    Lanes<W> a;
+    for (int i = 0; i < W; ++i) {
+        const int bits = std::max(0, std::min(64, k - 64 * i));
+        a.w[i] = bits == 64 ? ~0ull : ((1ull << bits) - 1ull);
+    }
+    return a;
+}
+
+template <int W>
+bfs_status run_batch_w(bfs_graph *g, const int32_t *roots, int k, int8_t *levels, cudaStream_t st) {
+    MsState *m = g->ms;
+    const bfs_batch_config &cfg = m->cfg;
+    const int64_t n = g->n;
+    const Lanes<W> act = active_lanes<W>(k);
+    unsigned long long *cur = m->cur, *nxt = m->nxt, *seen = m->seen;
+    const bool timing = cfg.timing != 0;
+    auto event = [&](size_t i) -> cudaEvent_t {
+        while (m->events.size() <= i) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            m->events.push_back(e);
+        }
+        return m->events[i];
+    };
+    int bu_occ = 1, td_occ = 1;
+    GB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu_occ, ms_bu_kernel<W>, kMsBlock, 0));
+    GB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&td_occ, ms_td_kernel<W>, kMsBlock, 0));
+    const int64_t total = (int64_t)k * n;
+    const int aligned = ((uintptr_t)levels % 16) == 0;
+    GB_LAUNCH(ms_fill_kernel, grid_cap(std::max<int64_t>(total / 16, n * W), kMsBlock, 8),
+              kMsBlock, 0, st, levels, total, aligned, seen, cur, n * W);
+    GB_CK(cudaMemsetAsync(m->trace, 0, (size_t)kMsRing * kMsFields * 8, st));
+    GB_LAUNCH(ms_roots_kernel<W>, 1, kMaxRoots, 0, st, roots, k, n, g->off, act, seen, cur,
+              levels, m->trace);
+    GB_CK(cudaMemcpyAsync(m->h_slot, m->trace, kMsFields * 8, cudaMemcpyDeviceToHost, st));
+    GB_CK(cudaStreamSynchronize(st));
+    int64_t v_f = m->h_slot[M_NV], e_f = m->h_slot[M_MF], pairs = k;
+    int64_t v_u = n - m->h_slot[M_FULLN], e_u = g->nnz - m->h_slot[M_FULLDEG];
+    m->last.clear();
+    m->last_pairs = k;
+    int cur_bu = 0;
+    const int64_t nwords = (n + 31) / 32;
+    const int bu_grid = grid_cap(nwords, kMsBlock / 32, bu_occ);
+    for (int d = 0; v_f > 0; ++d) {
+        if (d + 1 > 127) {
+            set_error("bfs_run_batch: a level above 127 does not fit in int8");
+            return BFS_ERR_DEPTH;
+        }
+        if (!cur_bu) cur_bu = ((double)e_f > (double)e_u / cfg.alpha) ? 1 : 0;
+        else cur_bu = ((double)v_f < (double)n / cfg.beta) ? 0 : 1;
+        bfs_batch_layer_stats ls;
+        memset(&ls, 0, sizeof ls);
+        ls.direction = cur_bu;
+        ls.v_f = v_f;
+        ls.e_f = e_f;
+        ls.pairs = pairs;
+        ls.v_u = v_u;
+        ls.e_u = e_u;
+        int64_t *slot_cur = m->trace + (d % kMsRing) * kMsFields;
+        int64_t *slot_next = m->trace + ((d + 1) % kMsRing) * kMsFields;
+        int64_t *slot_zero = m->trace + ((d + 2) % kMsRing) * kMsFields;
+        if (timing) GB_CK(cudaEventRecord(event(2 * d), st));
+        const int8_t nl = (int8_t)(d + 1);
+        if (cur_bu) {
+            GB_LAUNCH(ms_bu_kernel<W>, bu_grid, kMsBlock, 0, st, g->off, g->idx, g->base_vis, n,
+                      act, seen, cur, nxt, levels, nl, cfg.lane_probe,
+                      (unsigned long long *)slot_next, slot_zero);
+        } else {
+            GB_LAUNCH(ms_compact_kernel<W>, grid_cap(n, kMsBlock * 4, 8), kMsBlock, 0, st, cur, n,
+                      g->off, (int64_t)cfg.big_degree, m->list, m->big,
+                      (unsigned long long *)slot_cur);
+            GB_CK(cudaMemsetAsync(nxt, 0, (size_t)n * W * 8, st));
+            GB_LAUNCH(ms_td_kernel<W>, grid_cap(v_f, kMsBlock, td_occ), kMsBlock, 0, st, g->off,
+                      g->idx, m->list, (const unsigned long long *)slot_cur, cur, seen, nxt);
+            if (e_f >= cfg.big_degree)
+                GB_LAUNCH(ms_td_big_kernel<W>,
+                          (int)std::max<int64_t>(1, std::min<int64_t>(e_f / 2048 + 1,
+                                                                      (int64_t)sm_count() * 4)),
+                          kMsBlock, 0, st, g->off, g->idx, m->big,
+                          (const unsigned long long *)slot_cur, cur, seen, nxt);
+            GB_LAUNCH(ms_finalize_kernel<W>, grid_cap(n, kMsBlock, 8), kMsBlock, 0, st, g->off, n,
+                      act, seen, nxt, levels, nl, e_f, (unsigned long long *)slot_next,
+                      slot_zero);
+        }
+        if (timing) GB_CK(cudaEventRecord(event(2 * d + 1), st));
+        GB_CK(cudaMemcpyAsync(m->h_slot, slot_next, kMsFields * 8, cudaMemcpyDeviceToHost, st));
+        GB_CK(cudaStreamSynchronize(st));
+        m->last.push_back(ls);
+        v_f = m->h_slot[M_NV];
+        e_f = m->h_slot[M_MF];
+        pairs = m->h_slot[M_PAIRS];
+        m->last_pairs += pairs;
+        v_u -= m->h_slot[M_FULLN];
+        e_u -= m->h_slot[M_FULLDEG];
+        std::swap(cur, nxt);
+    }
+    if (timing)
+        for (size_t d = 0; d < m->last.size(); ++d)
+            cudaEventElapsedTime(&m->last[d].ms, m->events[2 * d], m->events[2 * d + 1]);
+    return BFS_OK;
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+}  // namespace gbfs
+
+using namespace gbfs;
+
+extern "C" BFS_API void bfs_batch_config_default(bfs_batch_config *c) {
+    if (!c) return;
+    memset(c, 0, sizeof *c);
+    c->alpha = 1.0;   // the autotuner's choice on R-MAT scale 22, k = 64..512
+    c->beta = 96.0;
+    c->lane_probe = 16;
+    c->big_degree = 4096;
+    c->use_graph = 0;
+    c->timing = 0;
+}
+
+extern "C" BFS_API bfs_status bfs_graph_set_batch_config(bfs_graph *g, const bfs_batch_config *cfg) {
+    clear_error();
+    if (!g) {
+        set_error("bfs_graph_set_batch_config: null graph");
+        return BFS_ERR_INVALID;
+    }
+    bfs_batch_config c;
+    if (cfg) c = *cfg;
+    else bfs_batch_config_default(&c);
+    if (!batch_cfg_ok(c)) {
+        set_error("bfs_graph_set_batch_config: invalid configuration");
+        return BFS_ERR_INVALID;
+    }
+    bfs_status s = ensure_ms(g, 0);
+    if (s != BFS_OK) return s;
+    g->ms->cfg = c;
+    return BFS_OK;
+}
+
+extern "C" BFS_API bfs_status bfs_graph_get_batch_config(const bfs_graph *g, bfs_batch_config *cfg) {
+    clear_error();
+    if (!g || !cfg) {
+        set_error("bfs_graph_get_batch_config: null argument");
+        return BFS_ERR_INVALID;
+    }
+    if (g->ms) *cfg = g->ms->cfg;
+    else bfs_batch_config_default(cfg);
+    return BFS_OK;
+}
+
+extern "C" BFS_API bfs_status bfs_run_batch(bfs_graph *g, const int32_t *roots, int32_t k,
+                                            int8_t *levels_out, void *stream) {
+    clear_error();
+    if (!g || !roots || !levels_out || k < 1 || k > kMaxRoots) {
+        set_error("bfs_run_batch: need a graph, roots, levels_out and 1 <= k <= %d", kMaxRoots);
+        return BFS_ERR_INVALID;
+    }
+    cudaStream_t st = as_stream(stream);
+    const int W = k <= 64 ? 1 : k <= 128 ? 2 : k <= 256 ? 4 : 8;
+    bfs_status s = ensure_ms(g, W);
+    if (s != BFS_OK) return s;
+    MsState *m = g->ms;
+    // roots are validated on the host (copied there first if they are device memory)
+    std::vector<int32_t> hr(k);
+    if (is_device_ptr(roots)) {
+        GB_CK(cudaMemcpyAsync(hr.data(), roots, (size_t)k * 4, cudaMemcpyDeviceToHost, st));
+        GB_CK(cudaStreamSynchronize(st));
+    } else {
+        memcpy(hr.data(), roots, (size_t)k * 4);
+    }
+    for (int i = 0; i < k; ++i)
+        if (hr[i] < 0 || hr[i] >= g->n) {
+            set_error("bfs_run_batch: root %d = %d is outside [0, n)", i, hr[i]);
+            return BFS_ERR_INVALID;
+        }
+    GB_CK(cudaMemcpyAsync(m->roots, hr.data(), (size_t)k * 4, cudaMemcpyHostToDevice, st));
+    switch (W) {
+        case 1: return run_batch_w<1>(g, m->roots, k, levels_out, st);
+        case 2: return run_batch_w<2>(g, m->roots, k, levels_out, st);
+        case 4: return run_batch_w<4>(g, m->roots, k, levels_out, st);
+        default: return run_batch_w<8>(g, m->roots, k, levels_out, st);
+    }
+}
+
+extern "C" BFS_API bfs_status bfs_last_batch_stats(const bfs_graph *g, bfs_batch_layer_stats *out,
+                                                   int32_t cap, int32_t *layers,
+                                                   int64_t *pairs_reached) {
+    clear_error();
+    if (!g || cap < 0 || (cap > 0 && !out)) {
+        set_error("bfs_last_batch_stats: null graph or output");
+        return BFS_ERR_INVALID;
+    }
+    const int32_t L = g->ms ? (int32_t)g->ms->last.size() : 0;
+    for (int32_t i = 0; i < std::min(cap, L); ++i) out[i] = g->ms->last[i];
+    if (layers) *layers = L;
+    if (pairs_reached) *pairs_reached = g->ms ? g->ms->last_pairs : 0;
+    return BFS_OK;
+}
+
+extern "C" BFS_API bfs_status bfs_batch_autotune(bfs_graph *g, const int32_t *roots, int32_t k,
+                                                 int8_t *levels_scratch, bfs_batch_config *best,
+                                                 void *stream) {
+    clear_error();
+    if (!g || !roots || !levels_scratch || k < 1 || k > kMaxRoots) {
+        set_error("bfs_batch_autotune: need a graph, roots, scratch and 1 <= k <= %d", kMaxRoots);
+        return BFS_ERR_INVALID;
+    }
+    bfs_status s = ensure_ms(g, 0);
+    if (s != BFS_OK) return s;
+    cudaStream_t st = as_stream(stream);
+    bfs_batch_config base = g->ms->cfg;
+    base.timing = 0;
+    cudaEvent_t e0, e1;
+    GB_CK(cudaEventCreate(&e0));
+    GB_CK(cudaEventCreate(&e1));
+    auto timed = [&](const bfs_batch_config &c, float *ms) -> bfs_status {
+        g->ms->cfg = c;
+        bfs_status r = bfs_run_batch(g, roots, k, levels_scratch, stream);  // warm
+        if (r != BFS_OK) return r;
+        float best_t = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+            GB_CK(cudaEventRecord(e0, st));
+            r = bfs_run_batch(g, roots, k, levels_scratch, stream);
+            if (r != BFS_OK) return r;
+            GB_CK(cudaEventRecord(e1, st));
+            GB_CK(cudaEventSynchronize(e1));
+            float t = 0;
+            GB_CK(cudaEventElapsedTime(&t, e0, e1));
+            best_t = std::min(best_t, t);
+        }
+        *ms = best_t;
+        return BFS_OK;
+    };
+    // Coordinate search: alpha, then beta, then the lane probe length.
+    bfs_batch_config cur = base;
+    float cur_t = 0;
+    if ((s = timed(cur, &cur_t)) != BFS_OK) goto done;
+    {
+        const double alphas[] = {1.0, 2.0, 4.0, 8.0, 14.0, 32.0, 128.0};
+        const double betas[] = {6.0, 24.0, 96.0, 1e9};
+        const int probes[] = {4, 16, 64, 256};
+        for (double a : alphas) {
+            bfs_batch_config c = cur;
+            c.alpha = a;
+            float t;
+            if ((s = timed(c, &t)) != BFS_OK) goto done;
+            if (t < cur_t) { cur = c; cur_t = t; }
+        }
+        for (double b : betas) {
+            bfs_batch_config c = cur;
+            c.beta = b;
+            float t;
+            if ((s = timed(c, &t)) != BFS_OK) goto done;
+            if (t < cur_t) { cur = c; cur_t = t; }
+        }
+        for (int p : probes) {
+            bfs_batch_config c = cur;
+            c.lane_probe = p;
+            float t;
+            if ((s = timed(c, &t)) != BFS_OK) goto done;
+            if (t < cur_t) { cur = c; cur_t = t; }
+        }
+    }
+done:
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cur.timing = base.timing;
+    g->ms->cfg = (s == BFS_OK) ? cur : base;
+    if (s == BFS_OK && best) *best = cur;
+    return s;
+}
