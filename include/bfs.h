@@ -278,6 +278,61 @@ BFS_API bfs_status bfs_batch_autotune(bfs_graph *g, const int32_t *roots, int32_
                                       void *stream);
 
 /* ---------------------------------------------------------------------- */
+/* Serving: a request loop over resident graphs. Not in the paper (which   */
+/* times one root at a time, Sec. 6.3): single-root queries are batched by  */
+/* graph into bfs_run_batch launches. Worker threads, each with its own     */
+/* CUDA stream, take whatever is queued whenever they are free, so queries */
+/* that arrive while others run are admitted as soon as a worker and memory */
+/* are free, and batches on different streams overlap on the GPU.          */
+/* ---------------------------------------------------------------------- */
+typedef struct bfs_server bfs_server;
+
+typedef struct bfs_serve_config {
+    int32_t workers;          /* worker threads = concurrent batches (1..16)   */
+    int32_t max_batch;        /* roots per launch (1..512)                     */
+    int64_t memory_budget;    /* device bytes the server may hold for batch
+                                 outputs and per-worker traversal state; a
+                                 batch that does not fit is halved or waits   */
+    int32_t queue_capacity;   /* queued requests beyond this: BFS_ERR_BUSY     */
+    int32_t cancel_on_destroy;/* 1 = queued requests end with BFS_ERR_SHUTDOWN
+                                 at destroy; 0 = destroy drains them first     */
+    int32_t reserved[8];
+} bfs_serve_config;
+
+typedef struct bfs_serve_stats {
+    int64_t completed;        /* requests finished (any status)                */
+    int64_t failed;           /* finished with a status other than BFS_OK      */
+    int64_t batches;          /* bfs_run_batch launches                        */
+    int64_t deferred;         /* times a batch waited for memory or was split */
+    double mean_batch;        /* mean roots per launch                         */
+    double p50_us, p99_us;    /* submit-to-completion latency percentiles      */
+    double qps;               /* completed / (last completion - first submit)  */
+} bfs_serve_stats;
+
+BFS_API void bfs_serve_config_default(bfs_serve_config *cfg);
+/* Starts the workers on the current CUDA device. cfg may be NULL. */
+BFS_API bfs_status bfs_serve_create(const bfs_serve_config *cfg, bfs_server **out);
+/* Registers a resident graph (it must outlive the server); *graph_id names
+ * it in bfs_serve_submit. Must be called before the first submit. */
+BFS_API bfs_status bfs_serve_add_graph(bfs_server *s, bfs_graph *g, int32_t *graph_id);
+/* Queues a BFS from `root` of graph `graph_id`. level_out: n int32, host or
+ * device memory, caller-owned, written when the request completes. *ticket
+ * identifies the request for bfs_serve_wait. BFS_ERR_BUSY when the queue is
+ * full, BFS_ERR_SHUTDOWN after destroy began, BFS_ERR_INVALID for a bad id
+ * or root. */
+BFS_API bfs_status bfs_serve_submit(bfs_server *s, int32_t graph_id, int32_t root,
+                                    int32_t *level_out, uint64_t *ticket);
+/* Waits up to timeout_us (< 0: forever) for a ticket. Returns BFS_OK and the
+ * request's own status in *result, or BFS_ERR_TIMEOUT (the ticket stays
+ * valid), or BFS_ERR_INVALID for an unknown or already collected ticket. */
+BFS_API bfs_status bfs_serve_wait(bfs_server *s, uint64_t ticket, int64_t timeout_us,
+                                  bfs_status *result);
+BFS_API bfs_status bfs_serve_stats_get(bfs_server *s, bfs_serve_stats *out);
+/* Stops accepting requests, drains or cancels the queue (cfg), finishes the
+ * batches in flight, joins the workers and frees the server. NULL is fine. */
+BFS_API bfs_status bfs_serve_destroy(bfs_server *s);
+
+/* ---------------------------------------------------------------------- */
 /* Allocation-free traversal. The paper has no counterpart: this entry     */
 /* point exists for callers that must not allocate device memory.         */
 /* ---------------------------------------------------------------------- */

@@ -66,6 +66,19 @@ class BatchLayerStats(ctypes.Structure):
                 ("pad2", ctypes.c_float)]
 
 
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("workers", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("memory_budget", ctypes.c_int64), ("queue_capacity", ctypes.c_int32),
+                ("cancel_on_destroy", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("deferred", ctypes.c_int64),
+                ("mean_batch", ctypes.c_double), ("p50_us", ctypes.c_double),
+                ("p99_us", ctypes.c_double), ("qps", ctypes.c_double)]
+
+
 _lib = None
 P = ctypes.c_void_p
 I32, I64, U32, U64, DBL = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
@@ -91,6 +104,13 @@ SIGNATURES = {
     "bfs_run_batch": (I32, [P, P, I32, P, P]),
     "bfs_last_batch_stats": (I32, [P, P, I32, P, P]),
     "bfs_batch_autotune": (I32, [P, P, I32, P, P, P]),
+    "bfs_serve_config_default": (None, [P]),
+    "bfs_serve_create": (I32, [P, P]),
+    "bfs_serve_add_graph": (I32, [P, P, P]),
+    "bfs_serve_submit": (I32, [P, I32, I32, P, P]),
+    "bfs_serve_wait": (I32, [P, U64, I64, P]),
+    "bfs_serve_stats_get": (I32, [P, P]),
+    "bfs_serve_destroy": (I32, [P]),
 }
 
 
@@ -305,3 +325,53 @@ def run_noalloc(offsets: torch.Tensor, indices: torch.Tensor, root: int, level: 
                                  indices.numel(), int(root), _ptr(level), _ptr(parent),
                                  _stream(stream)))
     return level, parent
+
+
+def default_serve_config() -> ServeConfig:
+    c = ServeConfig()
+    lib().bfs_serve_config_default(ctypes.byref(c))
+    return c
+
+
+class Server:
+    """bfs_server: batches single-root queries per graph (continuous batching)."""
+
+    def __init__(self, config: ServeConfig | None = None):
+        h = ctypes.c_void_p(0)
+        _check(lib().bfs_serve_create(ctypes.byref(config) if config else None, ctypes.byref(h)))
+        self._h = h
+        self._graphs = []
+
+    def add_graph(self, graph: Graph) -> int:
+        gid = ctypes.c_int32(0)
+        _check(lib().bfs_serve_add_graph(self._h, graph._h, ctypes.byref(gid)))
+        self._graphs.append(graph)
+        return gid.value
+
+    def submit(self, graph_id: int, root: int, level_out: torch.Tensor) -> int:
+        t = ctypes.c_uint64(0)
+        _check(lib().bfs_serve_submit(self._h, graph_id, int(root), _ptr(level_out),
+                                      ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int, timeout_us: int = -1) -> int:
+        """Returns the request's own status (0 = BFS_OK)."""
+        r = ctypes.c_int32(0)
+        _check(lib().bfs_serve_wait(self._h, ctypes.c_uint64(ticket), timeout_us, ctypes.byref(r)))
+        return r.value
+
+    def stats(self) -> dict:
+        o = ServeStats()
+        _check(lib().bfs_serve_stats_get(self._h, ctypes.byref(o)))
+        return {f: getattr(o, f) for f, _ in ServeStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().bfs_serve_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
