@@ -47,6 +47,14 @@ def parse():
     p.add_argument("--cpu-scale", type=int, default=20,
                    help="scale of the oracle's bounded sample graph")
     p.add_argument("--cpu-roots", type=int, default=8)
+    p.add_argument("--mode", default="single", choices=["single", "serve"],
+                   help="single: the headline line (single-source + batched); "
+                        "serve: the serving stream over 8 resident graphs")
+    p.add_argument("--no-batch", action="store_true", help="skip the batched comparison")
+    p.add_argument("--batch-scale", type=int, default=22)
+    p.add_argument("--serve-queries", type=int, default=10000)
+    p.add_argument("--serve-seconds", type=float, default=4.0,
+                   help="cap on each rate's arrival window")
     return p.parse_args()
 
 
@@ -57,6 +65,28 @@ def peaks():
             j = json.load(f)
         return float(j["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def measured_traffic(scale, edgefactor):
+    """DRAM bytes per bottom-up launch from the committed ncu summary, or None
+    when the workload differs or the kernel source changed since the capture
+    (the summary records the git blob of csrc/bfs.cu it was taken with)."""
+    import hashlib
+    path = os.path.join(HERE, "profiles", "bu_kernel_dram_rmat26.md")
+    if (scale, edgefactor) != (26, 16) or not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and line.split(":")[0] in ("traffic_bytes_per_launch",
+                                                      "kernel_source_blob"):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    src = open(os.path.join(HERE, "paper_1704_02259_gb300", "csrc", "bfs.cu"), "rb").read()
+    blob = hashlib.sha1(b"blob %d\x00" % len(src) + src).hexdigest()
+    if vals.get("kernel_source_blob") != blob or "traffic_bytes_per_launch" not in vals:
+        return None
+    return float(vals["traffic_bytes_per_launch"])
 
 
 class ClockSampler:
@@ -118,17 +148,28 @@ def hmean(x):
     return float(len(x) / np.sum(1.0 / x)) if len(x) and (x > 0).all() else 0.0
 
 
-def cpu_baseline(args, n_steps=None):
-    """The oracle (plain single-threaded C FIFO BFS) on a bounded sample of the
-    workload: the same R-MAT recipe at --cpu-scale, built by the oracle itself,
-    --cpu-roots roots from the same root seed. Returns per-root TEPS."""
+_CPU_GRAPH = {}
+
+
+def cpu_graph(args):
+    """The bounded sample's graph: the same R-MAT recipe at --cpu-scale, built
+    by the oracle itself (once per process)."""
     import oracle
-    scale = args.cpu_scale
-    n = 1 << scale
-    s, d = oracle.gen_edges(oracle.RMAT, scale, args.edgefactor, args.graph_seed)
-    off, idx = oracle.build_csr(n, s, d)
-    del s, d
-    roots = oracle.sample_roots(off, n, args.root_seed, args.cpu_roots)
+    key = (args.cpu_scale, args.edgefactor, args.graph_seed)
+    if key not in _CPU_GRAPH:
+        n = 1 << args.cpu_scale
+        s, d = oracle.gen_edges(oracle.RMAT, args.cpu_scale, args.edgefactor, args.graph_seed)
+        off, idx = oracle.build_csr(n, s, d)
+        roots = oracle.sample_roots(off, n, args.root_seed, args.cpu_roots)
+        _CPU_GRAPH[key] = (off, idx, roots)
+    return _CPU_GRAPH[key]
+
+
+def cpu_baseline(args):
+    """The oracle (plain single-threaded C FIFO BFS) on a bounded sample of the
+    workload: --cpu-roots roots on the same R-MAT recipe at --cpu-scale."""
+    import oracle
+    off, idx, roots = cpu_graph(args)
     teps, secs = [], 0.0
     for r in roots:
         t0 = time.perf_counter()
@@ -138,8 +179,8 @@ def cpu_baseline(args, n_steps=None):
         teps.append(oracle.component_edges(off, lv) / dt)
     return {"value": hmean(teps) / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
             "sample": f"oracle FIFO BFS, {len(roots)} roots on the same R-MAT recipe at scale "
-                      f"{scale} (edgefactor {args.edgefactor}), CSR built by the oracle; the "
-                      f"single-threaded oracle cannot build the scale-{args.scale} CSR in "
+                      f"{args.cpu_scale} (edgefactor {args.edgefactor}), CSR built by the oracle; "
+                      f"the single-threaded oracle cannot build the scale-{args.scale} CSR in "
                       f"the bench's time bound",
             "seconds": round(secs, 3)}
 
@@ -169,8 +210,116 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def batched_comparison(gb, torch, scale, seed=1, root_seed=4, ks=(64, 128, 256, 512)):
+    """Batched multi-source BFS against k sequential single-source runs on the
+    same GPU (R-MAT scale 22): aggregate TEPS = sum of the roots' component
+    edges / wall time on the stream (CUDA events)."""
+    n = 1 << scale
+    off, idx = gb.rmat_graph(scale, 16, seed)
+    g = gb.Graph(off, idx)
+    allroots = gb.sample_roots(off, n, root_seed, max(ks))
+    lv = torch.empty(n, dtype=torch.int32, device="cuda")
+    pa = torch.empty_like(lv)
+    st = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for r in allroots[:4].tolist():
+        g.run(r, lv, pa)
+    mc, seq_ms = {}, {}
+    for r in allroots.tolist():
+        ev[0].record(st)
+        g.run(r, lv, pa)
+        ev[1].record(st)
+        ev[1].synchronize()
+        seq_ms[r] = ev[0].elapsed_time(ev[1])
+        mc[r] = g.stats().component_edges
+    out = {"workload": f"rmat-scale{scale}-ef16", "per_k": []}
+    launches0 = gb.launch_count()
+    for k in ks:
+        roots = allroots[:k]
+        rl = roots.tolist()
+        edges = sum(mc[r] for r in rl)
+        t_seq = sum(seq_ms[r] for r in rl)
+        best = g.autotune_batch(roots)
+        levels = torch.empty((k, n), dtype=torch.int8, device="cuda")
+        g.run_batch(roots, levels)
+        ts = []
+        for _ in range(3):
+            ev[0].record(st)
+            g.run_batch(roots, levels)
+            ev[1].record(st)
+            ev[1].synchronize()
+            ts.append(ev[0].elapsed_time(ev[1]))
+        t = statistics.median(ts)
+        out["per_k"].append({
+            "k": k, "batch_ms": t, "sequential_ms": t_seq,
+            "batch_gteps": edges / t / 1e6, "sequential_gteps": edges / t_seq / 1e6,
+            "speedup": t_seq / t, "alpha": best.alpha, "beta": best.beta,
+            "lane_probe": best.lane_probe})
+    out["gpu_launches_batched"] = gb.launch_count() - launches0
+    g.close()
+    return out
+
+
+def run_serve(args):
+    """Serving: 8 resident R-MAT graphs (scales 14, 16, 18..23, edgefactor 16,
+    seeds 10..17), Poisson arrivals at each rate, graph uniform, root uniform
+    among degree >= 1 vertices; p50/p99 latency and queries/s per rate."""
+    import torch
+    import paper_1704_02259_gb300 as gb
+    torch.cuda.set_device(0)
+    scales = [14, 16, 18, 19, 20, 21, 22, 23]
+    graphs, roots, pools = [], [], []
+    csr_bytes = 0
+    for i, sc in enumerate(scales):
+        off, idx = gb.rmat_graph(sc, 16, 10 + i)
+        csr_bytes += off.numel() * 8 + idx.numel() * 4
+        g = gb.Graph(off, idx)
+        graphs.append(g)
+        roots.append(gb.sample_roots(off, 1 << sc, 5 + i, 4096).cpu().numpy())
+        pools.append([torch.empty(1 << sc, dtype=torch.int32, device="cuda") for _ in range(16)])
+    cfg = gb.default_serve_config()
+    cfg.workers = 4
+    cfg.max_batch = 512
+    rng = np.random.default_rng(5)
+    results = []
+    for rate in [100, 300, 1000, 3000, 10000, 20000]:
+        srv = gb.Server(cfg)
+        ids = [srv.add_graph(g) for g in graphs]
+        nq = int(min(args.serve_queries, rate * args.serve_seconds))
+        gsel = rng.integers(0, len(graphs), size=nq)
+        gaps = rng.exponential(1.0 / rate, size=nq)
+        tickets = []
+        t0 = time.perf_counter()
+        due = t0
+        for q in range(nq):
+            due += gaps[q]
+            while time.perf_counter() < due:
+                pass
+            gi = int(gsel[q])
+            r = int(roots[gi][rng.integers(0, len(roots[gi]))])
+            tickets.append(srv.submit(ids[gi], r, pools[gi][q % len(pools[gi])]))
+        bad = sum(1 for t in tickets if srv.wait(t) != 0)
+        st = srv.stats()
+        srv.close()
+        results.append({"rate_qps": rate, "queries": nq, "p50_ms": st["p50_us"] / 1e3,
+                        "p99_ms": st["p99_us"] / 1e3, "achieved_qps": st["qps"],
+                        "mean_batch": st["mean_batch"], "batches": st["batches"],
+                        "failed": bad})
+    line = {"metric": "serving latency p50/p99 and queries/s", "mode": "serve",
+            "value": max(r["achieved_qps"] for r in results), "unit": "queries/s",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "8 R-MAT graphs, scales 14,16,18-23, ef 16, Poisson stream",
+                       "csr_bytes": csr_bytes, "workers": cfg.workers,
+                       "max_batch": cfg.max_batch},
+            "rates": results}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.mode == "serve":
+        run_serve(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -310,7 +459,7 @@ def main():
                    "policy": "edge alpha=14 beta=24", "bu_probe": cfg.bu_probe},
         "roofline": {"bound": "hbm", "kernel": "bu_kernel", "achieved": achieved,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": measured_traffic(scale, ef),
                      "algorithmic_bytes_per_launch": bu_bytes / max(1, n_bu),
                      "avg_launch_ms": bu_ms / max(1, n_bu)},
         "sweep_roofline": {"bytes": b_sweep, "teps": roof_teps / 1e9, "unit": "GTEPS",
@@ -326,6 +475,8 @@ def main():
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if not args.no_batch and world == 1:
+        line["batched"] = batched_comparison(gb, torch, args.batch_scale)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(line), flush=True)
