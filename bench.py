@@ -143,6 +143,22 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def gather_ranks(dist, world, vals, device):
+    """All ranks' value vectors, as a [world, len(vals)] float64 array."""
+    import torch
+    t = torch.tensor(vals, dtype=torch.float64, device=device)
+    allv = [torch.zeros_like(t) for _ in range(world)]
+    dist.all_gather(allv, t)
+    return torch.stack(allv).cpu().numpy()
+
+
+def combine_ranks(rows):
+    """Whole-job figures from per-rank [hmean TEPS, timed seconds, wall]:
+    ranks run independent replicas, so rates add and times take the max."""
+    rows = np.asarray(rows, dtype=np.float64)
+    return float(rows[:, 0].sum()), float(rows[:, 1].max()), float(rows[:, 2].max())
+
+
 def hmean(x):
     x = np.asarray(x, dtype=np.float64)
     return float(len(x) / np.sum(1.0 / x)) if len(x) and (x > 0).all() else 0.0
@@ -406,13 +422,8 @@ def main():
     n_bu = sum(1 for _, _, st in recs for L in st.layers if L["direction"] == 1)
 
     if dist is not None:
-        t = torch.tensor([my_hmean, my_total_s, wall], dtype=torch.float64, device="cuda")
-        allv = [torch.zeros_like(t) for _ in range(world)]
-        dist.all_gather(allv, t)
-        vals = torch.stack(allv).cpu().numpy()
-        value = float(vals[:, 0].sum())
-        total_s = float(vals[:, 1].max())
-        wall = float(vals[:, 2].max())
+        value, total_s, wall = combine_ranks(
+            gather_ranks(dist, world, [my_hmean, my_total_s, wall], "cuda"))
     else:
         value, total_s = my_hmean, my_total_s
 
@@ -432,10 +443,7 @@ def main():
     barrier()
     e2e_val = hmean(e2e_teps)
     if dist is not None:
-        t = torch.tensor([e2e_val], dtype=torch.float64, device="cuda")
-        allv = [torch.zeros_like(t) for _ in range(world)]
-        dist.all_gather(allv, t)
-        e2e_val = float(sum(x.item() for x in allv))
+        e2e_val = float(gather_ranks(dist, world, [e2e_val], "cuda")[:, 0].sum())
 
     if rank != 0:
         if dist is not None:
