@@ -269,8 +269,19 @@ typedef struct bfs_batch_layer_stats {
 BFS_API bfs_status bfs_last_batch_stats(const bfs_graph *g, bfs_batch_layer_stats *out,
                                         int32_t cap, int32_t *layers, int64_t *pairs_reached);
 
+/* Self-test of the grid barrier that the device-side layer loop
+ * (bfs_batch_config.use_graph) synchronises with: one cooperative launch
+ * waits for `missing_blocks` more blocks than it has. With 0 the barrier
+ * completes (BFS_OK); with more, every block gives up after timeout_us
+ * (1 ms .. 10 s) and the call returns BFS_ERR_TIMEOUT with the CUDA context
+ * still usable. Failure detection on the GPU is tested this way: by a wait
+ * that runs out, never by a fault. */
+BFS_API bfs_status bfs_selftest_grid_barrier(int32_t missing_blocks, int64_t timeout_us,
+                                             void *stream);
+
 /* Autotuner: runs the batch from `roots` under a small grid of switch
- * thresholds (alpha, beta) and lane-probe lengths, keeps the fastest in the
+ * thresholds (alpha, beta), lane-probe lengths and both drivers (host loop,
+ * device loop), keeps the fastest in the
  * graph's batch configuration and copies it to *best (may be NULL).
  * levels_scratch is a device k*n int8 buffer it may overwrite. */
 BFS_API bfs_status bfs_batch_autotune(bfs_graph *g, const int32_t *roots, int32_t k,

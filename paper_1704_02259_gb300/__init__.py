@@ -104,6 +104,7 @@ SIGNATURES = {
     "bfs_run_batch": (I32, [P, P, I32, P, P]),
     "bfs_last_batch_stats": (I32, [P, P, I32, P, P]),
     "bfs_batch_autotune": (I32, [P, P, I32, P, P, P]),
+    "bfs_selftest_grid_barrier": (I32, [I32, I64, P]),
     "bfs_serve_config_default": (None, [P]),
     "bfs_serve_create": (I32, [P, P]),
     "bfs_serve_add_graph": (I32, [P, P, P]),
@@ -375,3 +376,8 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def selftest_grid_barrier(missing_blocks: int, timeout_us: int, stream=None) -> int:
+    """Status of one bounded grid barrier that lacks `missing_blocks` arrivals."""
+    return int(lib().bfs_selftest_grid_barrier(missing_blocks, timeout_us, _stream(stream)))

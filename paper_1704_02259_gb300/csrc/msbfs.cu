@@ -35,6 +35,15 @@ struct MsState {
     std::vector<bfs_batch_layer_stats> last;
     int64_t last_pairs = 0;
     std::vector<cudaEvent_t> events;
+    // device-loop variant: control block (layer records, result, barrier)
+    // and the captured graph with the arguments it was captured for
+    int64_t *pctl = nullptr, *h_pctl = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr;  // private stream the graph is captured on
+    int g_W = 0, g_k = -1;
+    const void *g_levels = nullptr, *g_seen = nullptr;
+    bfs_batch_config g_cfg;
 };
 
 namespace gbfs {
@@ -49,7 +58,12 @@ void free_ms_state(bfs_graph *g) {
     cudaFree(m->big);
     cudaFree(m->roots);
     cudaFree(m->trace);
+    cudaFree(m->pctl);
     if (m->h_slot) cudaFreeHost(m->h_slot);
+    if (m->h_pctl) cudaFreeHost(m->h_pctl);
+    if (m->exec) cudaGraphExecDestroy(m->exec);
+    if (m->graph) cudaGraphDestroy(m->graph);
+    if (m->cap) cudaStreamDestroy(m->cap);
     for (cudaEvent_t e : m->events) cudaEventDestroy(e);
     delete m;
     g->ms = nullptr;
@@ -69,15 +83,26 @@ struct Lanes {
     unsigned long long w[W];
 };
 
-template <int W>
+// Loads of data that changes during a traversal. CO (coherent) is set inside
+// the persistent kernel, where other blocks wrote the data earlier in the
+// same launch: those loads go to L2 (ld.global.cg) instead of the
+// non-coherent read-only path.
+template <bool CO, typename T>
+__device__ __forceinline__ T ld(const T *p) {
+    if constexpr (CO) return __ldcg(p);
+    else return *p;
+}
+
+template <int W, bool CO>
 __device__ __forceinline__ void load_lanes(const unsigned long long *p,
                                            unsigned long long (&x)[W]) {
     if constexpr (W == 1) {
-        x[0] = __ldg(p);
+        x[0] = CO ? __ldcg(p) : __ldg(p);
     } else {
 #pragma unroll
         for (int i = 0; i < W; i += 2) {
-            const ulonglong2 t = __ldg(reinterpret_cast<const ulonglong2 *>(p) + i / 2);
+            const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(p) + i / 2;
+            const ulonglong2 t = CO ? __ldcg(q) : __ldg(q);
             x[i] = t.x;
             x[i + 1] = t.y;
         }
@@ -216,8 +241,8 @@ __device__ __forceinline__ void ms_commit(int64_t v, int64_t n, int64_t deg,
 // Bottom-up layer on bit lanes. Warp per 32 consecutive vertices, lane per
 // vertex. need = roots this vertex still lacks; acc = OR of the neighbours'
 // frontier words restricted to need, in CSR order, stopping once acc = need.
-template <int W>
-__global__ void __launch_bounds__(kMsBlock) ms_bu_kernel(
+template <int W, bool CO>
+__device__ __forceinline__ void ms_bu_phase(
     const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
     const uint32_t *__restrict__ base_vis, int64_t n, Lanes<W> act,
     unsigned long long *__restrict__ seen, const unsigned long long *__restrict__ cur,
@@ -238,7 +263,7 @@ __global__ void __launch_bounds__(kMsBlock) ms_bu_kernel(
         bool anyneed = false;
 #pragma unroll
         for (int i = 0; i < W; ++i) {
-            s[i] = skip ? 0ull : seen[v * W + i];
+            s[i] = skip ? 0ull : ld<CO>(seen + v * W + i);
             need[i] = skip ? 0ull : (act.w[i] & ~s[i]);
             acc[i] = 0ull;
             anyneed = anyneed || need[i] != 0ull;
@@ -253,7 +278,7 @@ __global__ void __launch_bounds__(kMsBlock) ms_bu_kernel(
             for (int64_t q = 0; q < lim; ++q) {
                 const int64_t u = __ldg(idx + beg + q);
                 unsigned long long x[W];
-                load_lanes<W>(cur + u * W, x);
+                load_lanes<W, CO>(cur + u * W, x);
                 ++ex;
                 bool comp = true;
 #pragma unroll
@@ -285,7 +310,7 @@ __global__ void __launch_bounds__(kMsBlock) ms_bu_kernel(
                 unsigned long long x[W];
                 if (e < le) {
                     const int64_t u = __ldg(idx + e);
-                    load_lanes<W>(cur + u * W, x);
+                    load_lanes<W, CO>(cur + u * W, x);
                 } else {
 #pragma unroll
                     for (int i = 0; i < W; ++i) x[i] = 0ull;
@@ -317,8 +342,8 @@ __global__ void __launch_bounds__(kMsBlock) ms_bu_kernel(
 
 // Vertices holding a frontier bit -> list (block scan, one atomic per
 // block); those of degree >= big_deg -> the grid-spread list instead.
-template <int W>
-__global__ void __launch_bounds__(kMsBlock) ms_compact_kernel(
+template <int W, bool CO>
+__device__ __forceinline__ void ms_compact_phase(
     const unsigned long long *__restrict__ cur, int64_t n, const int64_t *__restrict__ off,
     int64_t big_deg, int32_t *__restrict__ list, int32_t *__restrict__ big,
     unsigned long long *slot_cur) {
@@ -337,7 +362,7 @@ __global__ void __launch_bounds__(kMsBlock) ms_compact_kernel(
             bool active = false, isbig = false;
             if (v < n) {
 #pragma unroll
-                for (int i = 0; i < W; ++i) active = active || cur[v * W + i] != 0ull;
+                for (int i = 0; i < W; ++i) active = active || ld<CO>(cur + v * W + i) != 0ull;
                 if (active) isbig = off[v + 1] - off[v] >= big_deg;
             }
             small[k] = active && !isbig;
@@ -372,12 +397,12 @@ __global__ void __launch_bounds__(kMsBlock) ms_compact_kernel(
 
 // OR the frontier words `cu` of u into neighbour v's next words, only the
 // bits v has not seen.
-template <int W>
+template <int W, bool CO>
 __device__ __forceinline__ void ms_push(const unsigned long long (&cu)[W], int64_t v,
                                         const unsigned long long *__restrict__ seen,
                                         unsigned long long *__restrict__ nxt) {
     unsigned long long sv[W];
-    load_lanes<W>(seen + v * W, sv);
+    load_lanes<W, CO>(seen + v * W, sv);
 #pragma unroll
     for (int i = 0; i < W; ++i) {
         const unsigned long long add = cu[i] & ~sv[i];
@@ -388,13 +413,13 @@ __device__ __forceinline__ void ms_push(const unsigned long long (&cu)[W], int64
 // Top-down layer on bit lanes over the compacted list: a warp takes 32
 // entries; rows shorter than 32 are walked by their own lane, longer ones
 // by the whole warp.
-template <int W>
-__global__ void __launch_bounds__(kMsBlock) ms_td_kernel(
+template <int W, bool CO>
+__device__ __forceinline__ void ms_td_phase(
     const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
     const int32_t *__restrict__ list, const unsigned long long *slot_cur,
     const unsigned long long *__restrict__ cur, const unsigned long long *__restrict__ seen,
     unsigned long long *__restrict__ nxt) {
-    const int64_t cnt = (int64_t)slot_cur[M_LIST];
+    const int64_t cnt = (int64_t)ld<CO>(slot_cur + M_LIST);
     const unsigned lane = lane_id();
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -405,14 +430,14 @@ __global__ void __launch_bounds__(kMsBlock) ms_td_kernel(
 #pragma unroll
         for (int j = 0; j < W; ++j) cu[j] = 0ull;
         if (i < cnt) {
-            u = list[i];
+            u = ld<CO>(list + i);
             beg = off[u];
             end = off[u + 1];
-            load_lanes<W>(cur + u * W, cu);
+            load_lanes<W, CO>(cur + u * W, cu);
         }
         const bool wide = end - beg >= 32;
         if (!wide)
-            for (int64_t e = beg; e < end; ++e) ms_push<W>(cu, __ldg(idx + e), seen, nxt);
+            for (int64_t e = beg; e < end; ++e) ms_push<W, CO>(cu, __ldg(idx + e), seen, nxt);
         unsigned wm = __ballot_sync(0xffffffffu, wide);
         while (wm) {
             const int L = __ffs(wm) - 1;
@@ -422,15 +447,15 @@ __global__ void __launch_bounds__(kMsBlock) ms_td_kernel(
             unsigned long long cL[W];
 #pragma unroll
             for (int j = 0; j < W; ++j) cL[j] = __shfl_sync(0xffffffffu, cu[j], L);
-            for (int64_t e = lb + lane; e < le; e += 32) ms_push<W>(cL, __ldg(idx + e), seen, nxt);
+            for (int64_t e = lb + lane; e < le; e += 32) ms_push<W, CO>(cL, __ldg(idx + e), seen, nxt);
         }
     }
 }
 
 // The grid-spread list: batches of kMsBigBatch vertices, degree prefix in
 // shared memory, grid-stride over the batch's edges.
-template <int W>
-__global__ void __launch_bounds__(kMsBlock) ms_td_big_kernel(
+template <int W, bool CO>
+__device__ __forceinline__ void ms_td_big_phase(
     const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
     const int32_t *__restrict__ big, const unsigned long long *slot_cur,
     const unsigned long long *__restrict__ cur, const unsigned long long *__restrict__ seen,
@@ -439,7 +464,7 @@ __global__ void __launch_bounds__(kMsBlock) ms_td_big_kernel(
     __shared__ long long beg_s[kMsBigBatch];
     __shared__ int32_t u_s[kMsBigBatch];
     __shared__ long long wtot[kMsBlock / 32];
-    const int64_t cnt = (int64_t)slot_cur[M_BIG];
+    const int64_t cnt = (int64_t)ld<CO>(slot_cur + M_BIG);
     const unsigned lane = lane_id(), w = threadIdx.x >> 5;
     const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t tt = (int64_t)gridDim.x * blockDim.x;
@@ -452,7 +477,7 @@ __global__ void __launch_bounds__(kMsBlock) ms_td_big_kernel(
             const int t = threadIdx.x * per + k;
             long long d = 0;
             if (t < nb) {
-                const int32_t u = big[b0 + t];
+                const int32_t u = ld<CO>(big + b0 + t);
                 u_s[t] = u;
                 beg_s[t] = off[u];
                 d = off[u + 1] - beg_s[t];
@@ -486,8 +511,8 @@ __global__ void __launch_bounds__(kMsBlock) ms_td_big_kernel(
                 else hi = mid;
             }
             unsigned long long cu[W];
-            load_lanes<W>(cur + (int64_t)u_s[lo] * W, cu);
-            ms_push<W>(cu, __ldg(idx + beg_s[lo] + (g - pre[lo])), seen, nxt);
+            load_lanes<W, CO>(cur + (int64_t)u_s[lo] * W, cu);
+            ms_push<W, CO>(cu, __ldg(idx + beg_s[lo] + (g - pre[lo])), seen, nxt);
         }
         __syncthreads();
     }
@@ -495,8 +520,8 @@ __global__ void __launch_bounds__(kMsBlock) ms_td_big_kernel(
 
 // After a top-down layer: keep the bits of nxt not yet seen (they become the
 // next frontier), update seen and the level rows, count.
-template <int W>
-__global__ void __launch_bounds__(kMsBlock) ms_finalize_kernel(
+template <int W, bool CO>
+__device__ __forceinline__ void ms_finalize_phase(
     const int64_t *__restrict__ off, int64_t n, Lanes<W> act,
     unsigned long long *__restrict__ seen, unsigned long long *__restrict__ nxt,
     int8_t *__restrict__ levels, int8_t new_level, int64_t td_edges,
@@ -508,7 +533,7 @@ __global__ void __launch_bounds__(kMsBlock) ms_finalize_kernel(
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += stride) {
         unsigned long long x[W], s[W], nw[W];
         bool any = false;
-        load_lanes<W>(nxt + v * W, x);
+        load_lanes<W, CO>(nxt + v * W, x);
         if constexpr (W == 1) {
             any = x[0] != 0ull;
         } else {
@@ -516,7 +541,7 @@ __global__ void __launch_bounds__(kMsBlock) ms_finalize_kernel(
             for (int i = 0; i < W; ++i) any = any || x[i] != 0ull;
         }
         if (!any) continue;
-        load_lanes<W>(seen + v * W, s);
+        load_lanes<W, CO>(seen + v * W, s);
 #pragma unroll
         for (int i = 0; i < W; ++i) {
             nw[i] = x[i] & ~s[i] & act.w[i];
@@ -525,6 +550,197 @@ __global__ void __launch_bounds__(kMsBlock) ms_finalize_kernel(
         ms_commit<W>(v, n, off[v + 1] - off[v], s, nw, act, seen, levels, new_level, c);
     }
     block_add<6>(c, slot_next);
+}
+
+// Kernels for the host-driven loop: one phase each.
+template <int W>
+__global__ void __launch_bounds__(kMsBlock) ms_bu_kernel(
+    const int64_t *off, const int32_t *idx, const uint32_t *base_vis, int64_t n, Lanes<W> act,
+    unsigned long long *seen, const unsigned long long *cur, unsigned long long *nxt,
+    int8_t *levels, int8_t new_level, int probe, unsigned long long *slot_next,
+    int64_t *zero_slot) {
+    ms_bu_phase<W, false>(off, idx, base_vis, n, act, seen, cur, nxt, levels, new_level, probe,
+                          slot_next, zero_slot);
+}
+
+template <int W>
+__global__ void __launch_bounds__(kMsBlock) ms_compact_kernel(
+    const unsigned long long *cur, int64_t n, const int64_t *off, int64_t big_deg, int32_t *list,
+    int32_t *big, unsigned long long *slot_cur) {
+    ms_compact_phase<W, false>(cur, n, off, big_deg, list, big, slot_cur);
+}
+
+template <int W>
+__global__ void __launch_bounds__(kMsBlock) ms_td_kernel(
+    const int64_t *off, const int32_t *idx, const int32_t *list, const unsigned long long *slot_cur,
+    const unsigned long long *cur, const unsigned long long *seen, unsigned long long *nxt) {
+    ms_td_phase<W, false>(off, idx, list, slot_cur, cur, seen, nxt);
+}
+
+template <int W>
+__global__ void __launch_bounds__(kMsBlock) ms_td_big_kernel(
+    const int64_t *off, const int32_t *idx, const int32_t *big, const unsigned long long *slot_cur,
+    const unsigned long long *cur, const unsigned long long *seen, unsigned long long *nxt) {
+    ms_td_big_phase<W, false>(off, idx, big, slot_cur, cur, seen, nxt);
+}
+
+template <int W>
+__global__ void __launch_bounds__(kMsBlock) ms_finalize_kernel(
+    const int64_t *off, int64_t n, Lanes<W> act, unsigned long long *seen,
+    unsigned long long *nxt, int8_t *levels, int8_t new_level, int64_t td_edges,
+    unsigned long long *slot_next, int64_t *zero_slot) {
+    ms_finalize_phase<W, false>(off, n, act, seen, nxt, levels, new_level, td_edges, slot_next,
+                                zero_slot);
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier for a cooperative launch (every block resident).
+// bar[0] counts arrivals, bar[1] is the generation the last arrival bumps.
+// Every wait is bounded: a block that waits longer than timeout_ns sets
+// *err, and every block that sees *err leaves; the caller then returns.
+// `expected` is gridDim.x except in the self-test, which asks for more.
+__device__ bool grid_barrier(unsigned *bar, int32_t *err, unsigned expected,
+                             unsigned long long timeout_ns) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned *gen = bar + 1;
+        volatile int32_t *verr = err;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == expected - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (*gen == g) {
+                if (*verr) {
+                    ok = 0;
+                    break;
+                }
+                if (global_ns() - t0 > timeout_ns) {
+                    atomicExch(err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(128);
+            }
+        }
+        __threadfence();
+        if (*verr) ok = 0;
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+struct MsPersist {
+    const int64_t *off;
+    const int32_t *idx;
+    const uint32_t *base_vis;
+    int64_t n, nnz;
+    unsigned long long *seen, *buf0, *buf1;
+    int8_t *levels;
+    int32_t *list, *big;
+    int64_t *trace;   // ring of kMsRing slots; slot 0 written by ms_roots_kernel
+    int64_t *layers;  // [128][8] per-layer record
+    int32_t *result;  // [0] layers, [1] status
+    unsigned *bar;    // barrier count, generation
+    int32_t *err;
+    double alpha, beta;
+    int probe;
+    int64_t big_deg;
+    unsigned long long timeout_ns;
+};
+
+constexpr int kMsRingP = 64;
+constexpr int kMsFieldsP = 8;
+
+// The whole batched traversal in one cooperative launch: every block runs
+// the same layer loop and takes the same direction decision from the layer
+// counters, which grid barriers make visible between phases. Bottom-up
+// layers are one phase; top-down layers are compaction (+ clearing nxt),
+// push, and the dense keep-unseen pass.
+template <int W>
+__global__ void __launch_bounds__(kMsBlock) ms_persistent_kernel(MsPersist p, Lanes<W> act) {
+    const unsigned expected = gridDim.x;
+    int64_t v_u = p.n - __ldcg(p.trace + M_FULLN);
+    int64_t e_u = p.nnz - __ldcg(p.trace + M_FULLDEG);
+    int cur_bu = 0, status = BFS_OK, d = 0;
+    for (;; ++d) {
+        int64_t *sc = p.trace + (d % kMsRingP) * kMsFieldsP;
+        int64_t *sn = p.trace + ((d + 1) % kMsRingP) * kMsFieldsP;
+        int64_t *sz = p.trace + ((d + 2) % kMsRingP) * kMsFieldsP;
+        const int64_t v_f = __ldcg(sc + M_NV), e_f = __ldcg(sc + M_MF);
+        if (v_f == 0) break;
+        if (d + 1 > 127) {
+            status = BFS_ERR_DEPTH;
+            break;
+        }
+        if (!cur_bu) cur_bu = ((double)e_f > (double)e_u / p.alpha) ? 1 : 0;
+        else cur_bu = ((double)v_f < (double)p.n / p.beta) ? 0 : 1;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            int64_t *rec = p.layers + (int64_t)d * 8;
+            rec[0] = cur_bu;
+            rec[1] = v_f;
+            rec[2] = e_f;
+            rec[3] = __ldcg(sc + M_PAIRS);
+            rec[4] = v_u;
+            rec[5] = e_u;
+        }
+        unsigned long long *cur = (d & 1) ? p.buf1 : p.buf0;
+        unsigned long long *nxt = (d & 1) ? p.buf0 : p.buf1;
+        const int8_t nl = (int8_t)(d + 1);
+        if (cur_bu) {
+            ms_bu_phase<W, true>(p.off, p.idx, p.base_vis, p.n, act, p.seen, cur, nxt, p.levels, nl,
+                                 p.probe, (unsigned long long *)sn, sz);
+        } else {
+            ms_compact_phase<W, true>(cur, p.n, p.off, p.big_deg, p.list, p.big,
+                                      (unsigned long long *)sc);
+            const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+            for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n * W; i += stride)
+                nxt[i] = 0ull;
+            if (!grid_barrier(p.bar, p.err, expected, p.timeout_ns)) {
+                status = BFS_ERR_TIMEOUT;
+                break;
+            }
+            ms_td_phase<W, true>(p.off, p.idx, p.list, (const unsigned long long *)sc, cur, p.seen,
+                                 nxt);
+            ms_td_big_phase<W, true>(p.off, p.idx, p.big, (const unsigned long long *)sc, cur,
+                                     p.seen, nxt);
+            if (!grid_barrier(p.bar, p.err, expected, p.timeout_ns)) {
+                status = BFS_ERR_TIMEOUT;
+                break;
+            }
+            ms_finalize_phase<W, true>(p.off, p.n, act, p.seen, nxt, p.levels, nl, e_f,
+                                       (unsigned long long *)sn, sz);
+        }
+        if (!grid_barrier(p.bar, p.err, expected, p.timeout_ns)) {
+            status = BFS_ERR_TIMEOUT;
+            break;
+        }
+        v_u -= __ldcg(sn + M_FULLN);
+        e_u -= __ldcg(sn + M_FULLDEG);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        p.result[0] = d;
+        p.result[1] = status;
+    }
+}
+
+// One barrier that waits for `missing` more blocks than the grid has: the
+// wait runs out and the kernel reports it instead of hanging.
+__global__ void barrier_probe_kernel(unsigned *bar, int32_t *err, unsigned missing,
+                                     unsigned long long timeout_ns, int32_t *ok) {
+    const bool r = grid_barrier(bar, err, gridDim.x + missing, timeout_ns);
+    if (threadIdx.x == 0 && !r) atomicExch(ok, 0);
 }
 
 }  // namespace
@@ -674,6 +890,130 @@ bfs_status run_batch_w(bfs_graph *g, const int32_t *roots, int k, int8_t *levels
     return BFS_OK;
 }
 
+constexpr int kPctlLayers = 128;
+constexpr size_t kPctlBytes = kPctlLayers * 8 * 8 + 64;  // records, result, barrier, err
+
+// The same traversal as run_batch_w, as one CUDA graph: fill, roots and the
+// persistent kernel (a cooperative node). The graph is captured once per
+// (W, k, output buffer, bitset buffers, configuration) and replayed.
+template <int W>
+bfs_status run_batch_graph(bfs_graph *g, const int32_t *roots, int k, int8_t *levels,
+                           cudaStream_t st) {
+    MsState *m = g->ms;
+    const int64_t n = g->n;
+    if (!m->pctl) {
+        GB_CK(cudaMalloc(&m->pctl, kPctlBytes));
+        GB_CK(cudaMallocHost(&m->h_pctl, kPctlBytes));
+    }
+    const bool stale = !m->exec || m->g_W != W || m->g_k != k || m->g_levels != levels ||
+                       m->g_seen != m->seen || memcmp(&m->g_cfg, &m->cfg, sizeof m->cfg) != 0;
+    if (stale) {
+        if (m->exec) cudaGraphExecDestroy(m->exec);
+        if (m->graph) cudaGraphDestroy(m->graph);
+        m->exec = nullptr;
+        m->graph = nullptr;
+        int occ = 0;
+        GB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ms_persistent_kernel<W>,
+                                                            kMsBlock, 0));
+        if (occ < 1) {
+            set_error("bfs_run_batch: the persistent kernel does not fit on an SM");
+            return BFS_ERR_CUDA;
+        }
+        const Lanes<W> act = active_lanes<W>(k);
+        MsPersist p;
+        p.off = g->off;
+        p.idx = g->idx;
+        p.base_vis = g->base_vis;
+        p.n = n;
+        p.nnz = g->nnz;
+        p.seen = m->seen;
+        p.buf0 = m->cur;
+        p.buf1 = m->nxt;
+        p.levels = levels;
+        p.list = m->list;
+        p.big = m->big;
+        p.trace = m->trace;
+        p.layers = m->pctl;
+        p.result = (int32_t *)(m->pctl + kPctlLayers * 8);
+        p.bar = (unsigned *)(p.result + 2);
+        p.err = (int32_t *)(p.bar + 2);
+        p.alpha = m->cfg.alpha;
+        p.beta = m->cfg.beta;
+        p.probe = m->cfg.lane_probe;
+        p.big_deg = m->cfg.big_degree;
+        p.timeout_ns = 2000000000ull;  // 2 s per barrier wait
+        const int64_t total = (int64_t)k * n;
+        const int aligned = ((uintptr_t)levels % 16) == 0;
+        // Captured on a private stream (capture cannot start on the legacy
+        // default stream); the instantiated graph is launched on `st`.
+        if (!m->cap) GB_CK(cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking));
+        cudaStream_t cs = m->cap;
+        GB_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        ms_fill_kernel<<<grid_cap(std::max<int64_t>(total / 16, n * W), kMsBlock, 8), kMsBlock, 0,
+                         cs>>>(levels, total, aligned, m->seen, m->cur, n * W);
+        cudaMemsetAsync(m->trace, 0, (size_t)kMsRing * kMsFields * 8, cs);
+        ms_roots_kernel<W><<<1, kMaxRoots, 0, cs>>>(roots, k, n, g->off, act, m->seen, m->cur,
+                                                    levels, m->trace);
+        cudaMemsetAsync(p.result, 0, 64, cs);
+        cudaLaunchConfig_t lc;
+        memset(&lc, 0, sizeof lc);
+        lc.gridDim = dim3(occ * sm_count());
+        lc.blockDim = dim3(kMsBlock);
+        lc.stream = cs;
+        cudaLaunchAttribute at;
+        at.id = cudaLaunchAttributeCooperative;
+        at.val.cooperative = 1;
+        lc.attrs = &at;
+        lc.numAttrs = 1;
+        cudaError_t le = cudaLaunchKernelEx(&lc, ms_persistent_kernel<W>, p, act);
+        cudaGraph_t graph = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+        if (le != cudaSuccess || ce != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return cuda_status(le != cudaSuccess ? le : ce, "capture of the batched traversal",
+                               __FILE__, __LINE__);
+        }
+        m->graph = graph;
+        GB_CK(cudaGraphInstantiate(&m->exec, graph, 0));
+        m->g_W = W;
+        m->g_k = k;
+        m->g_levels = levels;
+        m->g_seen = m->seen;
+        m->g_cfg = m->cfg;
+    }
+    GB_CK(cudaGraphLaunch(m->exec, st));
+    count_launch(3);
+    GB_CK(cudaMemcpyAsync(m->h_pctl, m->pctl, kPctlBytes, cudaMemcpyDeviceToHost, st));
+    GB_CK(cudaStreamSynchronize(st));
+    const int32_t *res = (const int32_t *)(m->h_pctl + kPctlLayers * 8);
+    const int L = std::min(res[0], kPctlLayers);
+    m->last.clear();
+    m->last_pairs = 0;
+    for (int d = 0; d < L; ++d) {
+        const int64_t *rec = m->h_pctl + (int64_t)d * 8;
+        bfs_batch_layer_stats ls;
+        memset(&ls, 0, sizeof ls);
+        ls.direction = (int32_t)rec[0];
+        ls.v_f = rec[1];
+        ls.e_f = rec[2];
+        ls.pairs = rec[3];
+        ls.v_u = rec[4];
+        ls.e_u = rec[5];
+        m->last.push_back(ls);
+        m->last_pairs += ls.pairs;
+    }
+    if (res[1] == BFS_ERR_DEPTH) {
+        set_error("bfs_run_batch: a level above 127 does not fit in int8");
+        return BFS_ERR_DEPTH;
+    }
+    if (res[1] != BFS_OK) {
+        set_error("bfs_run_batch: a grid barrier wait of the device loop ran out");
+        return (bfs_status)res[1];
+    }
+    return BFS_OK;
+}
+
 bool is_device_ptr(const void *p) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -755,6 +1095,14 @@ extern "C" BFS_API bfs_status bfs_run_batch(bfs_graph *g, const int32_t *roots, 
             return BFS_ERR_INVALID;
         }
     GB_CK(cudaMemcpyAsync(m->roots, hr.data(), (size_t)k * 4, cudaMemcpyHostToDevice, st));
+    if (m->cfg.use_graph) {
+        switch (W) {
+            case 1: return run_batch_graph<1>(g, m->roots, k, levels_out, st);
+            case 2: return run_batch_graph<2>(g, m->roots, k, levels_out, st);
+            case 4: return run_batch_graph<4>(g, m->roots, k, levels_out, st);
+            default: return run_batch_graph<8>(g, m->roots, k, levels_out, st);
+        }
+    }
     switch (W) {
         case 1: return run_batch_w<1>(g, m->roots, k, levels_out, st);
         case 2: return run_batch_w<2>(g, m->roots, k, levels_out, st);
@@ -841,6 +1189,13 @@ extern "C" BFS_API bfs_status bfs_batch_autotune(bfs_graph *g, const int32_t *ro
             if ((s = timed(c, &t)) != BFS_OK) goto done;
             if (t < cur_t) { cur = c; cur_t = t; }
         }
+        {  // host-driven layers or the device-side loop in one graph
+            bfs_batch_config c = cur;
+            c.use_graph = !cur.use_graph;
+            float t;
+            if ((s = timed(c, &t)) != BFS_OK) goto done;
+            if (t < cur_t) { cur = c; cur_t = t; }
+        }
     }
 done:
     cudaEventDestroy(e0);
@@ -849,4 +1204,40 @@ done:
     g->ms->cfg = (s == BFS_OK) ? cur : base;
     if (s == BFS_OK && best) *best = cur;
     return s;
+}
+
+extern "C" BFS_API bfs_status bfs_selftest_grid_barrier(int32_t missing_blocks, int64_t timeout_us,
+                                                        void *stream) {
+    clear_error();
+    if (missing_blocks < 0 || missing_blocks > 1024 || timeout_us < 1000 ||
+        timeout_us > 10000000) {
+        set_error("bfs_selftest_grid_barrier: need 0 <= missing <= 1024 and 1 ms <= timeout <= 10 s");
+        return BFS_ERR_INVALID;
+    }
+    cudaStream_t st = as_stream(stream);
+    int32_t *buf = nullptr;  // bar[2], err, ok
+    GB_CK(cudaMallocAsync(&buf, 16, st));
+    const int32_t init[4] = {0, 0, 0, 1};
+    int32_t out[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(buf, init, 16, cudaMemcpyHostToDevice, st);
+    const unsigned missing = (unsigned)missing_blocks;
+    unsigned long long tns = (unsigned long long)timeout_us * 1000ull;
+    unsigned *bar = (unsigned *)buf;
+    int32_t *err = buf + 2, *ok = buf + 3;
+    void *args[] = {&bar, &err, (void *)&missing, &tns, &ok};
+    if (e == cudaSuccess)
+        e = cudaLaunchCooperativeKernel((const void *)barrier_probe_kernel, dim3(sm_count()),
+                                        dim3(32), args, 0, st);
+    count_launch();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, buf, 16, cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(buf, st);
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e, "barrier self-test", __FILE__, __LINE__);
+    if (e2 != cudaSuccess) return cuda_status(e2, "barrier self-test", __FILE__, __LINE__);
+    if (!out[3]) {
+        set_error("grid barrier wait ran out after %lld us (%d blocks never arrived)",
+                  (long long)timeout_us, missing_blocks);
+        return BFS_ERR_TIMEOUT;
+    }
+    return BFS_OK;
 }

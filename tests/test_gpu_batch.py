@@ -2,6 +2,8 @@
 the oracle's single-source levels of that root (exact)."""
 from __future__ import annotations
 
+import time
+
 import numpy as np
 import pytest
 import torch
@@ -40,23 +42,49 @@ def check(g, o_off, o_idx, roots):
 
 @pytest.mark.parametrize("k", [1, 2, 63, 64, 65, 127, 128, 129, 256, 300, 512])
 @pytest.mark.parametrize("mode", ["auto", "bu", "td"])
-def test_batch_rmat14_matches_oracle(k, mode):
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_batch_rmat14_matches_oracle(k, mode, use_graph):
     n, o_off, o_idx, g = rmat(14)
-    set_cfg(g, **({"bu": ALL_BU, "td": ALL_TD}.get(mode, {})))
+    set_cfg(g, use_graph=use_graph, **({"bu": ALL_BU, "td": ALL_TD}.get(mode, {})))
     roots = np.random.default_rng(k).integers(0, n, size=k).astype(np.int32)
     check(g, o_off, o_idx, roots)
 
 
 @pytest.mark.parametrize("probe", [0, 1, 3, 64])
-def test_batch_lane_probe_and_hubs(probe):
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_batch_lane_probe_and_hubs(probe, use_graph):
     n = 3000
     s, d = inputs.powerlaw_edges(n, 12 * n, 7, hubs=4)
     o_off, o_idx, g_off, g_idx = both_csr(n, s, d)
     g = gb.Graph(g_off, g_idx)
     for mode in [{}, ALL_BU, ALL_TD]:
-        set_cfg(g, lane_probe=probe, big_degree=64, **mode)
+        set_cfg(g, lane_probe=probe, big_degree=64, use_graph=use_graph, **mode)
         roots = np.random.default_rng(probe).integers(0, n, size=200).astype(np.int32)
         check(g, o_off, o_idx, roots)
+
+
+def test_device_loop_replays_and_recaptures():
+    n, o_off, o_idx, g = rmat(13)
+    set_cfg(g, use_graph=1)
+    out = torch.empty((70, n), dtype=torch.int8, device="cuda")
+    for seed in range(3):   # same arguments: the captured graph is replayed
+        roots = np.random.default_rng(seed).integers(0, n, size=70).astype(np.int32)
+        g.run_batch(roots, out)
+        assert np.array_equal(out.cpu().numpy(), oracle.msbfs_levels(o_off, o_idx, roots.tolist()))
+        layers, pairs = g.batch_stats()
+        assert layers and pairs >= 70
+    roots = [5, 6, 7]       # new k and output buffer: captured again
+    check(g, o_off, o_idx, roots)
+
+
+def test_grid_barrier_wait_runs_out_and_context_survives():
+    assert gb.selftest_grid_barrier(0, 200000) == 0
+    t0 = time.time()
+    assert gb.selftest_grid_barrier(1, 200000) == 4          # BFS_ERR_TIMEOUT
+    assert time.time() - t0 < 30
+    assert gb.selftest_grid_barrier(0, 200000) == 0
+    n, o_off, o_idx, g = rmat(12)                            # the context still works
+    check(g, o_off, o_idx, [0, 1, 2])
 
 
 def test_batch_duplicate_roots_and_small_graphs():
@@ -93,10 +121,12 @@ def test_batch_device_roots_and_errors():
         g.run_batch(torch.zeros(0, dtype=torch.int32))
 
 
-def test_batch_depth_over_127_is_an_error():
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_batch_depth_over_127_is_an_error(use_graph):
     n = 300
     o_off, o_idx, g_off, g_idx = both_csr(n, *inputs.path_edges(n))
     g = gb.Graph(g_off, g_idx)
+    set_cfg(g, use_graph=use_graph)
     lv = torch.empty((2, n), dtype=torch.int8, device="cuda")
     with pytest.raises(gb.BfsError) as e:
         g.run_batch([0, 5], lv)
