@@ -136,12 +136,27 @@ typedef struct bfs_config {
     int32_t td_claim;        /* top-down claim of a vertex: 0 = atomicCAS on
                                 parent[v] (-1 -> u); 1 = atomicOr on the
                                 visited bitmap word, then plain parent store  */
-    int32_t bu_head;         /* 1 = the bottom-up probe reads a 16-byte record
-                                per vertex {first three neighbours, degree}
-                                built on first use (16*n bytes), one
-                                coalesced load instead of a row-bound pair
-                                and a random index sector; 0 = read the CSR  */
-    int32_t reserved[5];
+    int32_t bu_head;         /* 1 = the bottom-up probe reads an 8-byte record
+                                per vertex {first neighbour, degree}, built on
+                                first use (8*n bytes): one coalesced load
+                                instead of a row-bound pair and a random
+                                index sector; 0 = read the CSR only          */
+    int32_t prune_components;/* 1 = vertices outside the root's connected
+                                component start as visited, so bottom-up
+                                layers skip them (results unchanged; only the
+                                edges-examined count shrinks). The component
+                                of the highest-degree vertex is found once, by
+                                one traversal on first use, and kept (n/8
+                                bytes); roots outside it are not pruned.
+                                Off by default: on R-MAT graphs almost every
+                                vertex outside the giant component has degree
+                                0 and is skipped anyway                       */
+    int32_t bu_list_percent; /* bottom-up layers with at most this percentage
+                                of n vertices left to find (unvisited, degree
+                                > 0) run on a compacted list of those vertices,
+                                one thread each, instead of one warp per
+                                bitmap word; 0 = never                        */
+    int32_t reserved[3];
 } bfs_config;
 
 /* Fills `cfg` with the defaults (edge policy, alpha 14, beta 24, ...). */
@@ -157,7 +172,7 @@ BFS_API void bfs_config_default(bfs_config *cfg);
  * per-traversal scratch: four n-bit bitmaps (visited, frontier, next, and
  * the degree-0 mask), three n-entry vertex lists (two queues and the list of
  * grid-spread vertices) and a small counter block: about 12.5*n bytes. The
- * 16-byte head records (cfg.bu_head) are built by the first bfs_run that
+ * 8-byte head records (cfg.bu_head) are built by the first bfs_run that
  * asks for them.
  * Without BFS_BORROW the CSR is copied into library memory and the caller may
  * free its arrays. cfg may be NULL (defaults). Synchronous. */

@@ -42,7 +42,8 @@ class Config(ctypes.Structure):
                 ("td_warp_degree", ctypes.c_int32), ("td_grid_degree", ctypes.c_int32),
                 ("timing", ctypes.c_int32), ("bu_words", ctypes.c_int32),
                 ("td_claim", ctypes.c_int32), ("bu_head", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("prune_components", ctypes.c_int32), ("bu_list_percent", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class LayerStats(ctypes.Structure):
@@ -241,9 +242,11 @@ class Graph:
         self._h = h
         self.n = n
         self.nnz = nnz
+        self.config = config if config is not None else default_config()
 
     def set_config(self, config: Config | None):
         _check(lib().bfs_graph_set_config(self._h, ctypes.byref(config) if config else None))
+        self.config = config if config is not None else default_config()
 
     def run(self, root: int, level: torch.Tensor | None = None, parent: torch.Tensor | None = None,
             want_parent: bool = True, stream=None):

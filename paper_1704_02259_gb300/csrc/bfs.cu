@@ -57,20 +57,53 @@ __global__ void base_vis_kernel(const int64_t *__restrict__ off, int64_t n, int6
     }
 }
 
-// Per-vertex head record for the bottom-up probe: the first three entries of
-// the vertex's CSR row (-1 past its degree) and the degree.
+// Per-vertex head record for the bottom-up probe: the first entry of the
+// vertex's CSR row (-1 if it has none) and the degree.
 __global__ void head_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
-                            int64_t n, int4 *__restrict__ head) {
+                            int64_t n, int2 *__restrict__ head) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += stride) {
         const int64_t b = off[v];
         const int d = (int)(off[v + 1] - b);
-        head[v] = make_int4(d > 0 ? idx[b] : -1, d > 1 ? idx[b + 1] : -1, d > 2 ? idx[b + 2] : -1, d);
+        head[v] = make_int2(d > 0 ? idx[b] : -1, d);
+    }
+}
+
+// Highest-degree vertex (smallest id on ties), packed as degree << 32 | ~id.
+__global__ void max_degree_kernel(const int64_t *__restrict__ off, int64_t n,
+                                  unsigned long long *best) {
+    unsigned long long b = 0ull;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += stride) {
+        const unsigned long long d = (unsigned long long)(off[v + 1] - off[v]);
+        const unsigned long long key = (d << 32) | (0xffffffffull - (unsigned long long)v);
+        b = key > b ? key : b;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, b, o);
+        b = y > b ? y : b;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(best, b);
+}
+
+// Bitmap of the vertices a traversal reached (level >= 0).
+__global__ void reached_bits_kernel(const int32_t *__restrict__ level, int64_t n, int64_t nw_pad,
+                                    uint32_t *__restrict__ bits) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nw_pad; w += stride) {
+        uint32_t x = 0;
+        for (int b = 0; b < 32; ++b) {
+            const int64_t v = w * 32 + b;
+            if (v < n && level[v] >= 0) x |= 1u << b;
+        }
+        bits[w] = x;
     }
 }
 
 __global__ void init_kernel(int64_t n, int64_t nw_pad, int32_t root,
                             const int64_t *__restrict__ off, const uint32_t *__restrict__ base,
+                            const uint32_t *__restrict__ comp_in,
                             int32_t *__restrict__ level, int32_t *__restrict__ parent,
                             uint32_t *__restrict__ visited, uint32_t *__restrict__ front,
                             int32_t *__restrict__ queue, int64_t *__restrict__ trace) {
@@ -82,8 +115,11 @@ __global__ void init_kernel(int64_t n, int64_t nw_pad, int32_t root,
     }
     const int64_t rw = root >> 5;
     const uint32_t rbit = 1u << (root & 31);
+    // with a component mask that holds the root, everything outside it
+    // starts visited: no edge leads there from the root
+    const bool prune = comp_in && ((comp_in[rw] & rbit) != 0u);
     for (int64_t w = t0; w < nw_pad; w += stride) {
-        visited[w] = base[w] | (w == rw ? rbit : 0u);
+        visited[w] = base[w] | (w == rw ? rbit : 0u) | (prune ? ~comp_in[w] : 0u);
         front[w] = (w == rw) ? rbit : 0u;
     }
     for (int64_t i = t0; i < kRing * kFields; i += stride) {
@@ -249,17 +285,17 @@ __global__ void __launch_bounds__(kBlock) td_kernel(TdArgs a, const int32_t *__r
             const int32_t lu = __shfl_sync(0xffffffffu, u, L);
             const int64_t lb = __shfl_sync(0xffffffffu, beg, L);
             const int64_t le = __shfl_sync(0xffffffffu, end, L);
-            for (int64_t e0 = lb; e0 < le; e0 += 64) {
-                bool ok[2];
-                int32_t uu[2], vv[2];
+            for (int64_t e0 = lb; e0 < le; e0 += 32 * kTdK) {
+                bool ok[kTdK];
+                int32_t uu[kTdK], vv[kTdK];
 #pragma unroll
-                for (int k = 0; k < 2; ++k) {
+                for (int k = 0; k < kTdK; ++k) {
                     const int64_t e = e0 + 32 * k + lane;
                     ok[k] = e < le;
                     uu[k] = lu;
                     vv[k] = ok[k] ? a.idx[e] : 0;
                 }
-                td_visit<2>(a, ok, uu, vv, my_mf, my_nf);
+                td_visit<kTdK>(a, ok, uu, vv, my_mf, my_nf);
             }
         }
         const int sdeg = (have && !isbig && !isw) ? (int)deg : 0;
@@ -342,11 +378,11 @@ __global__ void __launch_bounds__(kBlock) td_big_kernel(TdArgs a, const int32_t 
         if (threadIdx.x == kBlock - 1) pre[kBigBatch] = run;
         __syncthreads();
         const long long total = pre[kBigBatch];
-        for (long long g0 = gw * 64; g0 < total; g0 += tw * 64) {
-            bool ok[2];
-            int32_t uu[2], vv[2];
+        for (long long g0 = gw * 32 * kTdK; g0 < total; g0 += tw * 32 * kTdK) {
+            bool ok[kTdK];
+            int32_t uu[kTdK], vv[kTdK];
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
+            for (int k = 0; k < kTdK; ++k) {
                 const long long g = g0 + 32 * k + lane;
                 ok[k] = g < total;
                 uu[k] = 0;
@@ -362,7 +398,7 @@ __global__ void __launch_bounds__(kBlock) td_big_kernel(TdArgs a, const int32_t 
                     vv[k] = a.idx[beg_s[lo] + (g - pre[lo])];
                 }
             }
-            td_visit<2>(a, ok, uu, vv, my_mf, my_nf);
+            td_visit<kTdK>(a, ok, uu, vv, my_mf, my_nf);
         }
         __syncthreads();
     }
@@ -382,13 +418,13 @@ __global__ void __launch_bounds__(kBlock) td_big_kernel(TdArgs a, const int32_t 
 //   3. the ballot of found lanes is the next word and is ORed into the
 //      visited word by the owning warp, without atomics.
 // Row positions are 32-bit offsets from a per-lane row pointer. With HEAD the
-// first three positions and the degree come from the vertex's 16-byte head
-// record (one coalesced load per lane); the row bounds are read only for
-// rows longer than three that found no parent there.
+// first position and the degree come from the vertex's 8-byte head record
+// (one coalesced load per lane); the row bound is read only for rows longer
+// than one whose first neighbour is not in the frontier.
 template <int W, int CH, bool HEAD>
-__global__ void __launch_bounds__(kBlock) bu_kernel(
+__global__ void __launch_bounds__(kBlock, 4) bu_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
-    const int4 *__restrict__ head, int64_t nw_pad,
+    const int2 *__restrict__ head, int64_t nw_pad,
     uint32_t *__restrict__ visited, const uint32_t *__restrict__ front,
     uint32_t *__restrict__ next_bm, int32_t *__restrict__ parent, int32_t *__restrict__ level,
     int32_t new_level, int probe, unsigned long long *slot_next, int64_t *zero_slot) {
@@ -420,9 +456,9 @@ __global__ void __launch_bounds__(kBlock) bu_kernel(
             int deg[W], ex[W];
             int32_t p[W];
             // positions [0, lane_lim) are tested by the lane itself
-            const int lane_lim = HEAD ? (probe > 3 ? probe : 3) : probe;
+            const int lane_lim = HEAD ? (probe > 1 ? probe : 1) : probe;
             if (HEAD) {
-                int4 h[W];
+                int2 h[W];
 #pragma unroll
                 for (int k = 0; k < W; ++k) {
                     const int64_t v = v_c + (j + k) * 32;
@@ -430,31 +466,23 @@ __global__ void __launch_bounds__(kBlock) bu_kernel(
                     found[k] = false;
                     p[k] = -1;
                     ex[k] = 0;
-                    h[k] = unv[k] ? __ldg(head + v) : make_int4(-1, -1, -1, 0);
-                    deg[k] = h[k].w;
+                    h[k] = unv[k] ? __ldg(head + v) : make_int2(-1, 0);
+                    deg[k] = h[k].y;
                     row[k] = idx;
                 }
-                uint32_t fw[W][3];
+                uint32_t fw[W];
+#pragma unroll
+                for (int k = 0; k < W; ++k) fw[k] = h[k].x >= 0 ? __ldg(front + (h[k].x >> 5)) : 0u;
 #pragma unroll
                 for (int k = 0; k < W; ++k) {
-                    fw[k][0] = h[k].x >= 0 ? __ldg(front + (h[k].x >> 5)) : 0u;
-                    fw[k][1] = h[k].y >= 0 ? __ldg(front + (h[k].y >> 5)) : 0u;
-                    fw[k][2] = h[k].z >= 0 ? __ldg(front + (h[k].z >> 5)) : 0u;
-                }
-#pragma unroll
-                for (int k = 0; k < W; ++k) {
-                    const int32_t c3[3] = {h[k].x, h[k].y, h[k].z};
-#pragma unroll
-                    for (int t = 0; t < 3; ++t) {
-                        if (!found[k] && c3[t] >= 0) {
-                            ++ex[k];
-                            if ((fw[k][t] >> (c3[t] & 31)) & 1u) {
-                                found[k] = true;
-                                p[k] = c3[t];
-                            }
+                    if (h[k].x >= 0) {
+                        ex[k] = 1;
+                        if ((fw[k] >> (h[k].x & 31)) & 1u) {
+                            found[k] = true;
+                            p[k] = h[k].x;
                         }
                     }
-                    if (unv[k] && !found[k] && deg[k] > 3)
+                    if (unv[k] && !found[k] && deg[k] > 1)
                         row[k] = idx + off[v_c + (j + k) * 32];
                 }
             } else {
@@ -474,7 +502,7 @@ __global__ void __launch_bounds__(kBlock) bu_kernel(
                     deg[k] = (int)(e - b);
                 }
             }
-            for (int p0 = HEAD ? 3 : 0; p0 < lane_lim; p0 += CH) {
+            for (int p0 = HEAD ? 1 : 0; p0 < lane_lim; p0 += CH) {
                 int32_t cand[W][CH];
                 bool any = false;
 #pragma unroll
@@ -568,6 +596,166 @@ __global__ void __launch_bounds__(kBlock) bu_kernel(
     block_add3(my_nf, my_mf, my_ex, slot_next + T_NF, slot_next + T_MF, slot_next + T_EXAM);
 }
 
+// Unvisited bitmap -> list of the vertices still to find (bits of ~visited;
+// degree-0 vertices and ids past n are set in visited and so never listed).
+// Same block scan as b2q_kernel.
+__global__ void __launch_bounds__(kBlock) unvisited_list_kernel(const uint32_t *__restrict__ vis,
+                                                                int64_t nw,
+                                                                int32_t *__restrict__ list,
+                                                                unsigned long long *count) {
+    __shared__ int wtot[kBlock / 32];
+    __shared__ unsigned long long base_s;
+    const unsigned lane = lane_id(), w = threadIdx.x >> 5;
+    for (int64_t t0 = (int64_t)blockIdx.x * kBlock * 4; t0 < nw; t0 += (int64_t)gridDim.x * kBlock * 4) {
+        const int64_t w0 = t0 + threadIdx.x * 4;
+        uint32_t words[4];
+        int c = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            words[k] = (w0 + k < nw) ? ~vis[w0 + k] : 0u;
+            c += __popc(words[k]);
+        }
+        int tot;
+        const int excl = warp_exclusive_scan(c, &tot);
+        if (lane == 31) wtot[w] = tot;
+        __syncthreads();
+        int before = 0, all = 0;
+        for (int i = 0; i < kBlock / 32; ++i) {
+            if (i < (int)w) before += wtot[i];
+            all += wtot[i];
+        }
+        if (threadIdx.x == 0) base_s = all ? atomicAdd(count, (unsigned long long)all) : 0ull;
+        __syncthreads();
+        unsigned long long pos = base_s + before + excl;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t x = words[k];
+            while (x) {
+                const int b = __ffs(x) - 1;
+                x &= x - 1;
+                list[pos++] = (int32_t)((w0 + k) * 32 + b);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Bottom-up step over a compacted list of the vertices still to find: one
+// lane per vertex, so a sparse layer keeps every lane busy. Same probe and
+// warp-cooperative tail as bu_kernel (first frontier neighbour in CSR
+// order); a found vertex sets its next and visited bits with atomicOr, since
+// no warp owns its word here.
+__global__ void __launch_bounds__(kBlock) bu_list_kernel(
+    const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
+    const int32_t *__restrict__ list, const unsigned long long *count,
+    uint32_t *__restrict__ visited, const uint32_t *__restrict__ front,
+    uint32_t *__restrict__ next_bm, int32_t *__restrict__ parent, int32_t *__restrict__ level,
+    int32_t new_level, int probe, unsigned long long *slot_next, int64_t *zero_slot) {
+    if (blockIdx.x == 0 && threadIdx.x < kFields) zero_slot[threadIdx.x] = 0;
+    const int64_t cnt = (int64_t)*count;
+    const unsigned lane = lane_id();
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t my_nf = 0, my_mf = 0, my_ex = 0;
+    for (int64_t base = gw * 32; base < cnt; base += tw * 32) {
+        const int64_t i = base + lane;
+        const bool have = i < cnt;
+        int32_t v = 0;
+        const int32_t *row = idx;
+        int deg = 0, ex = 0;
+        if (have) {
+            v = list[i];
+            const int64_t b = off[v];
+            row = idx + b;
+            deg = (int)(off[v + 1] - b);
+        }
+        bool found = false;
+        int32_t p = -1;
+        for (int p0 = 0; p0 < probe; p0 += 4) {
+            int32_t cand[4];
+            bool any = false;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int q = p0 + t;
+                const bool ok = have && !found && q < probe && q < deg;
+                cand[t] = ok ? __ldg(row + q) : -1;
+                any = any || ok;
+            }
+            if (!any) break;
+            uint32_t fw[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) fw[t] = cand[t] >= 0 ? __ldg(front + (cand[t] >> 5)) : 0u;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if (!found && cand[t] >= 0) {
+                    ++ex;
+                    if ((fw[t] >> (cand[t] & 31)) & 1u) {
+                        found = true;
+                        p = cand[t];
+                    }
+                }
+            }
+        }
+        unsigned pend = __ballot_sync(0xffffffffu, have && !found && probe < deg);
+        while (pend) {
+            const int L = __ffs(pend) - 1;
+            pend &= pend - 1;
+            const int32_t *lrow =
+                (const int32_t *)__shfl_sync(0xffffffffu, (unsigned long long)row, L);
+            const int ld = __shfl_sync(0xffffffffu, deg, L);
+            bool hit_any = false;
+            for (int q0 = probe; q0 < ld; q0 += 64) {
+                int32_t uu[2];
+                bool hit[2];
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    const int q = q0 + 32 * t + (int)lane;
+                    uu[t] = q < ld ? __ldg(lrow + q) : -1;
+                }
+#pragma unroll
+                for (int t = 0; t < 2; ++t)
+                    hit[t] = uu[t] >= 0 && ((__ldg(front + (uu[t] >> 5)) >> (uu[t] & 31)) & 1u);
+                const unsigned h0 = __ballot_sync(0xffffffffu, hit[0]);
+                const unsigned h1 = __ballot_sync(0xffffffffu, hit[1]);
+                if (h0 | h1) {
+                    const int t = h0 ? 0 : 1;
+                    const int first = __ffs(h0 ? h0 : h1) - 1;
+                    const int32_t pu = __shfl_sync(0xffffffffu, t ? uu[1] : uu[0], first);
+                    if ((int)lane == L) {
+                        found = true;
+                        p = pu;
+                        ex += (q0 - probe) + 32 * t + first + 1;
+                    }
+                    hit_any = true;
+                    break;
+                }
+            }
+            if (!hit_any && (int)lane == L) ex += ld - probe;
+        }
+        if (found) {
+            const uint32_t bit = 1u << (v & 31);
+            parent[v] = p;
+            level[v] = new_level;
+            atomicOr(next_bm + (v >> 5), bit);
+            atomicOr(visited + (v >> 5), bit);
+            my_mf += deg;
+            my_nf += 1;
+        }
+        my_ex += ex;
+    }
+    block_add3(my_nf, my_mf, my_ex, slot_next + T_NF, slot_next + T_MF, slot_next + T_EXAM);
+}
+
+__global__ void count_bits_kernel(const uint32_t *__restrict__ bits, int64_t nw,
+                                  unsigned long long *count) {
+    int64_t c = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nw; w += stride)
+        c += __popc(bits[w]);
+    c = warp_sum(c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, (unsigned long long)c);
+}
+
 constexpr auto BU1 = bu_kernel<1, 4, false>;
 constexpr auto BU2 = bu_kernel<2, 4, false>;
 constexpr auto BU4 = bu_kernel<4, 2, false>;
@@ -638,6 +826,8 @@ bool config_ok(const bfs_config &c) {
     if (c.bu_words != 1 && c.bu_words != 2 && c.bu_words != 4) return false;
     if (c.td_claim != 0 && c.td_claim != 1) return false;
     if (c.bu_head != 0 && c.bu_head != 1) return false;
+    if (c.prune_components != 0 && c.prune_components != 1) return false;
+    if (c.bu_list_percent < 0 || c.bu_list_percent > 100) return false;
     return true;
 }
 
@@ -671,6 +861,7 @@ void free_graph(bfs_graph *g) {
     cudaFree(g->visited);
     cudaFree(g->base_vis);
     cudaFree(g->head);
+    cudaFree(g->comp_in);
     cudaFree(g->bm_a);
     cudaFree(g->bm_b);
     cudaFree(g->q_a);
@@ -702,6 +893,8 @@ extern "C" BFS_API void bfs_config_default(bfs_config *c) {
     c->timing = 0;
     c->bu_words = 4;
     c->bu_head = 0;
+    c->prune_components = 0;
+    c->bu_list_percent = 10;
 }
 
 extern "C" BFS_API bfs_status bfs_graph_create(const int64_t *offsets, const int32_t *indices,
@@ -779,6 +972,17 @@ extern "C" BFS_API bfs_status bfs_graph_create(const int64_t *offsets, const int
     }
     base_vis_kernel<<<grid_cap(g->nw_pad, kBlock, 8), kBlock>>>(g->off, n, g->nw_pad, g->base_vis);
     count_launch();
+    {  // degree-0 vertices = set bits of base_vis minus the padding bits
+        unsigned long long *cnt = nullptr, hc = 0;
+        GB_CKG(cudaMalloc(&cnt, 8));
+        cudaMemset(cnt, 0, 8);
+        count_bits_kernel<<<grid_cap(g->nw_pad, kBlock, 8), kBlock>>>(g->base_vis, g->nw_pad, cnt);
+        count_launch();
+        cudaError_t e = cudaMemcpy(&hc, cnt, 8, cudaMemcpyDeviceToHost);
+        cudaFree(cnt);
+        GB_CKG(e);
+        g->deg0 = (int64_t)hc - (g->nw_pad * 32 - n);
+    }
     GB_CKG(cudaGetLastError());
     GB_CKG(cudaDeviceSynchronize());
     GB_CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->bu_blocks_per_sm[0], BU1, kBlock, 0));
@@ -788,6 +992,8 @@ extern "C" BFS_API bfs_status bfs_graph_create(const int64_t *offsets, const int
     GB_CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->bu_blocks_per_sm[4], BU2H, kBlock, 0));
     GB_CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->bu_blocks_per_sm[5], BU4H, kBlock, 0));
     GB_CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->td_blocks_per_sm, td_kernel, kBlock, 0));
+    GB_CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->bu_list_blocks_per_sm, bu_list_kernel,
+                                                         kBlock, 0));
 #undef GB_CKG
     *out = g;
     return BFS_OK;
@@ -865,16 +1071,42 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
         return g->events[i];
     };
 
+    if (cfg.prune_components && g->comp_rep < 0) {
+        // The component of the highest-degree vertex, found once by one
+        // traversal without pruning, kept as a bitmap.
+        unsigned long long *best = nullptr;
+        unsigned long long hb = 0;
+        GB_CK(cudaMallocAsync(&best, 8, st));
+        GB_CK(cudaMemsetAsync(best, 0, 8, st));
+        GB_LAUNCH(max_degree_kernel, grid_cap(n, kBlock, 8), kBlock, 0, st, g->off, n, best);
+        GB_CK(cudaMemcpyAsync(&hb, best, 8, cudaMemcpyDeviceToHost, st));
+        GB_CK(cudaFreeAsync(best, st));
+        GB_CK(cudaStreamSynchronize(st));
+        const int32_t rep = (int32_t)(0xffffffffull - (hb & 0xffffffffull));
+        if (!g->comp_in) GB_CK(cudaMalloc(&g->comp_in, (size_t)g->nw_pad * 4));
+        if (!g->level_scratch) GB_CK(cudaMalloc(&g->level_scratch, (size_t)n * 4));
+        if (!g->parent_scratch) GB_CK(cudaMalloc(&g->parent_scratch, (size_t)n * 4));
+        const bfs_config saved = g->cfg;
+        g->cfg.prune_components = 0;
+        g->cfg.timing = 0;
+        const bfs_status s = bfs_run(g, rep, g->level_scratch, g->parent_scratch, stream);
+        g->cfg = saved;
+        if (s != BFS_OK) return s;
+        GB_LAUNCH(reached_bits_kernel, grid_cap(g->nw_pad, kBlock, 8), kBlock, 0, st,
+                  g->level_scratch, n, g->nw_pad, g->comp_in);
+        GB_CK(cudaStreamSynchronize(st));
+        g->comp_rep = rep;
+    }
     if (cfg.bu_head && !g->head) {  // head records are built on first use
-        GB_CK(cudaMalloc(&g->head, (size_t)n * sizeof(int4)));
+        GB_CK(cudaMalloc(&g->head, (size_t)n * sizeof(int2)));
         GB_LAUNCH(head_kernel, grid_cap(n, kBlock, 8), kBlock, 0, st, g->off, g->idx, n, g->head);
     }
     g->last.clear();
     uint32_t *front = g->bm_a, *next = g->bm_b;
     int32_t *q_cur = g->q_a, *q_next = g->q_b;
     GB_LAUNCH(init_kernel, grid_cap(std::max(n, g->nw_pad), kBlock, 8), kBlock, 0, st, n,
-              g->nw_pad, root, g->off, g->base_vis, level, parent, g->visited, front, q_cur,
-              g->trace);
+              g->nw_pad, root, g->off, g->base_vis, cfg.prune_components ? g->comp_in : nullptr,
+              level, parent, g->visited, front, q_cur, g->trace);
     GB_CK(cudaMemcpyAsync(g->h_slot, g->trace, kFields * 8, cudaMemcpyDeviceToHost, st));
     GB_CK(cudaStreamSynchronize(st));
     int64_t n_f = 1, m_f = g->h_slot[T_MF];
@@ -944,11 +1176,26 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
             have_queue = queue_mode != 0;
         } else {
             if (timing) GB_CK(cudaEventRecord(event(e0 + 1), st));
-            decltype(BU1) const kernels[6] = {BU1, BU2, BU4, BU1H, BU2H, BU4H};
-            auto bu = kernels[bsel];
-            GB_LAUNCH(bu, bu_grid, kBlock, 0, st, g->off, g->idx, g->head, g->nw_pad, g->visited, front,
-                      next, parent, level, d + 1, cfg.bu_probe, (unsigned long long *)slot_next,
-                      slot_zero);
+            // vertices still to find: unvisited and of degree > 0
+            const int64_t active = n_u - g->deg0;
+            if (cfg.bu_list_percent > 0 && active * 100 <= (int64_t)cfg.bu_list_percent * n) {
+                // sparse layer: a compacted list of them, one lane each
+                GB_CK(cudaMemsetAsync(next, 0, (size_t)g->nw_pad * 4, st));
+                GB_LAUNCH(unvisited_list_kernel, grid_cap(g->nw, kBlock * 4, 8), kBlock, 0, st,
+                          g->visited, g->nw, q_next, (unsigned long long *)(slot_cur + T_ULIST));
+                GB_LAUNCH(bu_list_kernel,
+                          grid_cap((active + 31) / 32, kBlock / 32, g->bu_list_blocks_per_sm),
+                          kBlock, 0, st, g->off, g->idx, q_next,
+                          (const unsigned long long *)(slot_cur + T_ULIST), g->visited, front,
+                          next, parent, level, d + 1, cfg.bu_probe,
+                          (unsigned long long *)slot_next, slot_zero);
+            } else {
+                decltype(BU1) const kernels[6] = {BU1, BU2, BU4, BU1H, BU2H, BU4H};
+                auto bu = kernels[bsel];
+                GB_LAUNCH(bu, bu_grid, kBlock, 0, st, g->off, g->idx, g->head, g->nw_pad,
+                          g->visited, front, next, parent, level, d + 1, cfg.bu_probe,
+                          (unsigned long long *)slot_next, slot_zero);
+            }
             have_queue = false;
         }
         if (timing) GB_CK(cudaEventRecord(event(e0 + 2), st));
@@ -1083,7 +1330,8 @@ extern "C" BFS_API bfs_status bfs_run_noalloc(const int64_t *offsets, const int3
     GB_LAUNCH(base_vis_kernel, grid_cap(nw_pad, kBlock, 8), kBlock, 0, st, offsets, n, nw_pad,
               base_vis);
     GB_LAUNCH(init_kernel, grid_cap(std::max(n, nw_pad), kBlock, 8), kBlock, 0, st, n, nw_pad,
-              root, offsets, base_vis, level_out, parent_out, visited, front, q_cur, trace);
+              root, offsets, base_vis, nullptr, level_out, parent_out, visited, front, q_cur,
+              trace);
     int64_t h[kFields];
     GB_CK(cudaMemcpyAsync(h, trace, sizeof h, cudaMemcpyDeviceToHost, st));
     GB_CK(cudaStreamSynchronize(st));

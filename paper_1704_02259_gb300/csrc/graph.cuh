@@ -11,10 +11,11 @@ namespace gbfs {
 
 constexpr int kRing = 64;  // trace ring slots (layers)
 constexpr int kFields = 8;
-enum TraceField { T_NF = 0, T_MF = 1, T_EXAM = 2, T_CONV = 3, T_BIG = 4 };
+enum TraceField { T_NF = 0, T_MF = 1, T_EXAM = 2, T_CONV = 3, T_BIG = 4, T_ULIST = 5 };
 constexpr int kBlock = 256;
 constexpr int kBigBatch = 1024;
 constexpr int64_t kQueueModeMaxEdges = 1 << 18;
+constexpr int kTdK = 4;  // edges per lane in flight in the warp and grid top-down paths
 
 }  // namespace gbfs
 
@@ -28,7 +29,10 @@ struct bfs_graph {
     int64_t *off_own = nullptr;
     int32_t *idx_own = nullptr;
     uint32_t *visited = nullptr, *bm_a = nullptr, *bm_b = nullptr;
-    int4 *head = nullptr;          // {first three neighbours (-1 if none), degree}
+    int2 *head = nullptr;          // {first neighbour (-1 if none), degree}
+    uint32_t *comp_in = nullptr;   // vertices in the component of comp_rep
+    int32_t comp_rep = -1;         // highest-degree vertex; -1 = not built yet
+    int64_t deg0 = 0;              // vertices of degree 0
     uint32_t *base_vis = nullptr;  // bits that start every traversal visited:
                                    // degree-0 vertices and ids past n
     int32_t *q_a = nullptr, *q_b = nullptr, *big = nullptr;
@@ -41,6 +45,7 @@ struct bfs_graph {
     std::vector<cudaEvent_t> events;
     int bu_blocks_per_sm[6] = {1, 1, 1, 1, 1, 1};  // BU1, BU2, BU4, BU1H, BU2H, BU4H
     int td_blocks_per_sm = 1;
+    int bu_list_blocks_per_sm = 1;
     MsState *ms = nullptr;
 };
 

@@ -28,9 +28,17 @@ def check_run(o_off, o_idx, graph, root, policy=None, forced=None, alpha=14.0, b
     st = graph.stats()
     L = st.layers
     assert [x["direction"] for x in L] == dirs.tolist()
+    # with component pruning the bottom-up step skips vertices outside the
+    # root's component, so only its edges-examined count may be smaller
+    pruned = graph.config.prune_components
     for d, x in enumerate(L):
-        assert (x["n_f"], x["m_f"], x["n_u"], x["m_u"], x["examined"], x["found"]) == \
-            tuple(int(t) for t in tr[d]), f"layer {d}"
+        got = (x["n_f"], x["m_f"], x["n_u"], x["m_u"], x["examined"], x["found"])
+        exp = tuple(int(t) for t in tr[d])
+        if pruned and x["direction"] == 1:
+            assert got[:4] + got[5:] == exp[:4] + exp[5:], f"layer {d}"
+            assert got[4] <= exp[4], f"layer {d}"
+        else:
+            assert got == exp, f"layer {d}"
         if x["direction"] == 1:
             nxt = ref == d + 1
             assert np.array_equal(pa[nxt], h_pa[nxt]), f"bottom-up parents, layer {d}"
@@ -51,7 +59,8 @@ FORCED = {"td": [0], "bu": [1], "alt": [0, 1] * 32, "alt2": [1, 0] * 32,
 @pytest.mark.parametrize("name", ["path", "cycle", "star", "grid", "hypercube", "complete",
                                   "union", "single", "ragged"])
 @pytest.mark.parametrize("pat", list(FORCED))
-def test_closed_form_graphs_forced_directions(name, pat):
+@pytest.mark.parametrize("prune", [0, 1])
+def test_closed_form_graphs_forced_directions(name, pat, prune):
     if name == "path":
         n, (s, d) = 77, inputs.path_edges(77)
     elif name == "cycle":
@@ -73,7 +82,8 @@ def test_closed_form_graphs_forced_directions(name, pat):
         n = 1000 + 13
         s, d = inputs.random_edges(n, 3 * n, 5)
     forced = FORCED[pat]
-    o_off, o_idx, g = make(n, s, d, forced=forced)
+    o_off, o_idx, g = make(n, s, d, forced=forced, prune_components=prune,
+                           bu_list_percent=100 if prune else 0)
     for r in sorted({0, n // 2, n - 1}):
         check_run(o_off, o_idx, g, r, forced=forced)
 
@@ -89,7 +99,8 @@ def test_policies_on_skewed_graphs(seed, policy, claim):
         s, d = oracle.gen_edges(oracle.RMAT, 12 + seed // 2, 8, seed)
         n = 1 << (12 + seed // 2)
     o_off, o_idx, g = make(n, s, d, policy=policy, td_claim=claim, bu_words=[1, 2, 4][seed % 3],
-                           bu_head=(seed // 3 + claim) % 2)
+                           bu_head=(seed // 3 + claim) % 2, prune_components=(seed + claim) % 2,
+                           bu_list_percent=[0, 10, 100][(seed + claim) % 3])
     for r in oracle.sample_roots(o_off, n, seed, 4):
         check_run(o_off, o_idx, g, int(r), policy=policy)
 
@@ -109,7 +120,9 @@ def test_degree_bin_boundaries(deg, pat):
                 dict(forced=forced, bu_probe=1), dict(forced=forced, bu_probe=33),
                 dict(forced=forced, bu_words=1, bu_probe=5),
                 dict(forced=forced, bu_words=4, bu_probe=7, td_claim=1),
-                dict(forced=forced, bu_head=0), dict(forced=forced, bu_head=1, bu_probe=2),
+                dict(forced=forced, bu_head=0, prune_components=0),
+                dict(forced=forced, bu_list_percent=100, bu_probe=3),
+                dict(forced=forced, bu_head=1, bu_probe=2),
                 dict(forced=forced, bu_head=1, bu_probe=4, bu_words=2)]:
         o_off, o_idx, g = make(n, s, d, **cfg)
         for r in [0, 1, n - 1, deg // 2]:
