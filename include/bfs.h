@@ -207,7 +207,9 @@ BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level_out, int32
  * e_f (m_f), and the unvisited vertex / edge counts n_u, m_u.             */
 typedef struct bfs_layer_stats {
     int32_t direction;  /* 0 = top-down, 1 = bottom-up                          */
-    int32_t converted;  /* 1 = the frontier bitmap was turned into a queue     */
+    int32_t converted;  /* top-down: 1 = the frontier bitmap was turned into a
+                           queue; bottom-up: 2 = the layer ran on the compacted
+                           list of vertices still to find (bu_list_percent)   */
     int64_t n_f;        /* vertices in the frontier                            */
     int64_t m_f;        /* sum of their degrees                                */
     int64_t n_u;        /* vertices not yet visited                            */

@@ -1180,6 +1180,7 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
             const int64_t active = n_u - g->deg0;
             if (cfg.bu_list_percent > 0 && active * 100 <= (int64_t)cfg.bu_list_percent * n) {
                 // sparse layer: a compacted list of them, one lane each
+                ls.converted = 2;
                 GB_CK(cudaMemsetAsync(next, 0, (size_t)g->nw_pad * 4, st));
                 GB_LAUNCH(unvisited_list_kernel, grid_cap(g->nw, kBlock * 4, 8), kBlock, 0, st,
                           g->visited, g->nw, q_next, (unsigned long long *)(slot_cur + T_ULIST));
