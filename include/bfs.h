@@ -156,7 +156,14 @@ typedef struct bfs_config {
                                 > 0) run on a compacted list of those vertices,
                                 one thread each, instead of one warp per
                                 bitmap word; 0 = never                        */
-    int32_t reserved[3];
+    int32_t device_loop;     /* 1 = run all layers in one cooperative launch
+                                whose blocks take the Alg. 3 decision on the
+                                device, between bounded grid barriers (no host
+                                round trip per layer; per-layer times are not
+                                recorded); 0 = host loop; 2 (default) = the
+                                device loop for n <= 2^23, where the host round
+                                trips weigh most, the host loop above         */
+    int32_t reserved[2];
 } bfs_config;
 
 /* Fills `cfg` with the defaults (edge policy, alpha 14, beta 24, ...). */

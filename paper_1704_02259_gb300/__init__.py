@@ -43,7 +43,7 @@ class Config(ctypes.Structure):
                 ("timing", ctypes.c_int32), ("bu_words", ctypes.c_int32),
                 ("td_claim", ctypes.c_int32), ("bu_head", ctypes.c_int32),
                 ("prune_components", ctypes.c_int32), ("bu_list_percent", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("device_loop", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class LayerStats(ctypes.Structure):

@@ -38,6 +38,14 @@
 namespace gbfs {
 namespace {
 
+// Read-only loads of data that is constant within one launch of the
+// host-driven loop but written by other blocks earlier in a persistent launch.
+template <bool CO, typename T>
+__device__ __forceinline__ T ldro(const T *p) {
+    if constexpr (CO) return __ldcg(p);
+    else return __ldg(p);
+}
+
 __device__ __forceinline__ int64_t deg_of(const int64_t *__restrict__ off, int32_t v) {
     return off[v + 1] - off[v];
 }
@@ -246,7 +254,8 @@ __device__ __forceinline__ void td_visit(const TdArgs &a, const bool (&valid)[K]
 // list (td_big_kernel), >= warp_deg are expanded one at a time by the whole
 // warp (64 edges per round), the rest are gathered together: a warp-wide
 // exclusive scan of their degrees gives each lane two edges per round.
-__global__ void __launch_bounds__(kBlock) td_kernel(TdArgs a, const int32_t *__restrict__ q,
+template <bool CO>
+__device__ __forceinline__ void td_phase(TdArgs a, const int32_t *__restrict__ q,
                                                     int64_t qlen, int per_warp,
                                                     int32_t *__restrict__ big,
                                                     unsigned long long *big_count,
@@ -263,7 +272,7 @@ __global__ void __launch_bounds__(kBlock) td_kernel(TdArgs a, const int32_t *__r
         int32_t u = 0;
         int64_t beg = 0, end = 0;
         if (have) {
-            u = q[i];
+            u = ld<CO>(q + i);
             beg = a.off[u];
             end = a.off[u + 1];
         }
@@ -326,18 +335,29 @@ __global__ void __launch_bounds__(kBlock) td_kernel(TdArgs a, const int32_t *__r
     block_add3(my_mf, a.queue_mode ? 0 : my_nf, 0, next_mf, a.next_count, nullptr);
 }
 
+__global__ void __launch_bounds__(kBlock) td_kernel(TdArgs a, const int32_t *__restrict__ q,
+                                                    int64_t qlen, int per_warp,
+                                                    int32_t *__restrict__ big,
+                                                    unsigned long long *big_count,
+                                                    unsigned long long *next_mf, int warp_deg,
+                                                    int64_t grid_deg, int64_t *zero_slot) {
+    td_phase<false>(a, q, qlen, per_warp, big, big_count, next_mf, warp_deg, grid_deg, zero_slot);
+}
+
+
 // The edges of all big vertices, spread evenly over the grid: batches of
 // kBigBatch vertices, an exclusive scan of their degrees in shared memory,
 // then a grid-stride walk over the batch's edge range (64 edges per warp and
 // round) with a binary search for the owning vertex.
-__global__ void __launch_bounds__(kBlock) td_big_kernel(TdArgs a, const int32_t *__restrict__ big,
+template <bool CO>
+__device__ __forceinline__ void td_big_phase(TdArgs a, const int32_t *__restrict__ big,
                                                         const unsigned long long *big_count,
                                                         unsigned long long *next_mf) {
     __shared__ long long pre[kBigBatch + 1];
     __shared__ long long beg_s[kBigBatch];
     __shared__ int32_t u_s[kBigBatch];
     __shared__ long long wtot[kBlock / 32];
-    const int64_t cnt = (int64_t)*big_count;
+    const int64_t cnt = (int64_t)ld<CO>(big_count);
     const unsigned lane = lane_id(), w = threadIdx.x >> 5;
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -352,7 +372,7 @@ __global__ void __launch_bounds__(kBlock) td_big_kernel(TdArgs a, const int32_t 
             const int t = threadIdx.x * per + k;
             long long d = 0;
             if (t < nb) {
-                const int32_t u = big[b0 + t];
+                const int32_t u = ld<CO>(big + b0 + t);
                 u_s[t] = u;
                 beg_s[t] = a.off[u];
                 d = a.off[u + 1] - beg_s[t];
@@ -379,6 +399,19 @@ __global__ void __launch_bounds__(kBlock) td_big_kernel(TdArgs a, const int32_t 
         __syncthreads();
         const long long total = pre[kBigBatch];
         for (long long g0 = gw * 32 * kTdK; g0 < total; g0 += tw * 32 * kTdK) {
+            // Owner of the round's first edge by one binary search (the last
+            // j in [0, nb) with pre[j] <= g0), then each lane walks forward:
+            // every listed vertex has at least 4 * td_warp_degree edges, so a
+            // round's 32 * kTdK edges cross at most a couple of row ends.
+            int lo = 0;
+            {
+                int hi = nb;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (pre[mid] <= g0) lo = mid;
+                    else hi = mid;
+                }
+            }
             bool ok[kTdK];
             int32_t uu[kTdK], vv[kTdK];
 #pragma unroll
@@ -388,12 +421,7 @@ __global__ void __launch_bounds__(kBlock) td_big_kernel(TdArgs a, const int32_t 
                 uu[k] = 0;
                 vv[k] = 0;
                 if (ok[k]) {
-                    int lo = 0, hi = nb;  // last j in [0, nb) with pre[j] <= g
-                    while (hi - lo > 1) {
-                        const int mid = (lo + hi) >> 1;
-                        if (pre[mid] <= g) lo = mid;
-                        else hi = mid;
-                    }
+                    while (lo + 1 < nb && pre[lo + 1] <= g) ++lo;
                     uu[k] = u_s[lo];
                     vv[k] = a.idx[beg_s[lo] + (g - pre[lo])];
                 }
@@ -404,6 +432,13 @@ __global__ void __launch_bounds__(kBlock) td_big_kernel(TdArgs a, const int32_t 
     }
     block_add3(my_mf, a.queue_mode ? 0 : my_nf, 0, next_mf, a.next_count, nullptr);
 }
+
+__global__ void __launch_bounds__(kBlock) td_big_kernel(TdArgs a, const int32_t *__restrict__ big,
+                                                        const unsigned long long *big_count,
+                                                        unsigned long long *next_mf) {
+    td_big_phase<false>(a, big, big_count, next_mf);
+}
+
 
 // Bottom-up step (Alg. 2 with the Sec. 5.1 structure). Lane-per-vertex,
 // warp-per-word: a warp takes a chunk of 32 consecutive bitmap words (their
@@ -421,8 +456,8 @@ __global__ void __launch_bounds__(kBlock) td_big_kernel(TdArgs a, const int32_t 
 // first position and the degree come from the vertex's 8-byte head record
 // (one coalesced load per lane); the row bound is read only for rows longer
 // than one whose first neighbour is not in the frontier.
-template <int W, int CH, bool HEAD>
-__global__ void __launch_bounds__(kBlock, 4) bu_kernel(
+template <int W, int CH, bool HEAD, bool CO>
+__device__ __forceinline__ void bu_phase(
     const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
     const int2 *__restrict__ head, int64_t nw_pad,
     uint32_t *__restrict__ visited, const uint32_t *__restrict__ front,
@@ -435,7 +470,7 @@ __global__ void __launch_bounds__(kBlock, 4) bu_kernel(
     const int64_t nchunks = nw_pad >> 5;
     int64_t my_nf = 0, my_mf = 0, my_ex = 0;
     for (int64_t c = gw; c < nchunks; c += tw) {
-        const uint32_t vis_lane = visited[c * 32 + lane];
+        const uint32_t vis_lane = ld<CO>(visited + c * 32 + lane);
         uint32_t *const next_c = next_bm + c * 32;
         uint32_t *const vis_c = visited + c * 32;
         const int64_t v_c = c * 1024 + lane;
@@ -472,7 +507,7 @@ __global__ void __launch_bounds__(kBlock, 4) bu_kernel(
                 }
                 uint32_t fw[W];
 #pragma unroll
-                for (int k = 0; k < W; ++k) fw[k] = h[k].x >= 0 ? __ldg(front + (h[k].x >> 5)) : 0u;
+                for (int k = 0; k < W; ++k) fw[k] = h[k].x >= 0 ? ldro<CO>(front + (h[k].x >> 5)) : 0u;
 #pragma unroll
                 for (int k = 0; k < W; ++k) {
                     if (h[k].x >= 0) {
@@ -521,7 +556,7 @@ __global__ void __launch_bounds__(kBlock, 4) bu_kernel(
                 for (int k = 0; k < W; ++k)
 #pragma unroll
                     for (int t = 0; t < CH; ++t)
-                        fw[k][t] = cand[k][t] >= 0 ? __ldg(front + (cand[k][t] >> 5)) : 0u;
+                        fw[k][t] = cand[k][t] >= 0 ? ldro<CO>(front + (cand[k][t] >> 5)) : 0u;
 #pragma unroll
                 for (int k = 0; k < W; ++k) {
 #pragma unroll
@@ -556,7 +591,7 @@ __global__ void __launch_bounds__(kBlock, 4) bu_kernel(
                         }
 #pragma unroll
                         for (int t = 0; t < 2; ++t)
-                            hit[t] = uu[t] >= 0 && ((__ldg(front + (uu[t] >> 5)) >> (uu[t] & 31)) & 1u);
+                            hit[t] = uu[t] >= 0 && ((ldro<CO>(front + (uu[t] >> 5)) >> (uu[t] & 31)) & 1u);
                         const unsigned h0 = __ballot_sync(0xffffffffu, hit[0]);
                         const unsigned h1 = __ballot_sync(0xffffffffu, hit[1]);
                         if (h0 | h1) {
@@ -596,10 +631,22 @@ __global__ void __launch_bounds__(kBlock, 4) bu_kernel(
     block_add3(my_nf, my_mf, my_ex, slot_next + T_NF, slot_next + T_MF, slot_next + T_EXAM);
 }
 
+template <int W, int CH, bool HEAD>
+__global__ void __launch_bounds__(kBlock, 4) bu_kernel(
+    const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
+    const int2 *__restrict__ head, int64_t nw_pad,
+    uint32_t *__restrict__ visited, const uint32_t *__restrict__ front,
+    uint32_t *__restrict__ next_bm, int32_t *__restrict__ parent, int32_t *__restrict__ level,
+    int32_t new_level, int probe, unsigned long long *slot_next, int64_t *zero_slot) {
+    bu_phase<W, CH, HEAD, false>(off, idx, head, nw_pad, visited, front, next_bm, parent, level, new_level, probe, slot_next, zero_slot);
+}
+
+
 // Unvisited bitmap -> list of the vertices still to find (bits of ~visited;
 // degree-0 vertices and ids past n are set in visited and so never listed).
 // Same block scan as b2q_kernel.
-__global__ void __launch_bounds__(kBlock) unvisited_list_kernel(const uint32_t *__restrict__ vis,
+template <bool CO>
+__device__ __forceinline__ void unvisited_list_phase(const uint32_t *__restrict__ vis,
                                                                 int64_t nw,
                                                                 int32_t *__restrict__ list,
                                                                 unsigned long long *count) {
@@ -612,7 +659,7 @@ __global__ void __launch_bounds__(kBlock) unvisited_list_kernel(const uint32_t *
         int c = 0;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            words[k] = (w0 + k < nw) ? ~vis[w0 + k] : 0u;
+            words[k] = (w0 + k < nw) ? ~ld<CO>(vis + w0 + k) : 0u;
             c += __popc(words[k]);
         }
         int tot;
@@ -640,19 +687,28 @@ __global__ void __launch_bounds__(kBlock) unvisited_list_kernel(const uint32_t *
     }
 }
 
+__global__ void __launch_bounds__(kBlock) unvisited_list_kernel(const uint32_t *__restrict__ vis,
+                                                                int64_t nw,
+                                                                int32_t *__restrict__ list,
+                                                                unsigned long long *count) {
+    unvisited_list_phase<false>(vis, nw, list, count);
+}
+
+
 // Bottom-up step over a compacted list of the vertices still to find: one
 // lane per vertex, so a sparse layer keeps every lane busy. Same probe and
 // warp-cooperative tail as bu_kernel (first frontier neighbour in CSR
 // order); a found vertex sets its next and visited bits with atomicOr, since
 // no warp owns its word here.
-__global__ void __launch_bounds__(kBlock) bu_list_kernel(
+template <bool CO>
+__device__ __forceinline__ void bu_list_phase(
     const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
     const int32_t *__restrict__ list, const unsigned long long *count,
     uint32_t *__restrict__ visited, const uint32_t *__restrict__ front,
     uint32_t *__restrict__ next_bm, int32_t *__restrict__ parent, int32_t *__restrict__ level,
     int32_t new_level, int probe, unsigned long long *slot_next, int64_t *zero_slot) {
     if (blockIdx.x == 0 && threadIdx.x < kFields) zero_slot[threadIdx.x] = 0;
-    const int64_t cnt = (int64_t)*count;
+    const int64_t cnt = (int64_t)ld<CO>(count);
     const unsigned lane = lane_id();
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -664,7 +720,7 @@ __global__ void __launch_bounds__(kBlock) bu_list_kernel(
         const int32_t *row = idx;
         int deg = 0, ex = 0;
         if (have) {
-            v = list[i];
+            v = ld<CO>(list + i);
             const int64_t b = off[v];
             row = idx + b;
             deg = (int)(off[v + 1] - b);
@@ -684,7 +740,7 @@ __global__ void __launch_bounds__(kBlock) bu_list_kernel(
             if (!any) break;
             uint32_t fw[4];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) fw[t] = cand[t] >= 0 ? __ldg(front + (cand[t] >> 5)) : 0u;
+            for (int t = 0; t < 4; ++t) fw[t] = cand[t] >= 0 ? ldro<CO>(front + (cand[t] >> 5)) : 0u;
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 if (!found && cand[t] >= 0) {
@@ -714,7 +770,7 @@ __global__ void __launch_bounds__(kBlock) bu_list_kernel(
                 }
 #pragma unroll
                 for (int t = 0; t < 2; ++t)
-                    hit[t] = uu[t] >= 0 && ((__ldg(front + (uu[t] >> 5)) >> (uu[t] & 31)) & 1u);
+                    hit[t] = uu[t] >= 0 && ((ldro<CO>(front + (uu[t] >> 5)) >> (uu[t] & 31)) & 1u);
                 const unsigned h0 = __ballot_sync(0xffffffffu, hit[0]);
                 const unsigned h1 = __ballot_sync(0xffffffffu, hit[1]);
                 if (h0 | h1) {
@@ -746,6 +802,16 @@ __global__ void __launch_bounds__(kBlock) bu_list_kernel(
     block_add3(my_nf, my_mf, my_ex, slot_next + T_NF, slot_next + T_MF, slot_next + T_EXAM);
 }
 
+__global__ void __launch_bounds__(kBlock) bu_list_kernel(
+    const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
+    const int32_t *__restrict__ list, const unsigned long long *count,
+    uint32_t *__restrict__ visited, const uint32_t *__restrict__ front,
+    uint32_t *__restrict__ next_bm, int32_t *__restrict__ parent, int32_t *__restrict__ level,
+    int32_t new_level, int probe, unsigned long long *slot_next, int64_t *zero_slot) {
+    bu_list_phase<false>(off, idx, list, count, visited, front, next_bm, parent, level, new_level, probe, slot_next, zero_slot);
+}
+
+
 __global__ void count_bits_kernel(const uint32_t *__restrict__ bits, int64_t nw,
                                   unsigned long long *count) {
     int64_t c = 0;
@@ -765,7 +831,8 @@ constexpr auto BU4H = bu_kernel<4, 2, true>;
 
 // Frontier bitmap -> queue: each thread takes 4 consecutive words, a block
 // scan orders the set bits, one atomicAdd per block reserves queue space.
-__global__ void __launch_bounds__(kBlock) b2q_kernel(const uint32_t *__restrict__ bm, int64_t nw,
+template <bool CO>
+__device__ __forceinline__ void b2q_phase(const uint32_t *__restrict__ bm, int64_t nw,
                                                      int32_t *__restrict__ q,
                                                      unsigned long long *count) {
     __shared__ int wtot[kBlock / 32];
@@ -777,7 +844,7 @@ __global__ void __launch_bounds__(kBlock) b2q_kernel(const uint32_t *__restrict_
         int c = 0;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            words[k] = (w0 + k < nw) ? bm[w0 + k] : 0u;
+            words[k] = (w0 + k < nw) ? ld<CO>(bm + w0 + k) : 0u;
             c += __popc(words[k]);
         }
         int tot;
@@ -805,6 +872,13 @@ __global__ void __launch_bounds__(kBlock) b2q_kernel(const uint32_t *__restrict_
     }
 }
 
+__global__ void __launch_bounds__(kBlock) b2q_kernel(const uint32_t *__restrict__ bm, int64_t nw,
+                                                     int32_t *__restrict__ q,
+                                                     unsigned long long *count) {
+    b2q_phase<false>(bm, nw, q, count);
+}
+
+
 __global__ void validate_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
                                 int64_t n, int64_t nnz, int *bad) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -828,20 +902,239 @@ bool config_ok(const bfs_config &c) {
     if (c.bu_head != 0 && c.bu_head != 1) return false;
     if (c.prune_components != 0 && c.prune_components != 1) return false;
     if (c.bu_list_percent < 0 || c.bu_list_percent > 100) return false;
+    if (c.device_loop < 0 || c.device_loop > 2) return false;
     return true;
 }
 
 // Alg. 3 switch, read as hysteresis (Table 2 layer 5 rules out the
 // state-free reading). Returns 1 for bottom-up.
-int decide(const bfs_config &c, int cur_bu, int d, int64_t n, int64_t n_f, int64_t m_f,
-           int64_t n_u, int64_t m_u) {
-    if (c.policy == BFS_POLICY_FORCED) return c.forced[std::min(d, c.forced_len - 1)] ? 1 : 0;
+__host__ __device__ int decide(const bfs_config &c, int cur_bu, int d, int64_t n, int64_t n_f,
+                               int64_t m_f, int64_t n_u, int64_t m_u) {
+    if (c.policy == BFS_POLICY_FORCED)
+        return c.forced[d < c.forced_len - 1 ? d : c.forced_len - 1] ? 1 : 0;
     if (c.policy == BFS_POLICY_VERTEX) {
         if (!cur_bu) return n_f > (n_u >> 10) ? 1 : 0;
         return n_f < (n >> 6) ? 0 : 1;
     }
     if (!cur_bu) return ((double)m_f > (double)m_u / c.alpha) ? 1 : 0;
     return ((double)n_f < (double)n / c.beta) ? 0 : 1;
+}
+
+
+// ---------------------------------------------------------------------------
+// Device-side layer loop (cfg.device_loop): the traversal of bfs_run in one
+// cooperative launch. Every block runs the same loop over layers, reads the
+// layer counters after a grid barrier and so takes the same Alg. 3 decision
+// and the same launch parameters the host loop would compute; the phases are
+// the host loop's kernels as device functions, with coherent (L2) loads for
+// data other blocks wrote earlier in the launch.
+// ---------------------------------------------------------------------------
+constexpr int kSsMaxRecords = 4096;  // per-layer records kept for statistics
+
+struct SsPersist {
+    const int64_t *off;
+    const int32_t *idx;
+    int64_t n, nnz, nw, nw_pad, deg0;
+    uint32_t *visited, *bm_a, *bm_b;
+    int32_t *q_a, *q_b, *big;
+    int32_t *parent, *level;
+    int64_t *trace;    // ring of kRing slots; slot 0 written by init_kernel
+    int64_t *layers;   // [kSsMaxRecords][8] per-layer record
+    int64_t *result;   // [0] layers, [1] status, [2] degree sum over frontiers
+    unsigned *bar;     // barrier count, generation
+    int32_t *err;
+    bfs_config cfg;
+    unsigned long long timeout_ns;
+};
+
+__global__ void __launch_bounds__(kBlock, 4) bfs_persistent_kernel(SsPersist p) {
+    const unsigned expected = gridDim.x;
+    const int64_t td_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t n_f = 1, m_f = __ldcg(p.trace + T_MF);
+    int64_t n_u = p.n - 1, m_u = p.nnz - m_f, degsum = 0;
+    int cur_bu = 0, status = BFS_OK, d = 0;
+    bool have_queue = true;
+    for (; n_f > 0; ++d) {
+        if (d > p.n) {  // a BFS has at most n layers: the counters are inconsistent
+            status = BFS_ERR_CUDA;
+            break;
+        }
+        cur_bu = decide(p.cfg, cur_bu, d, p.n, n_f, m_f, n_u, m_u);
+        degsum += m_f;
+        int64_t *sc = p.trace + (d % kRing) * kFields;
+        int64_t *sn = p.trace + ((d + 1) % kRing) * kFields;
+        int64_t *sz = p.trace + ((d + 2) % kRing) * kFields;
+        uint32_t *front = (d & 1) ? p.bm_b : p.bm_a;
+        uint32_t *next = (d & 1) ? p.bm_a : p.bm_b;
+        int32_t *q_cur = (d & 1) ? p.q_b : p.q_a;
+        int32_t *q_next = (d & 1) ? p.q_a : p.q_b;
+        int converted = 0;
+        if (!cur_bu) {
+            if (!have_queue) {
+                b2q_phase<true>(front, p.nw, q_cur, (unsigned long long *)(sc + T_CONV));
+                converted = 1;
+            }
+            for (int64_t i = t0; i < p.nw_pad; i += stride) next[i] = 0u;
+            if (!grid_barrier(p.bar, p.err, expected, p.timeout_ns)) {
+                status = BFS_ERR_TIMEOUT;
+                break;
+            }
+            const int queue_mode = m_f <= kQueueModeMaxEdges ? 1 : 0;
+            TdArgs a{p.off, p.idx, p.visited, next, p.parent, p.level, q_next,
+                     (unsigned long long *)(sn + T_NF), d + 1, queue_mode, p.cfg.td_claim};
+            int64_t pw = (n_f + td_warps - 1) / td_warps;
+            const int per_warp = (int)(pw < 1 ? 1 : (pw > 32 ? 32 : pw));
+            int64_t gd = m_f / td_warps;
+            if (gd < 4 * (int64_t)p.cfg.td_warp_degree) gd = 4 * (int64_t)p.cfg.td_warp_degree;
+            if (gd > p.cfg.td_grid_degree) gd = p.cfg.td_grid_degree;
+            td_phase<true>(a, q_cur, n_f, per_warp, p.big, (unsigned long long *)(sc + T_BIG),
+                           (unsigned long long *)(sn + T_MF), p.cfg.td_warp_degree, gd, sz);
+            if (m_f >= gd) {
+                if (!grid_barrier(p.bar, p.err, expected, p.timeout_ns)) {
+                    status = BFS_ERR_TIMEOUT;
+                    break;
+                }
+                td_big_phase<true>(a, p.big, (const unsigned long long *)(sc + T_BIG),
+                                   (unsigned long long *)(sn + T_MF));
+            }
+            have_queue = queue_mode != 0;
+        } else {
+            const int64_t active = n_u - p.deg0;
+            if (p.cfg.bu_list_percent > 0 && active * 100 <= (int64_t)p.cfg.bu_list_percent * p.n) {
+                for (int64_t i = t0; i < p.nw_pad; i += stride) next[i] = 0u;
+                unvisited_list_phase<true>(p.visited, p.nw, q_next,
+                                           (unsigned long long *)(sc + T_ULIST));
+                if (!grid_barrier(p.bar, p.err, expected, p.timeout_ns)) {
+                    status = BFS_ERR_TIMEOUT;
+                    break;
+                }
+                bu_list_phase<true>(p.off, p.idx, q_next, (const unsigned long long *)(sc + T_ULIST),
+                                    p.visited, front, next, p.parent, p.level, d + 1,
+                                    p.cfg.bu_probe, (unsigned long long *)sn, sz);
+                converted = 2;
+            } else {
+                bu_phase<4, 2, false, true>(p.off, p.idx, nullptr, p.nw_pad, p.visited, front, next,
+                                            p.parent, p.level, d + 1, p.cfg.bu_probe,
+                                            (unsigned long long *)sn, sz);
+            }
+            have_queue = false;
+        }
+        if (!grid_barrier(p.bar, p.err, expected, p.timeout_ns)) {
+            status = BFS_ERR_TIMEOUT;
+            break;
+        }
+        const int64_t found = __ldcg(sn + T_NF), m_new = __ldcg(sn + T_MF);
+        if (blockIdx.x == 0 && threadIdx.x == 0 && d < kSsMaxRecords) {
+            int64_t *rec = p.layers + (int64_t)d * 8;
+            rec[0] = cur_bu;
+            rec[1] = converted;
+            rec[2] = n_f;
+            rec[3] = m_f;
+            rec[4] = n_u;
+            rec[5] = m_u;
+            rec[6] = cur_bu ? __ldcg(sn + T_EXAM) : m_f;
+            rec[7] = found;
+        }
+        n_u -= found;
+        m_u -= m_new;
+        n_f = found;
+        m_f = m_new;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        p.result[0] = d;
+        p.result[1] = status;
+        p.result[2] = degsum;
+    }
+}
+
+constexpr size_t kPctlSsBytes = (size_t)kSsMaxRecords * 8 * 8 + 64;
+constexpr int64_t kDeviceLoopAutoMaxN = 1ll << 23;  // device_loop = 2: on up to this n
+
+// Runs the traversal as one cooperative launch of bfs_persistent_kernel and
+// reads back the per-layer records (init_kernel has already run on `st`).
+bfs_status run_device_loop(bfs_graph *g, int32_t *level, int32_t *parent, cudaStream_t st) {
+    if (!g->pctl) {
+        GB_CK(cudaMalloc(&g->pctl, kPctlSsBytes));
+        GB_CK(cudaMallocHost(&g->h_pctl, kPctlSsBytes));
+    }
+    if (g->persist_blocks_per_sm <= 0) {
+        GB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->persist_blocks_per_sm,
+                                                            bfs_persistent_kernel, kBlock, 0));
+        if (g->persist_blocks_per_sm <= 0) {
+            set_error("bfs_run: the device-loop kernel does not fit on an SM");
+            return BFS_ERR_CUDA;
+        }
+    }
+    // layout: result[8] (layers, status, degree sum, barrier, error), then
+    // the per-layer records, so one small copy covers short traversals
+    int64_t *result = g->pctl;
+    GB_CK(cudaMemsetAsync(result, 0, 64, st));
+    SsPersist p;
+    p.off = g->off;
+    p.idx = g->idx;
+    p.n = g->n;
+    p.nnz = g->nnz;
+    p.nw = g->nw;
+    p.nw_pad = g->nw_pad;
+    p.deg0 = g->deg0;
+    p.visited = g->visited;
+    p.bm_a = g->bm_a;
+    p.bm_b = g->bm_b;
+    p.q_a = g->q_a;
+    p.q_b = g->q_b;
+    p.big = g->big;
+    p.parent = parent;
+    p.level = level;
+    p.trace = g->trace;
+    p.layers = g->pctl + 8;
+    p.result = result;
+    p.bar = (unsigned *)(result + 4);
+    p.err = (int32_t *)(p.bar + 2);
+    p.cfg = g->cfg;
+    p.timeout_ns = 2000000000ull;  // 2 s per barrier wait
+    void *args[] = {&p};
+    GB_CK(cudaLaunchCooperativeKernel((const void *)bfs_persistent_kernel,
+                                      dim3(g->persist_blocks_per_sm * sm_count()), dim3(kBlock),
+                                      args, 0, st));
+    count_launch();
+    constexpr int64_t kFirst = 64;  // records fetched with the result
+    GB_CK(cudaMemcpyAsync(g->h_pctl, g->pctl, (size_t)(8 + kFirst * 8) * 8, cudaMemcpyDeviceToHost,
+                          st));
+    GB_CK(cudaStreamSynchronize(st));
+    const int64_t *hres = g->h_pctl;
+    const int64_t L = hres[0];
+    if (L > kFirst) {
+        const int64_t more = std::min<int64_t>(L, kSsMaxRecords) - kFirst;
+        GB_CK(cudaMemcpyAsync(g->h_pctl + 8 + kFirst * 8, g->pctl + 8 + kFirst * 8,
+                              (size_t)more * 64, cudaMemcpyDeviceToHost, st));
+        GB_CK(cudaStreamSynchronize(st));
+    }
+    for (int64_t d = 0; d < L && d < kSsMaxRecords; ++d) {
+        const int64_t *rec = g->h_pctl + 8 + d * 8;
+        bfs_layer_stats ls;
+        memset(&ls, 0, sizeof ls);
+        ls.direction = (int32_t)rec[0];
+        ls.converted = (int32_t)rec[1];
+        ls.n_f = rec[2];
+        ls.m_f = rec[3];
+        ls.n_u = rec[4];
+        ls.m_u = rec[5];
+        ls.examined = rec[6];
+        ls.found = rec[7];
+        g->last.push_back(ls);
+    }
+    g->last_component_edges = hres[2] / 2;
+    if (hres[1] == BFS_ERR_TIMEOUT) {
+        set_error("bfs_run: a grid barrier wait of the device loop ran out");
+        return BFS_ERR_TIMEOUT;
+    }
+    if (hres[1] != BFS_OK) {
+        set_error("bfs_run: the device loop stopped (status %lld)", (long long)hres[1]);
+        return (bfs_status)hres[1];
+    }
+    return BFS_OK;
 }
 
 bool is_host_ptr(const void *p) {
@@ -862,6 +1155,8 @@ void free_graph(bfs_graph *g) {
     cudaFree(g->base_vis);
     cudaFree(g->head);
     cudaFree(g->comp_in);
+    cudaFree(g->pctl);
+    if (g->h_pctl) cudaFreeHost(g->h_pctl);
     cudaFree(g->bm_a);
     cudaFree(g->bm_b);
     cudaFree(g->q_a);
@@ -895,6 +1190,7 @@ extern "C" BFS_API void bfs_config_default(bfs_config *c) {
     c->bu_head = 0;
     c->prune_components = 0;
     c->bu_list_percent = 10;
+    c->device_loop = 2;
 }
 
 extern "C" BFS_API bfs_status bfs_graph_create(const int64_t *offsets, const int32_t *indices,
@@ -1107,120 +1403,125 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
     GB_LAUNCH(init_kernel, grid_cap(std::max(n, g->nw_pad), kBlock, 8), kBlock, 0, st, n,
               g->nw_pad, root, g->off, g->base_vis, cfg.prune_components ? g->comp_in : nullptr,
               level, parent, g->visited, front, q_cur, g->trace);
-    GB_CK(cudaMemcpyAsync(g->h_slot, g->trace, kFields * 8, cudaMemcpyDeviceToHost, st));
-    GB_CK(cudaStreamSynchronize(st));
-    int64_t n_f = 1, m_f = g->h_slot[T_MF];
-    int64_t n_u = n - 1, m_u = g->nnz - m_f;
-    int cur_bu = 0;
-    bool have_queue = true;
-    int64_t degree_sum = 0;
-    const int bw = cfg.bu_words;
-    const int bsel = (bw == 4 ? 2 : bw - 1) + (cfg.bu_head ? 3 : 0);
-    const int bu_grid = (int)std::max<int64_t>(
-        1, std::min<int64_t>(g->nw_pad / 32 / (kBlock / 32) + 1,
-                             (int64_t)sm_count() * g->bu_blocks_per_sm[bsel]));
-    const int64_t td_warps = (int64_t)sm_count() * g->td_blocks_per_sm * (kBlock / 32);
-    for (int d = 0; n_f > 0; ++d) {
-        if (d > n) {  // a BFS has at most n layers: the counters are inconsistent
-            set_error("bfs_run: traversal did not terminate after %lld layers", (long long)n);
-            return BFS_ERR_CUDA;
-        }
-        cur_bu = decide(cfg, cur_bu, d, n, n_f, m_f, n_u, m_u);
-        bfs_layer_stats ls;
-        memset(&ls, 0, sizeof ls);
-        ls.direction = cur_bu;
-        ls.n_f = n_f;
-        ls.m_f = m_f;
-        ls.n_u = n_u;
-        ls.m_u = m_u;
-        degree_sum += m_f;
-        int64_t *slot_cur = g->trace + (d % kRing) * kFields;
-        int64_t *slot_next = g->trace + ((d + 1) % kRing) * kFields;
-        int64_t *slot_zero = g->trace + ((d + 2) % kRing) * kFields;
-        const size_t e0 = (size_t)d * 3;
-        if (timing) GB_CK(cudaEventRecord(event(e0), st));
-        if (!cur_bu) {
-            if (!have_queue) {
-                GB_LAUNCH(b2q_kernel, grid_cap(g->nw, kBlock * 4, 8), kBlock, 0, st, front, g->nw,
-                          q_cur, (unsigned long long *)(slot_cur + T_CONV));
-                ls.converted = 1;
-            }
-            GB_CK(cudaMemsetAsync(next, 0, (size_t)g->nw_pad * 4, st));
-            // Queue output only while the layer is small enough that one
-            // atomicAdd per warp and round on the queue tail does not
-            // serialise; a large layer leaves only the next bitmap, and the
-            // queue is rebuilt by b2q if the next layer is top-down too.
-            const int queue_mode = m_f <= kQueueModeMaxEdges ? 1 : 0;
-            TdArgs a{g->off, g->idx, g->visited, next, parent, level, q_next,
-                     (unsigned long long *)(slot_next + T_NF), d + 1, queue_mode, cfg.td_claim};
-            // Entries per warp so that a small frontier still covers the GPU,
-            // and the grid-spread threshold at the frontier's edges per warp.
-            const int per_warp = (int)std::min<int64_t>(32, std::max<int64_t>(1, (n_f + td_warps - 1) / td_warps));
-            const int64_t grid_deg = std::min<int64_t>(
-                cfg.td_grid_degree,
-                std::max<int64_t>(4 * (int64_t)cfg.td_warp_degree, m_f / td_warps));
-            const int td_grid = grid_cap((n_f + per_warp - 1) / per_warp, kBlock / 32,
-                                         g->td_blocks_per_sm);
-            if (timing) GB_CK(cudaEventRecord(event(e0 + 1), st));
-            GB_LAUNCH(td_kernel, td_grid, kBlock, 0, st, a, q_cur, n_f, per_warp, g->big,
-                      (unsigned long long *)(slot_cur + T_BIG),
-                      (unsigned long long *)(slot_next + T_MF), cfg.td_warp_degree, grid_deg,
-                      slot_zero);
-            if (m_f >= grid_deg) {
-                const int big_grid = (int)std::max<int64_t>(
-                    1, std::min<int64_t>(m_f / 4096 + 1, (int64_t)sm_count() * g->td_blocks_per_sm));
-                GB_LAUNCH(td_big_kernel, big_grid, kBlock, 0, st, a, g->big,
-                          (const unsigned long long *)(slot_cur + T_BIG),
-                          (unsigned long long *)(slot_next + T_MF));
-            }
-            have_queue = queue_mode != 0;
-        } else {
-            if (timing) GB_CK(cudaEventRecord(event(e0 + 1), st));
-            // vertices still to find: unvisited and of degree > 0
-            const int64_t active = n_u - g->deg0;
-            if (cfg.bu_list_percent > 0 && active * 100 <= (int64_t)cfg.bu_list_percent * n) {
-                // sparse layer: a compacted list of them, one lane each
-                ls.converted = 2;
-                GB_CK(cudaMemsetAsync(next, 0, (size_t)g->nw_pad * 4, st));
-                GB_LAUNCH(unvisited_list_kernel, grid_cap(g->nw, kBlock * 4, 8), kBlock, 0, st,
-                          g->visited, g->nw, q_next, (unsigned long long *)(slot_cur + T_ULIST));
-                GB_LAUNCH(bu_list_kernel,
-                          grid_cap((active + 31) / 32, kBlock / 32, g->bu_list_blocks_per_sm),
-                          kBlock, 0, st, g->off, g->idx, q_next,
-                          (const unsigned long long *)(slot_cur + T_ULIST), g->visited, front,
-                          next, parent, level, d + 1, cfg.bu_probe,
-                          (unsigned long long *)slot_next, slot_zero);
-            } else {
-                decltype(BU1) const kernels[6] = {BU1, BU2, BU4, BU1H, BU2H, BU4H};
-                auto bu = kernels[bsel];
-                GB_LAUNCH(bu, bu_grid, kBlock, 0, st, g->off, g->idx, g->head, g->nw_pad,
-                          g->visited, front, next, parent, level, d + 1, cfg.bu_probe,
-                          (unsigned long long *)slot_next, slot_zero);
-            }
-            have_queue = false;
-        }
-        if (timing) GB_CK(cudaEventRecord(event(e0 + 2), st));
-        GB_CK(cudaMemcpyAsync(g->h_slot, slot_next, kFields * 8, cudaMemcpyDeviceToHost, st));
+    if (cfg.device_loop == 1 || (cfg.device_loop == 2 && n <= kDeviceLoopAutoMaxN)) {
+        const bfs_status ds = run_device_loop(g, level, parent, st);
+        if (ds != BFS_OK) return ds;
+    } else {
+        GB_CK(cudaMemcpyAsync(g->h_slot, g->trace, kFields * 8, cudaMemcpyDeviceToHost, st));
         GB_CK(cudaStreamSynchronize(st));
-        const int64_t found = g->h_slot[T_NF], m_new = g->h_slot[T_MF];
-        ls.examined = cur_bu ? g->h_slot[T_EXAM] : m_f;
-        ls.found = found;
-        g->last.push_back(ls);
-        n_u -= found;
-        m_u -= m_new;
-        n_f = found;
-        m_f = m_new;
-        std::swap(front, next);
-        std::swap(q_cur, q_next);
-    }
-    g->last_component_edges = degree_sum / 2;
-    if (timing) {
-        for (size_t d = 0; d < g->last.size(); ++d) {
-            float t0 = 0, t1 = 0;
-            cudaEventElapsedTime(&t0, g->events[3 * d], g->events[3 * d + 2]);
-            cudaEventElapsedTime(&t1, g->events[3 * d + 1], g->events[3 * d + 2]);
-            g->last[d].ms_total = t0;
-            g->last[d].ms_main = t1;
+        int64_t n_f = 1, m_f = g->h_slot[T_MF];
+        int64_t n_u = n - 1, m_u = g->nnz - m_f;
+        int cur_bu = 0;
+        bool have_queue = true;
+        int64_t degree_sum = 0;
+        const int bw = cfg.bu_words;
+        const int bsel = (bw == 4 ? 2 : bw - 1) + (cfg.bu_head ? 3 : 0);
+        const int bu_grid = (int)std::max<int64_t>(
+            1, std::min<int64_t>(g->nw_pad / 32 / (kBlock / 32) + 1,
+                                 (int64_t)sm_count() * g->bu_blocks_per_sm[bsel]));
+        const int64_t td_warps = (int64_t)sm_count() * g->td_blocks_per_sm * (kBlock / 32);
+        for (int d = 0; n_f > 0; ++d) {
+            if (d > n) {  // a BFS has at most n layers: the counters are inconsistent
+                set_error("bfs_run: traversal did not terminate after %lld layers", (long long)n);
+                return BFS_ERR_CUDA;
+            }
+            cur_bu = decide(cfg, cur_bu, d, n, n_f, m_f, n_u, m_u);
+            bfs_layer_stats ls;
+            memset(&ls, 0, sizeof ls);
+            ls.direction = cur_bu;
+            ls.n_f = n_f;
+            ls.m_f = m_f;
+            ls.n_u = n_u;
+            ls.m_u = m_u;
+            degree_sum += m_f;
+            int64_t *slot_cur = g->trace + (d % kRing) * kFields;
+            int64_t *slot_next = g->trace + ((d + 1) % kRing) * kFields;
+            int64_t *slot_zero = g->trace + ((d + 2) % kRing) * kFields;
+            const size_t e0 = (size_t)d * 3;
+            if (timing) GB_CK(cudaEventRecord(event(e0), st));
+            if (!cur_bu) {
+                if (!have_queue) {
+                    GB_LAUNCH(b2q_kernel, grid_cap(g->nw, kBlock * 4, 8), kBlock, 0, st, front, g->nw,
+                              q_cur, (unsigned long long *)(slot_cur + T_CONV));
+                    ls.converted = 1;
+                }
+                GB_CK(cudaMemsetAsync(next, 0, (size_t)g->nw_pad * 4, st));
+                // Queue output only while the layer is small enough that one
+                // atomicAdd per warp and round on the queue tail does not
+                // serialise; a large layer leaves only the next bitmap, and the
+                // queue is rebuilt by b2q if the next layer is top-down too.
+                const int queue_mode = m_f <= kQueueModeMaxEdges ? 1 : 0;
+                TdArgs a{g->off, g->idx, g->visited, next, parent, level, q_next,
+                         (unsigned long long *)(slot_next + T_NF), d + 1, queue_mode, cfg.td_claim};
+                // Entries per warp so that a small frontier still covers the GPU,
+                // and the grid-spread threshold at the frontier's edges per warp.
+                const int per_warp = (int)std::min<int64_t>(32, std::max<int64_t>(1, (n_f + td_warps - 1) / td_warps));
+                const int64_t grid_deg = std::min<int64_t>(
+                    cfg.td_grid_degree,
+                    std::max<int64_t>(4 * (int64_t)cfg.td_warp_degree, m_f / td_warps));
+                const int td_grid = grid_cap((n_f + per_warp - 1) / per_warp, kBlock / 32,
+                                             g->td_blocks_per_sm);
+                if (timing) GB_CK(cudaEventRecord(event(e0 + 1), st));
+                GB_LAUNCH(td_kernel, td_grid, kBlock, 0, st, a, q_cur, n_f, per_warp, g->big,
+                          (unsigned long long *)(slot_cur + T_BIG),
+                          (unsigned long long *)(slot_next + T_MF), cfg.td_warp_degree, grid_deg,
+                          slot_zero);
+                if (m_f >= grid_deg) {
+                    const int big_grid = (int)std::max<int64_t>(
+                        1, std::min<int64_t>(m_f / 4096 + 1, (int64_t)sm_count() * g->td_blocks_per_sm));
+                    GB_LAUNCH(td_big_kernel, big_grid, kBlock, 0, st, a, g->big,
+                              (const unsigned long long *)(slot_cur + T_BIG),
+                              (unsigned long long *)(slot_next + T_MF));
+                }
+                have_queue = queue_mode != 0;
+            } else {
+                if (timing) GB_CK(cudaEventRecord(event(e0 + 1), st));
+                // vertices still to find: unvisited and of degree > 0
+                const int64_t active = n_u - g->deg0;
+                if (cfg.bu_list_percent > 0 && active * 100 <= (int64_t)cfg.bu_list_percent * n) {
+                    // sparse layer: a compacted list of them, one lane each
+                    ls.converted = 2;
+                    GB_CK(cudaMemsetAsync(next, 0, (size_t)g->nw_pad * 4, st));
+                    GB_LAUNCH(unvisited_list_kernel, grid_cap(g->nw, kBlock * 4, 8), kBlock, 0, st,
+                              g->visited, g->nw, q_next, (unsigned long long *)(slot_cur + T_ULIST));
+                    GB_LAUNCH(bu_list_kernel,
+                              grid_cap((active + 31) / 32, kBlock / 32, g->bu_list_blocks_per_sm),
+                              kBlock, 0, st, g->off, g->idx, q_next,
+                              (const unsigned long long *)(slot_cur + T_ULIST), g->visited, front,
+                              next, parent, level, d + 1, cfg.bu_probe,
+                              (unsigned long long *)slot_next, slot_zero);
+                } else {
+                    decltype(BU1) const kernels[6] = {BU1, BU2, BU4, BU1H, BU2H, BU4H};
+                    auto bu = kernels[bsel];
+                    GB_LAUNCH(bu, bu_grid, kBlock, 0, st, g->off, g->idx, g->head, g->nw_pad,
+                              g->visited, front, next, parent, level, d + 1, cfg.bu_probe,
+                              (unsigned long long *)slot_next, slot_zero);
+                }
+                have_queue = false;
+            }
+            if (timing) GB_CK(cudaEventRecord(event(e0 + 2), st));
+            GB_CK(cudaMemcpyAsync(g->h_slot, slot_next, kFields * 8, cudaMemcpyDeviceToHost, st));
+            GB_CK(cudaStreamSynchronize(st));
+            const int64_t found = g->h_slot[T_NF], m_new = g->h_slot[T_MF];
+            ls.examined = cur_bu ? g->h_slot[T_EXAM] : m_f;
+            ls.found = found;
+            g->last.push_back(ls);
+            n_u -= found;
+            m_u -= m_new;
+            n_f = found;
+            m_f = m_new;
+            std::swap(front, next);
+            std::swap(q_cur, q_next);
+        }
+        g->last_component_edges = degree_sum / 2;
+        if (timing) {
+            for (size_t d = 0; d < g->last.size(); ++d) {
+                float t0 = 0, t1 = 0;
+                cudaEventElapsedTime(&t0, g->events[3 * d], g->events[3 * d + 2]);
+                cudaEventElapsedTime(&t1, g->events[3 * d + 1], g->events[3 * d + 2]);
+                g->last[d].ms_total = t0;
+                g->last[d].ms_main = t1;
+            }
         }
     }
     if (host_out) {

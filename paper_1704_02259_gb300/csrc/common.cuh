@@ -78,4 +78,62 @@ __device__ __forceinline__ int warp_exclusive_scan(int v, int *total) {
     return x - v;
 }
 
+// Loads of data that changes during a traversal. CO (coherent) is set inside
+// the persistent kernels, where other blocks wrote the data earlier in the
+// same launch: those loads go to L2 (ld.global.cg) instead of the
+// non-coherent read-only path.
+template <bool CO, typename T>
+__device__ __forceinline__ T ld(const T *p) {
+    if constexpr (CO) return __ldcg(p);
+    else return *p;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier for a cooperative launch (every block resident).
+// bar[0] counts arrivals, bar[1] is the generation the last arrival bumps.
+// Every wait is bounded: a block that waits longer than timeout_ns sets
+// *err, and every block that sees *err leaves; the caller then returns.
+// `expected` is gridDim.x except in the self-test, which asks for more.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, int32_t *err, unsigned expected,
+                             unsigned long long timeout_ns) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned *gen = bar + 1;
+        volatile int32_t *verr = err;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == expected - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (*gen == g) {
+                if (*verr) {
+                    ok = 0;
+                    break;
+                }
+                if (global_ns() - t0 > timeout_ns) {
+                    atomicExch(err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(128);
+            }
+        }
+        __threadfence();
+        if (*verr) ok = 0;
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
 }  // namespace gbfs

@@ -46,6 +46,8 @@ struct bfs_graph {
     int bu_blocks_per_sm[6] = {1, 1, 1, 1, 1, 1};  // BU1, BU2, BU4, BU1H, BU2H, BU4H
     int td_blocks_per_sm = 1;
     int bu_list_blocks_per_sm = 1;
+    int persist_blocks_per_sm = 0;  // device-loop kernel, 0 = not queried yet
+    int64_t *pctl = nullptr, *h_pctl = nullptr;  // device-loop layer records
     MsState *ms = nullptr;
 };
 

@@ -60,7 +60,8 @@ FORCED = {"td": [0], "bu": [1], "alt": [0, 1] * 32, "alt2": [1, 0] * 32,
                                   "union", "single", "ragged"])
 @pytest.mark.parametrize("pat", list(FORCED))
 @pytest.mark.parametrize("prune", [0, 1])
-def test_closed_form_graphs_forced_directions(name, pat, prune):
+@pytest.mark.parametrize("loop", [0, 1])
+def test_closed_form_graphs_forced_directions(name, pat, prune, loop):
     if name == "path":
         n, (s, d) = 77, inputs.path_edges(77)
     elif name == "cycle":
@@ -83,7 +84,7 @@ def test_closed_form_graphs_forced_directions(name, pat, prune):
         s, d = inputs.random_edges(n, 3 * n, 5)
     forced = FORCED[pat]
     o_off, o_idx, g = make(n, s, d, forced=forced, prune_components=prune,
-                           bu_list_percent=100 if prune else 0)
+                           bu_list_percent=100 if prune else 0, device_loop=loop)
     for r in sorted({0, n // 2, n - 1}):
         check_run(o_off, o_idx, g, r, forced=forced)
 
@@ -100,7 +101,7 @@ def test_policies_on_skewed_graphs(seed, policy, claim):
         n = 1 << (12 + seed // 2)
     o_off, o_idx, g = make(n, s, d, policy=policy, td_claim=claim, bu_words=[1, 2, 4][seed % 3],
                            bu_head=(seed // 3 + claim) % 2, prune_components=(seed + claim) % 2,
-                           bu_list_percent=[0, 10, 100][(seed + claim) % 3])
+                           bu_list_percent=[0, 10, 100][(seed + claim) % 3], device_loop=claim)
     for r in oracle.sample_roots(o_off, n, seed, 4):
         check_run(o_off, o_idx, g, int(r), policy=policy)
 
@@ -122,6 +123,8 @@ def test_degree_bin_boundaries(deg, pat):
                 dict(forced=forced, bu_words=4, bu_probe=7, td_claim=1),
                 dict(forced=forced, bu_head=0, prune_components=0),
                 dict(forced=forced, bu_list_percent=100, bu_probe=3),
+                dict(forced=forced, device_loop=1),
+                dict(forced=forced, device_loop=1, bu_list_percent=100, td_grid_degree=64),
                 dict(forced=forced, bu_head=1, bu_probe=2),
                 dict(forced=forced, bu_head=1, bu_probe=4, bu_words=2)]:
         o_off, o_idx, g = make(n, s, d, **cfg)
@@ -157,6 +160,9 @@ def test_rmat_scale16_all_64_roots():
     g = gb.Graph(g_off, g_idx)
     roots = gb.sample_roots(g_off, n, 2, 64).cpu().numpy()
     assert np.array_equal(roots, oracle.sample_roots(o_off, n, 2, 64))
+    for r in roots:
+        check_run(o_off, o_idx, g, int(r))
+    g.set_config(config(device_loop=0))    # the same 64 roots with the host-driven loop
     for r in roots:
         check_run(o_off, o_idx, g, int(r))
 
