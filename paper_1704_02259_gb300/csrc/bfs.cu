@@ -462,19 +462,25 @@ __device__ __forceinline__ void bu_phase(
     const int2 *__restrict__ head, int64_t nw_pad,
     uint32_t *__restrict__ visited, const uint32_t *__restrict__ front,
     uint32_t *__restrict__ next_bm, int32_t *__restrict__ parent, int32_t *__restrict__ level,
-    int32_t new_level, int probe, unsigned long long *slot_next, int64_t *zero_slot) {
+    int32_t new_level, int probe, unsigned long long *slot_next, int64_t *zero_slot, int span) {
     if (blockIdx.x == 0 && threadIdx.x < kFields) zero_slot[threadIdx.x] = 0;
     const unsigned lane = lane_id();
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nchunks = nw_pad >> 5;
+    // a warp task is `span` consecutive words of a 32-word chunk (span = 32
+    // on large graphs; smaller on small ones so every warp gets work)
+    const int per = 32 / span;
+    const int64_t ntasks = nchunks * per;
     int64_t my_nf = 0, my_mf = 0, my_ex = 0;
-    for (int64_t c = gw; c < nchunks; c += tw) {
+    for (int64_t t = gw; t < ntasks; t += tw) {
+        const int64_t c = t / per;
+        const int j0 = (int)(t - c * per) * span;
         const uint32_t vis_lane = ld<CO>(visited + c * 32 + lane);
         uint32_t *const next_c = next_bm + c * 32;
         uint32_t *const vis_c = visited + c * 32;
         const int64_t v_c = c * 1024 + lane;
-        for (int j = 0; j < 32; j += W) {
+        for (int j = j0; j < j0 + span; j += W) {
             uint32_t vw[W];
             bool all = true;
 #pragma unroll
@@ -637,8 +643,9 @@ __global__ void __launch_bounds__(kBlock, 4) bu_kernel(
     const int2 *__restrict__ head, int64_t nw_pad,
     uint32_t *__restrict__ visited, const uint32_t *__restrict__ front,
     uint32_t *__restrict__ next_bm, int32_t *__restrict__ parent, int32_t *__restrict__ level,
-    int32_t new_level, int probe, unsigned long long *slot_next, int64_t *zero_slot) {
-    bu_phase<W, CH, HEAD, false>(off, idx, head, nw_pad, visited, front, next_bm, parent, level, new_level, probe, slot_next, zero_slot);
+    int32_t new_level, int probe, unsigned long long *slot_next, int64_t *zero_slot, int span) {
+    bu_phase<W, CH, HEAD, false>(off, idx, head, nw_pad, visited, front, next_bm, parent, level,
+                                 new_level, probe, slot_next, zero_slot, span);
 }
 
 
@@ -931,6 +938,14 @@ __host__ __device__ int decide(const bfs_config &c, int cur_bu, int d, int64_t n
 // ---------------------------------------------------------------------------
 constexpr int kSsMaxRecords = 4096;  // per-layer records kept for statistics
 
+// Words per dense bottom-up warp task: 32 (a whole chunk) unless that leaves
+// fewer than two tasks per warp, then halved down to the words in flight.
+__host__ __device__ inline int bu_span(int64_t nchunks, int w, int64_t warps) {
+    int span = 32;
+    while (span > w && nchunks * (32 / span) < 2 * warps) span >>= 1;
+    return span;
+}
+
 struct SsPersist {
     const int64_t *off;
     const int32_t *idx;
@@ -1017,7 +1032,8 @@ __global__ void __launch_bounds__(kBlock, 4) bfs_persistent_kernel(SsPersist p) 
             } else {
                 bu_phase<4, 2, false, true>(p.off, p.idx, nullptr, p.nw_pad, p.visited, front, next,
                                             p.parent, p.level, d + 1, p.cfg.bu_probe,
-                                            (unsigned long long *)sn, sz);
+                                            (unsigned long long *)sn, sz,
+                                            bu_span(p.nw_pad >> 5, 4, td_warps));
             }
             have_queue = false;
         }
@@ -1095,8 +1111,13 @@ bfs_status run_device_loop(bfs_graph *g, int32_t *level, int32_t *parent, cudaSt
     p.cfg = g->cfg;
     p.timeout_ns = 2000000000ull;  // 2 s per barrier wait
     void *args[] = {&p};
-    GB_CK(cudaLaunchCooperativeKernel((const void *)bfs_persistent_kernel,
-                                      dim3(g->persist_blocks_per_sm * sm_count()), dim3(kBlock),
+    // Grid sized to the graph: barrier cost grows with the block count, and a
+    // small graph cannot use the whole GPU anyway (one block per 2048
+    // vertices, at least one per SM, at most the resident maximum).
+    const int64_t full = (int64_t)g->persist_blocks_per_sm * sm_count();
+    const int64_t want = std::max<int64_t>(sm_count(), (g->n + 2047) / 2048);
+    const int grid = (int)std::min<int64_t>(full, want);
+    GB_CK(cudaLaunchCooperativeKernel((const void *)bfs_persistent_kernel, dim3(grid), dim3(kBlock),
                                       args, 0, st));
     count_launch();
     constexpr int64_t kFirst = 64;  // records fetched with the result
@@ -1416,9 +1437,11 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
         int64_t degree_sum = 0;
         const int bw = cfg.bu_words;
         const int bsel = (bw == 4 ? 2 : bw - 1) + (cfg.bu_head ? 3 : 0);
+        const int64_t bu_full = (int64_t)sm_count() * g->bu_blocks_per_sm[bsel];
+        const int bu_span_w = bu_span(g->nw_pad >> 5, bw, bu_full * (kBlock / 32));
         const int bu_grid = (int)std::max<int64_t>(
-            1, std::min<int64_t>(g->nw_pad / 32 / (kBlock / 32) + 1,
-                                 (int64_t)sm_count() * g->bu_blocks_per_sm[bsel]));
+            1, std::min<int64_t>((g->nw_pad >> 5) * (32 / bu_span_w) / (kBlock / 32) + 1,
+                                 bu_full));
         const int64_t td_warps = (int64_t)sm_count() * g->td_blocks_per_sm * (kBlock / 32);
         for (int d = 0; n_f > 0; ++d) {
             if (d > n) {  // a BFS has at most n layers: the counters are inconsistent
@@ -1495,7 +1518,7 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                     auto bu = kernels[bsel];
                     GB_LAUNCH(bu, bu_grid, kBlock, 0, st, g->off, g->idx, g->head, g->nw_pad,
                               g->visited, front, next, parent, level, d + 1, cfg.bu_probe,
-                              (unsigned long long *)slot_next, slot_zero);
+                              (unsigned long long *)slot_next, slot_zero, bu_span_w);
                 }
                 have_queue = false;
             }
@@ -1682,7 +1705,7 @@ extern "C" BFS_API bfs_status bfs_run_noalloc(const int64_t *offsets, const int3
         } else {
             GB_LAUNCH(BU2, bu_grid, kBlock, 0, st, offsets, indices, nullptr, nw_pad, visited,
                       front, next, parent_out, level_out, d + 1, cfg.bu_probe,
-                      (unsigned long long *)slot_next, slot_zero);
+                      (unsigned long long *)slot_next, slot_zero, 32);
             have_queue = false;
         }
         GB_CK(cudaMemcpyAsync(h, slot_next, sizeof h, cudaMemcpyDeviceToHost, st));
