@@ -59,7 +59,8 @@ def _load():
             "orc_sample_roots": (i32, [P, i64, u64, i32, i64, P]),
             "orc_bfs": (i32, [P, P, i64, i32, P, P]),
             "orc_policy_decide": (i32, [i32, i32, i64, i64, i64, i64, i64, dbl, dbl]),
-            "orc_hybrid_bfs": (i32, [P, P, i64, i32, i32, dbl, dbl, P, P, P, P, P, i32]),
+            "orc_hybrid_bfs": (i32, [P, P, i64, i32, i32, dbl, dbl, P, P, P, P, P, i32, P]),
+            "orc_hub": (None, [P, P, i64, P]),
             "orc_check_levels": (i64, [P, P, i64, i32, P]),
             "orc_check_parents": (i64, [P, P, i64, i32, P, P]),
             "orc_min_parent": (None, [P, P, i64, i32, P, P]),
@@ -148,8 +149,9 @@ def policy_decide(policy: int, cur_bottom_up: bool, n: int, n_f: int, m_f: int,
 
 def hybrid_bfs(offsets, indices, root: int, policy: int = POLICY_EDGE,
                alpha: float = 14.0, beta: float = 24.0, forced=None,
-               max_levels: int | None = None):
-    """Alg. 3 run sequentially. Returns level, parent, dirs, trace[L, 6]."""
+               max_levels: int | None = None, hint=None):
+    """Alg. 3 run sequentially. Returns level, parent, dirs, trace[L, 6].
+    ``hint`` (int32 [n] or None): a neighbour the bottom-up step tests first."""
     off, idx = _csr(offsets, indices)
     n = off.size - 1
     if max_levels is None:
@@ -163,11 +165,26 @@ def hybrid_bfs(offsets, indices, root: int, policy: int = POLICY_EDGE,
     parent = np.empty(n, dtype=np.int32)
     dirs = np.empty(max_levels, dtype=np.int32)
     trace = np.empty(6 * max_levels, dtype=np.int64)
+    h = None
+    if hint is not None:
+        h = np.ascontiguousarray(hint, dtype=np.int32)
+        if h.size != n:
+            raise ValueError("hint must have one entry per vertex")
     L = _load().orc_hybrid_bfs(_p(off), _p(idx), n, root, policy, alpha, beta, _p(f),
-                               _p(level), _p(parent), _p(dirs), _p(trace), max_levels)
+                               _p(level), _p(parent), _p(dirs), _p(trace), max_levels,
+                               None if h is None else _p(h))
     if L < 0:
         raise ValueError("bad root or too many layers")
     return level, parent, dirs[:L].copy(), trace[:6 * L].reshape(L, 6).copy()
+
+
+def hub(offsets, indices):
+    """Neighbour of largest degree per vertex (smallest id on ties; -1 if none)."""
+    off, idx = _csr(offsets, indices)
+    n = off.size - 1
+    out = np.empty(n, dtype=np.int32)
+    _load().orc_hub(_p(off), _p(idx), n, _p(out))
+    return out
 
 
 def check_levels(offsets, indices, root: int, level) -> int:

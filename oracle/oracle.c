@@ -33,6 +33,8 @@
  *                        size (used where the FIFO oracle is too slow).
  *   orc_check_parents    BFS-tree invariants (Sec. 7.1: many trees are valid).
  *   orc_min_parent       smallest-id parent one level up (a deterministic tree).
+ *   orc_hub              per-vertex neighbour of largest degree, the optional
+ *                        first probe of the bottom-up step.
  *   orc_component_edges  undirected edges in the root's component, the TEPS
  *                        numerator (Sec. 6.3).
  *
@@ -246,6 +248,11 @@ int32_t orc_policy_decide(int32_t policy, int32_t cur_bottom_up, int64_t n, int6
  *             it to `out`, P[v] = n, stop.
  * policy 2 forces the direction of layer d to forced[d] (1 = bottom-up;
  * layers past max_levels keep the last entry).
+ * hint (may be NULL): a neighbour of each vertex (-1 for none) that the
+ * bottom-up step tests before the scan. A hit there ends the search with
+ * P[v] = hint[v]; a miss counts one examined edge and the scan of Adj[v]
+ * then runs as above, from its first entry. Levels do not depend on it
+ * (Alg. 2 accepts any neighbour in `in`).
  * Per-layer outputs (layer d = the frontier of vertices at level d):
  *   dir[d] (1 = bottom-up), trace[6*d + 0..5] = n_f, m_f, n_u, m_u,
  *   edges examined while processing the layer, vertices found.
@@ -257,7 +264,7 @@ int32_t orc_policy_decide(int32_t policy, int32_t cur_bottom_up, int64_t n, int6
 int32_t orc_hybrid_bfs(const int64_t *offsets, const int32_t *indices, int64_t n, int32_t root,
                        int32_t policy, double alpha, double beta, const int32_t *forced,
                        int32_t *level, int32_t *parent, int32_t *dir, int64_t *trace,
-                       int32_t max_levels)
+                       int32_t max_levels, const int32_t *hint)
 {
     if (root < 0 || root >= n || max_levels < 1) return -1;
     char *vis = (char *)calloc((size_t)n, 1);
@@ -301,6 +308,16 @@ int32_t orc_hybrid_bfs(const int64_t *offsets, const int32_t *indices, int64_t n
             for (int64_t i = 0; i < n_in; ++i) in_set[in[i]] = 1;
             for (int64_t v = 0; v < n; ++v) {
                 if (vis[v]) continue;
+                if (hint && hint[v] >= 0) {
+                    ++examined;
+                    if (in_set[hint[v]]) {
+                        vis[v] = 1;
+                        out[n_out++] = (int32_t)v;
+                        parent[v] = hint[v];
+                        level[v] = d + 1;
+                        continue;
+                    }
+                }
                 for (int64_t e = offsets[v]; e < offsets[v + 1]; ++e) {
                     int32_t nb = indices[e];
                     ++examined;
@@ -396,6 +413,28 @@ int64_t orc_check_parents(const int64_t *offsets, const int32_t *indices, int64_
         if (!orc_has_edge(offsets, indices, p, (int32_t)v)) return 1 + v;
     }
     return 0;
+}
+
+/* Hub of each vertex: the neighbour of largest degree, the smallest id among
+ * neighbours of equal degree; -1 for a vertex without neighbours. A
+ * high-degree neighbour is the one most likely to be in an early frontier,
+ * so it is a cheap first test for the bottom-up step (hint of
+ * orc_hybrid_bfs). */
+void orc_hub(const int64_t *offsets, const int32_t *indices, int64_t n, int32_t *hub)
+{
+    for (int64_t v = 0; v < n; ++v) {
+        int32_t best = -1;
+        int64_t best_deg = -1;
+        for (int64_t e = offsets[v]; e < offsets[v + 1]; ++e) {
+            int32_t u = indices[e];
+            int64_t du = offsets[u + 1] - offsets[u];
+            if (du > best_deg || (du == best_deg && u < best)) {
+                best = u;
+                best_deg = du;
+            }
+        }
+        hub[v] = best;
+    }
 }
 
 /* Smallest-id parent: for each reached v != root, the smallest neighbour u

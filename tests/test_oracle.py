@@ -327,6 +327,84 @@ def test_hybrid_bottom_up_examined_edges_brute_force():
         assert tr[dd, 4] == exp
 
 
+# ------------------------------------------------- hub record and first probe
+def test_hub_star_path_and_isolated():
+    # star: every leaf's only neighbour is the centre; the centre's neighbours
+    # all have degree 1, so its hub is the smallest leaf
+    s, d = inputs.star_edges(9, centre=4)
+    off, idx = csr(9, s, d)
+    h = oracle.hub(off, idx)
+    assert h[4] == 0
+    assert all(h[v] == 4 for v in range(9) if v != 4)
+    # path 0-1-2-3-4: interior vertices have degree 2, the ends degree 1
+    s, d = inputs.path_edges(5)
+    off, idx = csr(5, s, d)
+    assert oracle.hub(off, idx).tolist() == [1, 2, 1, 2, 3]
+    # isolated vertex 3
+    off, idx = csr(4, np.array([0, 1], np.int32), np.array([1, 2], np.int32))
+    assert oracle.hub(off, idx).tolist() == [1, 0, 1, -1]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_hub_brute_force(seed):
+    n = 150
+    s, d = inputs.powerlaw_edges(n, 500, seed)
+    off, idx = csr(n, s, d)
+    dg = deg(off)
+    h = oracle.hub(off, idx)
+    for v in range(n):
+        nb = idx[off[v]:off[v + 1]].tolist()
+        if not nb:
+            assert h[v] == -1
+            continue
+        best = max(nb, key=lambda u: (dg[u], -u))
+        assert h[v] == best
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_hint_keeps_levels_and_counts_examined_edges(seed):
+    n = 1 << 9
+    s, d = oracle.gen_edges(oracle.RMAT, 9, 8, seed)
+    off, idx = csr(n, s, d)
+    dg = deg(off)
+    root = int(np.argmax(dg))
+    ref, _ = oracle.bfs(off, idx, root)
+    hub = oracle.hub(off, idx)
+    first = np.where(dg > 0, idx[np.minimum(off[:-1], idx.size - 1)], -1).astype(np.int32)
+    for forced in ([1], [0, 1], [0, 0, 1, 0]):
+        lv0, pa0, dirs0, tr0 = oracle.hybrid_bfs(off, idx, root, oracle.POLICY_FORCED,
+                                                 forced=forced)
+        # a hint equal to the first CSR neighbour changes nothing but adds one
+        # examined edge per unvisited vertex whose first neighbour misses
+        lv1, pa1, dirs1, tr1 = oracle.hybrid_bfs(off, idx, root, oracle.POLICY_FORCED,
+                                                 forced=forced, hint=first)
+        assert (lv1 == ref).all() and (pa1 == pa0).all() and (dirs1 == dirs0).all()
+        lvh, pah, dirsh, trh = oracle.hybrid_bfs(off, idx, root, oracle.POLICY_FORCED,
+                                                 forced=forced, hint=hub)
+        assert (lvh == ref).all()
+        check_tree(off, idx, root, lvh, pah)
+        for dd in range(len(dirs0)):
+            if dirs0[dd] != 1:
+                assert tr1[dd, 4] == tr0[dd, 4] and trh[dd, 4] == tr0[dd, 4]
+                continue
+            unv = [v for v in range(n) if not (0 <= ref[v] <= dd) and dg[v] > 0]
+            miss_first = sum(1 for v in unv if ref[first[v]] != dd)
+            assert tr1[dd, 4] == tr0[dd, 4] + miss_first
+            # hub: one examined edge for a hit, else one plus the plain scan
+            exp = 0
+            for v in unv:
+                if ref[hub[v]] == dd:
+                    exp += 1
+                    assert pah[v] == hub[v]
+                    continue
+                row = idx[off[v]:off[v + 1]].tolist()
+                hits = [i for i, u in enumerate(row) if ref[u] == dd]
+                exp += 1 + ((hits[0] + 1) if hits else len(row))
+                if hits:
+                    assert pah[v] == row[hits[0]]
+            assert trh[dd, 4] == exp
+
+
 # ----------------------------------------------------------- direction policy
 def read_rows(name):
     rows = []
