@@ -136,11 +136,20 @@ typedef struct bfs_config {
     int32_t td_claim;        /* top-down claim of a vertex: 0 = atomicCAS on
                                 parent[v] (-1 -> u); 1 = atomicOr on the
                                 visited bitmap word, then plain parent store  */
-    int32_t bu_head;         /* 1 = the bottom-up probe reads an 8-byte record
-                                per vertex {first neighbour, degree}, built on
-                                first use (8*n bytes): one coalesced load
-                                instead of a row-bound pair and a random
-                                index sector; 0 = read the CSR only          */
+    int32_t bu_head;         /* the bottom-up step first tests the neighbour
+                                held in an 8-byte record per vertex
+                                {neighbour, degree}, built on first use (8*n
+                                bytes): one coalesced load instead of a
+                                row-bound pair and a random index sector.
+                                1 = the row's first entry (the scan then goes
+                                on from its second); 2 = the hub, the
+                                neighbour of largest degree (smallest id on
+                                ties), the likeliest to be in an early
+                                frontier (on a miss the row is scanned from
+                                its first entry; Alg. 2 accepts any frontier
+                                neighbour, so levels are unchanged and the
+                                parent is the hub whenever it is in the
+                                frontier); 0 = read the CSR only            */
     int32_t prune_components;/* 1 = vertices outside the root's connected
                                 component start as visited, so bottom-up
                                 layers skip them (results unchanged; only the
@@ -179,8 +188,8 @@ BFS_API void bfs_config_default(bfs_config *cfg);
  * per-traversal scratch: four n-bit bitmaps (visited, frontier, next, and
  * the degree-0 mask), three n-entry vertex lists (two queues and the list of
  * grid-spread vertices) and a small counter block: about 12.5*n bytes. The
- * 8-byte head records (cfg.bu_head) are built by the first bfs_run that
- * asks for them.
+ * 8-byte head records (cfg.bu_head, 8*n bytes) are built here when cfg asks
+ * for them (the defaults do), else by the first bfs_run that does.
  * Without BFS_BORROW the CSR is copied into library memory and the caller may
  * free its arrays. cfg may be NULL (defaults). Synchronous. */
 BFS_API bfs_status bfs_graph_create(const int64_t *offsets, const int32_t *indices, int64_t n,
@@ -376,8 +385,9 @@ BFS_API bfs_status bfs_serve_destroy(bfs_server *s);
  * (a framework's caching pool that has reserved the GPU), or code on a
  * latency-critical path where an allocation's implicit synchronisation is not
  * acceptable. bfs_run_noalloc runs the same hybrid BFS as bfs_run (default
- * configuration, edge policy) without creating a bfs_graph and without any
- * allocation: its bitmaps, queues and counters live in one fixed device
+ * configuration, edge policy, except that the bottom-up probe reads the CSR
+ * only: head records would need an allocation) without creating a bfs_graph
+ * and without any allocation: its bitmaps, queues and counters live in one fixed device
  * array compiled into the library (about 12.5 MiB on every GPU that loads
  * the library, held until the process exits).
  *   offsets, indices   device CSR (layout above), caller-owned, n <= 2^20

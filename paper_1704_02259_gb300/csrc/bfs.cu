@@ -77,6 +77,34 @@ __global__ void head_kernel(const int64_t *__restrict__ off, const int32_t *__re
     }
 }
 
+// Hub head record: the neighbour of largest degree (smallest id on ties, -1
+// if none) and the degree. One warp per vertex; the lanes stride over the row
+// and a warp max of degree << 32 | ~id picks the hub.
+__global__ void hub_head_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
+                                int64_t n, int2 *__restrict__ head) {
+    const unsigned lane = lane_id();
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = gw; v < n; v += tw) {
+        const int64_t b = off[v], e = off[v + 1];
+        unsigned long long best = 0;
+        for (int64_t q = b + lane; q < e; q += 32) {
+            const int32_t u = idx[q];
+            const unsigned long long du = (unsigned long long)(off[u + 1] - off[u]);
+            const unsigned long long key = du << 32 | (unsigned long long)(~(uint32_t)u);
+            best = key > best ? key : best;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+            best = other > best ? other : best;
+        }
+        if (lane == 0)
+            head[v] = make_int2(e > b ? (int32_t)(~(uint32_t)(best & 0xffffffffull)) : -1,
+                                (int)(e - b));
+    }
+}
+
 // Highest-degree vertex (smallest id on ties), packed as degree << 32 | ~id.
 __global__ void max_degree_kernel(const int64_t *__restrict__ off, int64_t n,
                                   unsigned long long *best) {
@@ -453,16 +481,18 @@ __global__ void __launch_bounds__(kBlock) td_big_kernel(TdArgs a, const int32_t 
 //   3. the ballot of found lanes is the next word and is ORed into the
 //      visited word by the owning warp, without atomics.
 // Row positions are 32-bit offsets from a per-lane row pointer. With HEAD the
-// first position and the degree come from the vertex's 8-byte head record
-// (one coalesced load per lane); the row bound is read only for rows longer
-// than one whose first neighbour is not in the frontier.
+// first probe and the degree come from the vertex's 8-byte head record (one
+// coalesced load per lane) and the row bound is read only after that probe
+// misses. hskip says where the row scan then starts: 1 when the record holds
+// the row's first entry (already tested), 0 when it holds the hub.
 template <int W, int CH, bool HEAD, bool CO>
 __device__ __forceinline__ void bu_phase(
     const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
     const int2 *__restrict__ head, int64_t nw_pad,
     uint32_t *__restrict__ visited, const uint32_t *__restrict__ front,
     uint32_t *__restrict__ next_bm, int32_t *__restrict__ parent, int32_t *__restrict__ level,
-    int32_t new_level, int probe, unsigned long long *slot_next, int64_t *zero_slot, int span) {
+    int32_t new_level, int probe, unsigned long long *slot_next, int64_t *zero_slot, int span,
+    int hskip) {
     if (blockIdx.x == 0 && threadIdx.x < kFields) zero_slot[threadIdx.x] = 0;
     const unsigned lane = lane_id();
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -497,7 +527,7 @@ __device__ __forceinline__ void bu_phase(
             int deg[W], ex[W];
             int32_t p[W];
             // positions [0, lane_lim) are tested by the lane itself
-            const int lane_lim = HEAD ? (probe > 1 ? probe : 1) : probe;
+            const int lane_lim = HEAD ? (probe > hskip ? probe : hskip) : probe;
             if (HEAD) {
                 int2 h[W];
 #pragma unroll
@@ -523,7 +553,7 @@ __device__ __forceinline__ void bu_phase(
                             p[k] = h[k].x;
                         }
                     }
-                    if (unv[k] && !found[k] && deg[k] > 1)
+                    if (unv[k] && !found[k] && deg[k] > hskip)
                         row[k] = idx + off[v_c + (j + k) * 32];
                 }
             } else {
@@ -543,7 +573,7 @@ __device__ __forceinline__ void bu_phase(
                     deg[k] = (int)(e - b);
                 }
             }
-            for (int p0 = HEAD ? 1 : 0; p0 < lane_lim; p0 += CH) {
+            for (int p0 = HEAD ? hskip : 0; p0 < lane_lim; p0 += CH) {
                 int32_t cand[W][CH];
                 bool any = false;
 #pragma unroll
@@ -643,9 +673,10 @@ __global__ void __launch_bounds__(kBlock, 4) bu_kernel(
     const int2 *__restrict__ head, int64_t nw_pad,
     uint32_t *__restrict__ visited, const uint32_t *__restrict__ front,
     uint32_t *__restrict__ next_bm, int32_t *__restrict__ parent, int32_t *__restrict__ level,
-    int32_t new_level, int probe, unsigned long long *slot_next, int64_t *zero_slot, int span) {
+    int32_t new_level, int probe, unsigned long long *slot_next, int64_t *zero_slot, int span,
+    int hskip) {
     bu_phase<W, CH, HEAD, false>(off, idx, head, nw_pad, visited, front, next_bm, parent, level,
-                                 new_level, probe, slot_next, zero_slot, span);
+                                 new_level, probe, slot_next, zero_slot, span, hskip);
 }
 
 
@@ -705,15 +736,20 @@ __global__ void __launch_bounds__(kBlock) unvisited_list_kernel(const uint32_t *
 // Bottom-up step over a compacted list of the vertices still to find: one
 // lane per vertex, so a sparse layer keeps every lane busy. Same probe and
 // warp-cooperative tail as bu_kernel (first frontier neighbour in CSR
-// order); a found vertex sets its next and visited bits with atomicOr, since
-// no warp owns its word here.
+// order, after the head record's probe when head is set); a found vertex
+// sets its next and visited bits with atomicOr, since no warp owns its word
+// here.
 template <bool CO>
 __device__ __forceinline__ void bu_list_phase(
     const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
+    const int2 *__restrict__ head, int hskip,
     const int32_t *__restrict__ list, const unsigned long long *count,
     uint32_t *__restrict__ visited, const uint32_t *__restrict__ front,
     uint32_t *__restrict__ next_bm, int32_t *__restrict__ parent, int32_t *__restrict__ level,
     int32_t new_level, int probe, unsigned long long *slot_next, int64_t *zero_slot) {
+    // positions [p_start, lim) are tested by the lane itself
+    const int p_start = head ? hskip : 0;
+    const int lim = head ? (probe > hskip ? probe : hskip) : probe;
     if (blockIdx.x == 0 && threadIdx.x < kFields) zero_slot[threadIdx.x] = 0;
     const int64_t cnt = (int64_t)ld<CO>(count);
     const unsigned lane = lane_id();
@@ -726,21 +762,34 @@ __device__ __forceinline__ void bu_list_phase(
         int32_t v = 0;
         const int32_t *row = idx;
         int deg = 0, ex = 0;
-        if (have) {
-            v = ld<CO>(list + i);
-            const int64_t b = off[v];
-            row = idx + b;
-            deg = (int)(off[v + 1] - b);
-        }
         bool found = false;
         int32_t p = -1;
-        for (int p0 = 0; p0 < probe; p0 += 4) {
+        if (have) {
+            v = ld<CO>(list + i);
+            if (head) {
+                const int2 h = __ldg(head + v);
+                deg = h.y;
+                if (h.x >= 0) {
+                    ex = 1;
+                    if ((ldro<CO>(front + (h.x >> 5)) >> (h.x & 31)) & 1u) {
+                        found = true;
+                        p = h.x;
+                    }
+                }
+                if (!found && deg > hskip) row = idx + off[v];
+            } else {
+                const int64_t b = off[v];
+                row = idx + b;
+                deg = (int)(off[v + 1] - b);
+            }
+        }
+        for (int p0 = p_start; p0 < lim; p0 += 4) {
             int32_t cand[4];
             bool any = false;
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 const int q = p0 + t;
-                const bool ok = have && !found && q < probe && q < deg;
+                const bool ok = have && !found && q < lim && q < deg;
                 cand[t] = ok ? __ldg(row + q) : -1;
                 any = any || ok;
             }
@@ -759,7 +808,7 @@ __device__ __forceinline__ void bu_list_phase(
                 }
             }
         }
-        unsigned pend = __ballot_sync(0xffffffffu, have && !found && probe < deg);
+        unsigned pend = __ballot_sync(0xffffffffu, have && !found && lim < deg);
         while (pend) {
             const int L = __ffs(pend) - 1;
             pend &= pend - 1;
@@ -767,7 +816,7 @@ __device__ __forceinline__ void bu_list_phase(
                 (const int32_t *)__shfl_sync(0xffffffffu, (unsigned long long)row, L);
             const int ld = __shfl_sync(0xffffffffu, deg, L);
             bool hit_any = false;
-            for (int q0 = probe; q0 < ld; q0 += 64) {
+            for (int q0 = lim; q0 < ld; q0 += 64) {
                 int32_t uu[2];
                 bool hit[2];
 #pragma unroll
@@ -787,13 +836,13 @@ __device__ __forceinline__ void bu_list_phase(
                     if ((int)lane == L) {
                         found = true;
                         p = pu;
-                        ex += (q0 - probe) + 32 * t + first + 1;
+                        ex += (q0 - lim) + 32 * t + first + 1;
                     }
                     hit_any = true;
                     break;
                 }
             }
-            if (!hit_any && (int)lane == L) ex += ld - probe;
+            if (!hit_any && (int)lane == L) ex += ld - lim;
         }
         if (found) {
             const uint32_t bit = 1u << (v & 31);
@@ -811,11 +860,13 @@ __device__ __forceinline__ void bu_list_phase(
 
 __global__ void __launch_bounds__(kBlock) bu_list_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
+    const int2 *__restrict__ head, int hskip,
     const int32_t *__restrict__ list, const unsigned long long *count,
     uint32_t *__restrict__ visited, const uint32_t *__restrict__ front,
     uint32_t *__restrict__ next_bm, int32_t *__restrict__ parent, int32_t *__restrict__ level,
     int32_t new_level, int probe, unsigned long long *slot_next, int64_t *zero_slot) {
-    bu_list_phase<false>(off, idx, list, count, visited, front, next_bm, parent, level, new_level, probe, slot_next, zero_slot);
+    bu_list_phase<false>(off, idx, head, hskip, list, count, visited, front, next_bm, parent,
+                         level, new_level, probe, slot_next, zero_slot);
 }
 
 
@@ -906,7 +957,7 @@ bool config_ok(const bfs_config &c) {
     if (c.td_warp_degree < 1 || c.td_grid_degree < c.td_warp_degree) return false;
     if (c.bu_words != 1 && c.bu_words != 2 && c.bu_words != 4) return false;
     if (c.td_claim != 0 && c.td_claim != 1) return false;
-    if (c.bu_head != 0 && c.bu_head != 1) return false;
+    if (c.bu_head < 0 || c.bu_head > 2) return false;
     if (c.prune_components != 0 && c.prune_components != 1) return false;
     if (c.bu_list_percent < 0 || c.bu_list_percent > 100) return false;
     if (c.device_loop < 0 || c.device_loop > 2) return false;
@@ -949,6 +1000,8 @@ __host__ __device__ inline int bu_span(int64_t nchunks, int w, int64_t warps) {
 struct SsPersist {
     const int64_t *off;
     const int32_t *idx;
+    const int2 *head;  // head records for the bottom-up probe, or null
+    int hskip;
     int64_t n, nnz, nw, nw_pad, deg0;
     uint32_t *visited, *bm_a, *bm_b;
     int32_t *q_a, *q_b, *big;
@@ -1025,15 +1078,22 @@ __global__ void __launch_bounds__(kBlock, 4) bfs_persistent_kernel(SsPersist p) 
                     status = BFS_ERR_TIMEOUT;
                     break;
                 }
-                bu_list_phase<true>(p.off, p.idx, q_next, (const unsigned long long *)(sc + T_ULIST),
+                bu_list_phase<true>(p.off, p.idx, p.head, p.hskip, q_next,
+                                    (const unsigned long long *)(sc + T_ULIST),
                                     p.visited, front, next, p.parent, p.level, d + 1,
                                     p.cfg.bu_probe, (unsigned long long *)sn, sz);
                 converted = 2;
             } else {
-                bu_phase<4, 2, false, true>(p.off, p.idx, nullptr, p.nw_pad, p.visited, front, next,
-                                            p.parent, p.level, d + 1, p.cfg.bu_probe,
-                                            (unsigned long long *)sn, sz,
-                                            bu_span(p.nw_pad >> 5, 4, td_warps));
+                if (p.head)
+                    bu_phase<2, 4, true, true>(p.off, p.idx, p.head, p.nw_pad, p.visited, front,
+                                               next, p.parent, p.level, d + 1, p.cfg.bu_probe,
+                                               (unsigned long long *)sn, sz,
+                                               bu_span(p.nw_pad >> 5, 2, td_warps), p.hskip);
+                else
+                    bu_phase<4, 2, false, true>(p.off, p.idx, nullptr, p.nw_pad, p.visited, front,
+                                                next, p.parent, p.level, d + 1, p.cfg.bu_probe,
+                                                (unsigned long long *)sn, sz,
+                                                bu_span(p.nw_pad >> 5, 4, td_warps), 0);
             }
             have_queue = false;
         }
@@ -1109,6 +1169,8 @@ bfs_status run_device_loop(bfs_graph *g, int32_t *level, int32_t *parent, cudaSt
     p.bar = (unsigned *)(result + 4);
     p.err = (int32_t *)(p.bar + 2);
     p.cfg = g->cfg;
+    p.head = g->cfg.bu_head ? g->head : nullptr;
+    p.hskip = g->cfg.bu_head == 1 ? 1 : 0;
     p.timeout_ns = 2000000000ull;  // 2 s per barrier wait
     void *args[] = {&p};
     // Grid sized to the graph: barrier cost grows with the block count, and a
@@ -1191,6 +1253,21 @@ void free_graph(bfs_graph *g) {
     delete g;
 }
 
+// Head records for the bottom-up probe (kind 1: the row's first entry, kind
+// 2: the hub), built with the graph when its configuration asks for them,
+// else on first use, and rebuilt when the kind changes.
+bfs_status build_head(bfs_graph *g, int kind, cudaStream_t st) {
+    if (!g->head) GB_CK(cudaMalloc(&g->head, (size_t)g->n * sizeof(int2)));
+    if (kind == 1)
+        GB_LAUNCH(head_kernel, grid_cap(g->n, kBlock, 8), kBlock, 0, st, g->off, g->idx, g->n,
+                  g->head);
+    else
+        GB_LAUNCH(hub_head_kernel, grid_cap(g->n, kBlock / 32, 8), kBlock, 0, st, g->off,
+                  g->idx, g->n, g->head);
+    g->head_kind = kind;
+    return BFS_OK;
+}
+
 }  // namespace
 }  // namespace gbfs
 
@@ -1207,8 +1284,8 @@ extern "C" BFS_API void bfs_config_default(bfs_config *c) {
     c->td_warp_degree = 32;
     c->td_grid_degree = 1024;
     c->timing = 0;
-    c->bu_words = 4;
-    c->bu_head = 0;
+    c->bu_words = 2;
+    c->bu_head = 2;
     c->prune_components = 0;
     c->bu_list_percent = 10;
     c->device_loop = 2;
@@ -1311,6 +1388,14 @@ extern "C" BFS_API bfs_status bfs_graph_create(const int64_t *offsets, const int
     GB_CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->td_blocks_per_sm, td_kernel, kBlock, 0));
     GB_CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->bu_list_blocks_per_sm, bu_list_kernel,
                                                          kBlock, 0));
+    if (g->cfg.bu_head) {
+        const bfs_status hs = build_head(g, g->cfg.bu_head, 0);
+        if (hs != BFS_OK) {
+            free_graph(g);
+            return hs;
+        }
+        GB_CKG(cudaDeviceSynchronize());
+    }
 #undef GB_CKG
     *out = g;
     return BFS_OK;
@@ -1414,10 +1499,11 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
         GB_CK(cudaStreamSynchronize(st));
         g->comp_rep = rep;
     }
-    if (cfg.bu_head && !g->head) {  // head records are built on first use
-        GB_CK(cudaMalloc(&g->head, (size_t)n * sizeof(int2)));
-        GB_LAUNCH(head_kernel, grid_cap(n, kBlock, 8), kBlock, 0, st, g->off, g->idx, n, g->head);
+    if (cfg.bu_head && g->head_kind != cfg.bu_head) {  // head records are built on first use
+        const bfs_status hs = build_head(g, cfg.bu_head, st);
+        if (hs != BFS_OK) return hs;
     }
+    const int hskip = cfg.bu_head == 1 ? 1 : 0;
     g->last.clear();
     uint32_t *front = g->bm_a, *next = g->bm_b;
     int32_t *q_cur = g->q_a, *q_next = g->q_b;
@@ -1509,16 +1595,16 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                               g->visited, g->nw, q_next, (unsigned long long *)(slot_cur + T_ULIST));
                     GB_LAUNCH(bu_list_kernel,
                               grid_cap((active + 31) / 32, kBlock / 32, g->bu_list_blocks_per_sm),
-                              kBlock, 0, st, g->off, g->idx, q_next,
-                              (const unsigned long long *)(slot_cur + T_ULIST), g->visited, front,
-                              next, parent, level, d + 1, cfg.bu_probe,
+                              kBlock, 0, st, g->off, g->idx, cfg.bu_head ? g->head : nullptr,
+                              hskip, q_next, (const unsigned long long *)(slot_cur + T_ULIST),
+                              g->visited, front, next, parent, level, d + 1, cfg.bu_probe,
                               (unsigned long long *)slot_next, slot_zero);
                 } else {
                     decltype(BU1) const kernels[6] = {BU1, BU2, BU4, BU1H, BU2H, BU4H};
                     auto bu = kernels[bsel];
                     GB_LAUNCH(bu, bu_grid, kBlock, 0, st, g->off, g->idx, g->head, g->nw_pad,
                               g->visited, front, next, parent, level, d + 1, cfg.bu_probe,
-                              (unsigned long long *)slot_next, slot_zero, bu_span_w);
+                              (unsigned long long *)slot_next, slot_zero, bu_span_w, hskip);
                 }
                 have_queue = false;
             }
@@ -1705,7 +1791,7 @@ extern "C" BFS_API bfs_status bfs_run_noalloc(const int64_t *offsets, const int3
         } else {
             GB_LAUNCH(BU2, bu_grid, kBlock, 0, st, offsets, indices, nullptr, nw_pad, visited,
                       front, next, parent_out, level_out, d + 1, cfg.bu_probe,
-                      (unsigned long long *)slot_next, slot_zero, 32);
+                      (unsigned long long *)slot_next, slot_zero, 32, 0);
             have_queue = false;
         }
         GB_CK(cudaMemcpyAsync(h, slot_next, sizeof h, cudaMemcpyDeviceToHost, st));

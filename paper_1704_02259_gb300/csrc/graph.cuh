@@ -29,7 +29,8 @@ struct bfs_graph {
     int64_t *off_own = nullptr;
     int32_t *idx_own = nullptr;
     uint32_t *visited = nullptr, *bm_a = nullptr, *bm_b = nullptr;
-    int2 *head = nullptr;          // {first neighbour (-1 if none), degree}
+    int2 *head = nullptr;          // {first probe (-1 if none), degree}
+    int head_kind = 0;             // what head holds: 1 first neighbour, 2 hub
     uint32_t *comp_in = nullptr;   // vertices in the component of comp_rep
     int32_t comp_rep = -1;         // highest-degree vertex; -1 = not built yet
     int64_t deg0 = 0;              // vertices of degree 0

@@ -185,8 +185,11 @@ void worker_main(bfs_server *s, int wid) {
         bfs_status status = BFS_OK;
         if (!views[gi]) {
             bfs_graph *v = nullptr;
-            status = bfs_graph_create(g_off, g_idx, n, nnz, BFS_DEVICE_PTRS | BFS_BORROW,
-                                      nullptr, &v);
+            bfs_config vc;  // a view runs batches only: no single-source head records
+            bfs_config_default(&vc);
+            vc.bu_head = 0;
+            status = bfs_graph_create(g_off, g_idx, n, nnz, BFS_DEVICE_PTRS | BFS_BORROW, &vc,
+                                      &v);
             if (status == BFS_OK) {
                 bfs_batch_config bc;
                 bfs_graph_get_batch_config(g_src, &bc);

@@ -23,8 +23,10 @@ def check_run(o_off, o_idx, graph, root, policy=None, forced=None, alpha=14.0, b
     assert oracle.check_parents(o_off, o_idx, root, lv, pa) == 0
     if policy is None:
         policy = oracle.POLICY_FORCED if forced is not None else oracle.POLICY_EDGE
+    # bu_head 2: the bottom-up step tests each vertex's hub before its row
+    hint = oracle.hub(o_off, o_idx) if graph.config.bu_head == 2 else None
     h_lv, h_pa, dirs, tr = oracle.hybrid_bfs(o_off, o_idx, root, policy, alpha, beta,
-                                             forced=forced)
+                                             forced=forced, hint=hint)
     st = graph.stats()
     L = st.layers
     assert [x["direction"] for x in L] == dirs.tolist()
@@ -84,7 +86,8 @@ def test_closed_form_graphs_forced_directions(name, pat, prune, loop):
         s, d = inputs.random_edges(n, 3 * n, 5)
     forced = FORCED[pat]
     o_off, o_idx, g = make(n, s, d, forced=forced, prune_components=prune,
-                           bu_list_percent=100 if prune else 0, device_loop=loop)
+                           bu_list_percent=100 if prune else 0, device_loop=loop,
+                           bu_head=(prune + 2 * loop) % 3)
     for r in sorted({0, n // 2, n - 1}):
         check_run(o_off, o_idx, g, r, forced=forced)
 
@@ -100,7 +103,7 @@ def test_policies_on_skewed_graphs(seed, policy, claim):
         s, d = oracle.gen_edges(oracle.RMAT, 12 + seed // 2, 8, seed)
         n = 1 << (12 + seed // 2)
     o_off, o_idx, g = make(n, s, d, policy=policy, td_claim=claim, bu_words=[1, 2, 4][seed % 3],
-                           bu_head=(seed // 3 + claim) % 2, prune_components=(seed + claim) % 2,
+                           bu_head=(seed // 2 + claim) % 3, prune_components=(seed + claim) % 2,
                            bu_list_percent=[0, 10, 100][(seed + claim) % 3], device_loop=claim)
     for r in oracle.sample_roots(o_off, n, seed, 4):
         check_run(o_off, o_idx, g, int(r), policy=policy)
@@ -126,7 +129,12 @@ def test_degree_bin_boundaries(deg, pat):
                 dict(forced=forced, device_loop=1),
                 dict(forced=forced, device_loop=1, bu_list_percent=100, td_grid_degree=64),
                 dict(forced=forced, bu_head=1, bu_probe=2),
-                dict(forced=forced, bu_head=1, bu_probe=4, bu_words=2)]:
+                dict(forced=forced, bu_head=1, bu_probe=4, bu_words=2),
+                dict(forced=forced, bu_head=2, bu_probe=2),
+                dict(forced=forced, bu_head=2, bu_probe=1, bu_words=4),
+                dict(forced=forced, bu_head=2, bu_list_percent=100, bu_probe=1),
+                dict(forced=forced, bu_head=2, device_loop=1),
+                dict(forced=forced, bu_head=2, device_loop=1, bu_list_percent=100)]:
         o_off, o_idx, g = make(n, s, d, **cfg)
         for r in [0, 1, n - 1, deg // 2]:
             check_run(o_off, o_idx, g, r, forced=forced)
@@ -165,6 +173,10 @@ def test_rmat_scale16_all_64_roots():
     g.set_config(config(device_loop=0))    # the same 64 roots with the host-driven loop
     for r in roots:
         check_run(o_off, o_idx, g, int(r))
+    for head in (1, 2):                     # and with each kind of head record
+        g.set_config(config(device_loop=0, bu_head=head))
+        for r in roots[:16]:
+            check_run(o_off, o_idx, g, int(r))
 
 
 @pytest.mark.parametrize("kind,seed", [(oracle.RMAT, 1), (oracle.ER, 3)])
