@@ -208,9 +208,11 @@ struct TdArgs {
     int32_t new_level;
     int queue_mode;  // 1: append winners to q_next; 0: next bitmap only
     int claim;       // 0: atomicCAS on parent; 1: atomicOr on the visited word
+    int defer;       // 1: a winner stores only its parent and next bit; its
+                     // level and the n_f / m_f counts come from td_post
 };
 
-// K edges (u[k], v[k]) per lane of the top-down step (Alg. 1, lines 3-6),
+// K edges (u[k], v[k]) per lane of the top-down step (the inner loop of Alg. 1),
 // called by all 32 lanes together; valid[k] masks missing edges. The visited
 // bitmap (L2-resident) filters first. The claim is either the CAS of
 // parent[v] from -1 to u (claim 0), or a fetch-or of v's bit into its
@@ -255,10 +257,12 @@ __device__ __forceinline__ void td_visit(const TdArgs &a, const bool (&valid)[K]
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         if (won[k]) {
-            a.level[v[k]] = a.new_level;
             atomicOr(a.next_bm + (v[k] >> 5), 1u << (v[k] & 31));
-            mf += deg_of(a.off, v[k]);
-            nf += 1;
+            if (!a.defer) {
+                a.level[v[k]] = a.new_level;
+                mf += deg_of(a.off, v[k]);
+                nf += 1;
+            }
         }
     }
     if (a.queue_mode) {
@@ -465,6 +469,60 @@ __global__ void __launch_bounds__(kBlock) td_big_kernel(TdArgs a, const int32_t 
                                                         const unsigned long long *big_count,
                                                         unsigned long long *next_mf) {
     td_big_phase<false>(a, big, big_count, next_mf);
+}
+
+// A bitmap-output top-down layer defers its winners' level stores and
+// counts to td_post when the vertices it can still find (unvisited, degree
+// > 0) outnumber the bitmap words; with fewer, one random store per winner
+// costs less than a pass over the bitmap.
+__host__ __device__ inline int td_defer(int queue_mode, int64_t findable, int64_t nw) {
+    return !queue_mode && findable >= nw ? 1 : 0;
+}
+
+// Completes a deferred top-down layer from its next bitmap: level = d+1 for
+// every new frontier vertex, and the counters n_f (popcount) and m_f (degree
+// sum) of the next layer. A warp takes 8 words per round and lane i handles
+// bit i of each, so the level stores and row-bound loads are coalesced
+// instead of one random sector per winner.
+template <bool CO>
+__device__ __forceinline__ void td_post_phase(const int64_t *__restrict__ off,
+                                              const uint32_t *__restrict__ next, int64_t nw,
+                                              int32_t *__restrict__ level, int32_t new_level,
+                                              unsigned long long *next_nf,
+                                              unsigned long long *next_mf) {
+    const unsigned lane = lane_id();
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t my_nf = 0, my_mf = 0;
+    for (int64_t w0 = gw * 8; w0 < nw; w0 += tw * 8) {
+        uint32_t x[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = w0 + k < nw ? ld<CO>(next + w0 + k) : 0u;
+        int64_t b[8], e[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int64_t v = (w0 + k) * 32 + lane;
+            const bool on = (x[k] >> lane) & 1u;
+            b[k] = on ? off[v] : 0;
+            e[k] = on ? off[v + 1] : 0;
+            if (on) level[v] = new_level;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            my_mf += e[k] - b[k];
+            my_nf += (x[k] >> lane) & 1u;
+        }
+    }
+    block_add3(my_nf, my_mf, 0, next_nf, next_mf, nullptr);
+}
+
+__global__ void __launch_bounds__(kBlock) td_post_kernel(const int64_t *__restrict__ off,
+                                                         const uint32_t *__restrict__ next,
+                                                         int64_t nw, int32_t *__restrict__ level,
+                                                         int32_t new_level,
+                                                         unsigned long long *next_nf,
+                                                         unsigned long long *next_mf) {
+    td_post_phase<false>(off, next, nw, level, new_level, next_nf, next_mf);
 }
 
 
@@ -1050,8 +1108,9 @@ __global__ void __launch_bounds__(kBlock, 4) bfs_persistent_kernel(SsPersist p) 
                 break;
             }
             const int queue_mode = m_f <= kQueueModeMaxEdges ? 1 : 0;
+            const int defer = td_defer(queue_mode, n_u - p.deg0, p.nw);
             TdArgs a{p.off, p.idx, p.visited, next, p.parent, p.level, q_next,
-                     (unsigned long long *)(sn + T_NF), d + 1, queue_mode, p.cfg.td_claim};
+                     (unsigned long long *)(sn + T_NF), d + 1, queue_mode, p.cfg.td_claim, defer};
             int64_t pw = (n_f + td_warps - 1) / td_warps;
             const int per_warp = (int)(pw < 1 ? 1 : (pw > 32 ? 32 : pw));
             int64_t gd = m_f / td_warps;
@@ -1066,6 +1125,15 @@ __global__ void __launch_bounds__(kBlock, 4) bfs_persistent_kernel(SsPersist p) 
                 }
                 td_big_phase<true>(a, p.big, (const unsigned long long *)(sc + T_BIG),
                                    (unsigned long long *)(sn + T_MF));
+            }
+            if (defer) {
+                if (!grid_barrier(p.bar, p.err, expected, p.timeout_ns)) {
+                    status = BFS_ERR_TIMEOUT;
+                    break;
+                }
+                td_post_phase<true>(p.off, next, p.nw, p.level, d + 1,
+                                    (unsigned long long *)(sn + T_NF),
+                                    (unsigned long long *)(sn + T_MF));
             }
             have_queue = queue_mode != 0;
         } else {
@@ -1560,8 +1628,10 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                 // serialise; a large layer leaves only the next bitmap, and the
                 // queue is rebuilt by b2q if the next layer is top-down too.
                 const int queue_mode = m_f <= kQueueModeMaxEdges ? 1 : 0;
+                const int defer = td_defer(queue_mode, n_u - g->deg0, g->nw);
                 TdArgs a{g->off, g->idx, g->visited, next, parent, level, q_next,
-                         (unsigned long long *)(slot_next + T_NF), d + 1, queue_mode, cfg.td_claim};
+                         (unsigned long long *)(slot_next + T_NF), d + 1, queue_mode, cfg.td_claim,
+                         defer};
                 // Entries per warp so that a small frontier still covers the GPU,
                 // and the grid-spread threshold at the frontier's edges per warp.
                 const int per_warp = (int)std::min<int64_t>(32, std::max<int64_t>(1, (n_f + td_warps - 1) / td_warps));
@@ -1582,6 +1652,11 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                               (const unsigned long long *)(slot_cur + T_BIG),
                               (unsigned long long *)(slot_next + T_MF));
                 }
+                if (defer)
+                    GB_LAUNCH(td_post_kernel, grid_cap(g->nw, kBlock / 4, 8), kBlock, 0, st,
+                              g->off, next, g->nw, level, d + 1,
+                              (unsigned long long *)(slot_next + T_NF),
+                              (unsigned long long *)(slot_next + T_MF));
                 have_queue = queue_mode != 0;
             } else {
                 if (timing) GB_CK(cudaEventRecord(event(e0 + 1), st));
@@ -1769,8 +1844,10 @@ extern "C" BFS_API bfs_status bfs_run_noalloc(const int64_t *offsets, const int3
                           (n + 31) / 32, q_cur, (unsigned long long *)(slot_cur + T_CONV));
             GB_CK(cudaMemsetAsync(next, 0, (size_t)nw_pad * 4, st));
             const int queue_mode = m_f <= kQueueModeMaxEdges ? 1 : 0;
+            const int defer = td_defer(queue_mode, n_u, (n + 31) / 32);
             TdArgs a{offsets, indices, visited, next, parent_out, level_out, q_next,
-                     (unsigned long long *)(slot_next + T_NF), d + 1, queue_mode, cfg.td_claim};
+                     (unsigned long long *)(slot_next + T_NF), d + 1, queue_mode, cfg.td_claim,
+                     defer};
             const int per_warp = (int)std::min<int64_t>(
                 32, std::max<int64_t>(1, (n_f + td_warps - 1) / td_warps));
             const int64_t grid_deg = std::min<int64_t>(
@@ -1786,6 +1863,11 @@ extern "C" BFS_API bfs_status bfs_run_noalloc(const int64_t *offsets, const int3
                           (int)std::max<int64_t>(1, std::min<int64_t>(m_f / 4096 + 1,
                                                                       (int64_t)sm_count() * td_occ)),
                           kBlock, 0, st, a, big, (const unsigned long long *)(slot_cur + T_BIG),
+                          (unsigned long long *)(slot_next + T_MF));
+            if (defer)
+                GB_LAUNCH(td_post_kernel, grid_cap((n + 31) / 32, kBlock / 4, 8), kBlock, 0, st,
+                          offsets, next, (n + 31) / 32, level_out, d + 1,
+                          (unsigned long long *)(slot_next + T_NF),
                           (unsigned long long *)(slot_next + T_MF));
             have_queue = queue_mode != 0;
         } else {

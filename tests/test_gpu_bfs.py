@@ -179,6 +179,20 @@ def test_rmat_scale16_all_64_roots():
             check_run(o_off, o_idx, g, int(r))
 
 
+@pytest.mark.parametrize("pat", ["td", "late_bu", "alt"])
+@pytest.mark.parametrize("loop", [0, 1])
+def test_large_top_down_layers(pat, loop):
+    # forced top-down layers with more than 2^18 frontier edges leave only the
+    # next bitmap, and with many vertices still findable they defer level
+    # stores and counts to a pass over that bitmap: counters stay exact
+    n, o_off, o_idx, g_off, g_idx = _rmat_both(17, 16, 4)
+    g = gb.Graph(g_off, g_idx, config(forced=FORCED[pat], device_loop=loop))
+    for r in oracle.sample_roots(o_off, n, 5, 3):
+        check_run(o_off, o_idx, g, int(r), forced=FORCED[pat])
+    if pat == "td":
+        assert max(x["m_f"] for x in g.stats().layers) > (1 << 18)
+
+
 @pytest.mark.parametrize("kind,seed", [(oracle.RMAT, 1), (oracle.ER, 3)])
 def test_scale20_all_64_roots(kind, seed):
     # R-MAT scale 20 (the paper's one-million-vertex size) and its ER control
