@@ -738,14 +738,14 @@ __global__ void __launch_bounds__(kBlock, 4) bu_kernel(
 }
 
 
-// Unvisited bitmap -> list of the vertices still to find (bits of ~visited;
-// degree-0 vertices and ids past n are set in visited and so never listed).
-// Same block scan as b2q_kernel.
+// Bitmap -> list of its set bits after XOR with `flip`: flip = ~0 lists the
+// vertices still to find from the visited bitmap (degree-0 vertices and ids
+// past n are set in visited and so never listed); flip = 0 lists the pend
+// bits of the two-pass bottom-up step. Same block scan as b2q_kernel.
 template <bool CO>
-__device__ __forceinline__ void unvisited_list_phase(const uint32_t *__restrict__ vis,
-                                                                int64_t nw,
-                                                                int32_t *__restrict__ list,
-                                                                unsigned long long *count) {
+__device__ __forceinline__ void bits_list_phase(const uint32_t *__restrict__ vis, uint32_t flip,
+                                                int64_t nw, int32_t *__restrict__ list,
+                                                unsigned long long *count) {
     __shared__ int wtot[kBlock / 32];
     __shared__ unsigned long long base_s;
     const unsigned lane = lane_id(), w = threadIdx.x >> 5;
@@ -755,7 +755,7 @@ __device__ __forceinline__ void unvisited_list_phase(const uint32_t *__restrict_
         int c = 0;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            words[k] = (w0 + k < nw) ? ~ld<CO>(vis + w0 + k) : 0u;
+            words[k] = (w0 + k < nw) ? ld<CO>(vis + w0 + k) ^ flip : 0u;
             c += __popc(words[k]);
         }
         int tot;
@@ -783,11 +783,11 @@ __device__ __forceinline__ void unvisited_list_phase(const uint32_t *__restrict_
     }
 }
 
-__global__ void __launch_bounds__(kBlock) unvisited_list_kernel(const uint32_t *__restrict__ vis,
-                                                                int64_t nw,
-                                                                int32_t *__restrict__ list,
-                                                                unsigned long long *count) {
-    unvisited_list_phase<false>(vis, nw, list, count);
+__global__ void __launch_bounds__(kBlock) bits_list_kernel(const uint32_t *__restrict__ vis,
+                                                           uint32_t flip, int64_t nw,
+                                                           int32_t *__restrict__ list,
+                                                           unsigned long long *count) {
+    bits_list_phase<false>(vis, flip, nw, list, count);
 }
 
 
@@ -914,6 +914,74 @@ __device__ __forceinline__ void bu_list_phase(
         my_ex += ex;
     }
     block_add3(my_nf, my_mf, my_ex, slot_next + T_NF, slot_next + T_MF, slot_next + T_EXAM);
+}
+
+// First pass of the two-pass bottom-up step (hub head records): every
+// unvisited vertex tests only its hub against the frontier. A warp owns 8
+// consecutive bitmap words per round (lane i = bit i of each), so it writes
+// their next and pend words and ORs the found bits into visited without
+// atomics or block barriers; the warps run independently and keep many head
+// loads in flight. pend marks the vertices whose hub missed and whose row
+// must be scanned (bits_list_phase then compacts them for bu_list_phase); a
+// vertex of degree 1 is not marked, since its only neighbour is the hub (its
+// one-entry scan is counted here). Every word below nw_pad is written, so
+// next and pend need no clearing.
+template <bool CO>
+__device__ __forceinline__ void bu_hub_phase(
+    const int2 *__restrict__ head, int64_t nw_pad, uint32_t *__restrict__ visited,
+    const uint32_t *__restrict__ front, uint32_t *__restrict__ next_bm,
+    uint32_t *__restrict__ pend, int32_t *__restrict__ parent, int32_t *__restrict__ level,
+    int32_t new_level, unsigned long long *slot_next, int64_t *zero_slot) {
+    constexpr int R = 8;
+    if (blockIdx.x == 0 && threadIdx.x < kFields) zero_slot[threadIdx.x] = 0;
+    const unsigned lane = lane_id();
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t my_nf = 0, my_mf = 0, my_ex = 0;
+    for (int64_t w0 = gw * R; w0 < nw_pad; w0 += tw * R) {  // nw_pad is a multiple of 32
+        uint32_t vw[R];
+        int2 h[R];
+        uint32_t fw[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) vw[k] = ld<CO>(visited + w0 + k);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const bool unv = !((vw[k] >> lane) & 1u);  // bits past n are set
+            h[k] = unv ? __ldg(head + (w0 + k) * 32 + lane) : make_int2(-1, 0);
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) fw[k] = h[k].x >= 0 ? ldro<CO>(front + (h[k].x >> 5)) : 0u;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int64_t v = (w0 + k) * 32 + lane;
+            const bool probed = h[k].x >= 0;
+            const bool found = probed && ((fw[k] >> (h[k].x & 31)) & 1u);
+            my_ex += probed ? (found || h[k].y > 1 ? 1 : 2) : 0;
+            if (found) {
+                parent[v] = h[k].x;
+                level[v] = new_level;
+                my_mf += h[k].y;
+                my_nf += 1;
+            }
+            const unsigned fb = __ballot_sync(0xffffffffu, found);
+            const unsigned pb = __ballot_sync(0xffffffffu, probed && !found && h[k].y > 1);
+            if (lane == 0) {
+                next_bm[w0 + k] = fb;
+                pend[w0 + k] = pb;
+                if (fb) visited[w0 + k] = vw[k] | fb;
+            }
+        }
+    }
+    block_add3(my_nf, my_mf, my_ex, slot_next + T_NF, slot_next + T_MF, slot_next + T_EXAM);
+}
+
+__global__ void __launch_bounds__(kBlock, 4) bu_hub_kernel(
+    const int2 *__restrict__ head, int64_t nw_pad, uint32_t *__restrict__ visited,
+    const uint32_t *__restrict__ front, uint32_t *__restrict__ next_bm,
+    uint32_t *__restrict__ pend, int32_t *__restrict__ parent, int32_t *__restrict__ level,
+    int32_t new_level, unsigned long long *slot_next, int64_t *zero_slot) {
+    bu_hub_phase<false>(head, nw_pad, visited, front, next_bm, pend, parent, level, new_level,
+                        slot_next, zero_slot);
 }
 
 __global__ void __launch_bounds__(kBlock) bu_list_kernel(
@@ -1140,7 +1208,7 @@ __global__ void __launch_bounds__(kBlock, 4) bfs_persistent_kernel(SsPersist p) 
             const int64_t active = n_u - p.deg0;
             if (p.cfg.bu_list_percent > 0 && active * 100 <= (int64_t)p.cfg.bu_list_percent * p.n) {
                 for (int64_t i = t0; i < p.nw_pad; i += stride) next[i] = 0u;
-                unvisited_list_phase<true>(p.visited, p.nw, q_next,
+                bits_list_phase<true>(p.visited, ~0u, p.nw, q_next,
                                            (unsigned long long *)(sc + T_ULIST));
                 if (!grid_barrier(p.bar, p.err, expected, p.timeout_ns)) {
                     status = BFS_ERR_TIMEOUT;
@@ -1310,6 +1378,7 @@ void free_graph(bfs_graph *g) {
     if (g->h_pctl) cudaFreeHost(g->h_pctl);
     cudaFree(g->bm_a);
     cudaFree(g->bm_b);
+    cudaFree(g->pend);
     cudaFree(g->q_a);
     cudaFree(g->q_b);
     cudaFree(g->big);
@@ -1455,6 +1524,8 @@ extern "C" BFS_API bfs_status bfs_graph_create(const int64_t *offsets, const int
     GB_CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->bu_blocks_per_sm[5], BU4H, kBlock, 0));
     GB_CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->td_blocks_per_sm, td_kernel, kBlock, 0));
     GB_CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->bu_list_blocks_per_sm, bu_list_kernel,
+                                                         kBlock, 0));
+    GB_CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->bu_hub_blocks_per_sm, bu_hub_kernel,
                                                          kBlock, 0));
     if (g->cfg.bu_head) {
         const bfs_status hs = build_head(g, g->cfg.bu_head, 0);
@@ -1666,13 +1737,31 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                     // sparse layer: a compacted list of them, one lane each
                     ls.converted = 2;
                     GB_CK(cudaMemsetAsync(next, 0, (size_t)g->nw_pad * 4, st));
-                    GB_LAUNCH(unvisited_list_kernel, grid_cap(g->nw, kBlock * 4, 8), kBlock, 0, st,
-                              g->visited, g->nw, q_next, (unsigned long long *)(slot_cur + T_ULIST));
+                    GB_LAUNCH(bits_list_kernel, grid_cap(g->nw, kBlock * 4, 8), kBlock, 0, st,
+                              g->visited, ~0u, g->nw, q_next,
+                              (unsigned long long *)(slot_cur + T_ULIST));
                     GB_LAUNCH(bu_list_kernel,
                               grid_cap((active + 31) / 32, kBlock / 32, g->bu_list_blocks_per_sm),
                               kBlock, 0, st, g->off, g->idx, cfg.bu_head ? g->head : nullptr,
                               hskip, q_next, (const unsigned long long *)(slot_cur + T_ULIST),
                               g->visited, front, next, parent, level, d + 1, cfg.bu_probe,
+                              (unsigned long long *)slot_next, slot_zero);
+                } else if (cfg.bu_head == 2) {
+                    // two passes: hub probes over the words, then the rows of
+                    // the vertices whose hub missed, one lane each
+                    ls.converted = 3;
+                    if (!g->pend) GB_CK(cudaMalloc(&g->pend, (size_t)g->nw_pad * 4));
+                    GB_LAUNCH(bu_hub_kernel, grid_cap(g->nw_pad, kBlock / 32 * 8, g->bu_hub_blocks_per_sm),
+                              kBlock, 0, st, g->head, g->nw_pad, g->visited, front, next, g->pend,
+                              parent, level, d + 1, (unsigned long long *)slot_next, slot_zero);
+                    GB_LAUNCH(bits_list_kernel, grid_cap(g->nw, kBlock * 4, 8), kBlock, 0, st,
+                              g->pend, 0u, g->nw, q_next,
+                              (unsigned long long *)(slot_cur + T_ULIST));
+                    GB_LAUNCH(bu_list_kernel,
+                              grid_cap((active + 31) / 32, kBlock / 32, g->bu_list_blocks_per_sm),
+                              kBlock, 0, st, g->off, g->idx, nullptr, 0, q_next,
+                              (const unsigned long long *)(slot_cur + T_ULIST), g->visited, front,
+                              next, parent, level, d + 1, cfg.bu_probe,
                               (unsigned long long *)slot_next, slot_zero);
                 } else {
                     decltype(BU1) const kernels[6] = {BU1, BU2, BU4, BU1H, BU2H, BU4H};
