@@ -51,6 +51,8 @@ def parse():
                    help="single: the headline line (single-source + batched); "
                         "serve: the serving stream over 8 resident graphs")
     p.add_argument("--no-batch", action="store_true", help="skip the batched comparison")
+    p.add_argument("--device-loop", type=int, default=2, choices=[0, 1, 2],
+                   help="bfs_config.device_loop: 0 host loop, 1 device loop, 2 library default")
     p.add_argument("--batch-scale", type=int, default=22)
     p.add_argument("--serve-queries", type=int, default=10000)
     p.add_argument("--serve-seconds", type=float, default=4.0,
@@ -68,11 +70,11 @@ def peaks():
 
 
 def measured_traffic(scale, edgefactor):
-    """DRAM bytes per dense bottom-up launch from the committed ncu summary, or
-    None when the workload differs or the kernel changed since the capture (the
-    summary records the SHA-1 of the bu_kernel template's source text)."""
+    """DRAM bytes per hub sweep launch from the committed ncu summary, or None
+    when the workload differs or the kernel changed since the capture (the
+    summary records the SHA-1 of the bu_hub_phase source text)."""
     import hashlib
-    path = os.path.join(HERE, "profiles", "bu_kernel_dram_rmat26.md")
+    path = os.path.join(HERE, "profiles", "bu_hub_kernel_dram_rmat26.md")
     if (scale, edgefactor) != (26, 16) or not os.path.exists(path):
         return None
     vals = {}
@@ -83,8 +85,8 @@ def measured_traffic(scale, edgefactor):
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip()
     src = open(os.path.join(HERE, "paper_1704_02259_gb300", "csrc", "bfs.cu")).read()
-    a = src.find("template <int W, int CH, bool HEAD>")
-    b = src.find("// Unvisited bitmap -> list", a)
+    a = src.find("// First pass of the two-pass bottom-up step")
+    b = src.find("__global__ void __launch_bounds__(kBlock, 4) bu_hub_kernel(", a)
     if a < 0 or b < 0:
         return None
     if hashlib.sha1(src[a:b].encode()).hexdigest() != vals.get("kernel_source_sha1"):
@@ -372,6 +374,7 @@ def main():
     deg1 = int(((off[1:] - off[:-1]) > 0).sum().item())  # vertices of degree >= 1
     cfg = gb.default_config()
     cfg.timing = 1
+    cfg.device_loop = args.device_loop
     g = gb.Graph(off, idx, cfg)
     roots = gb.sample_roots(off, n, args.root_seed + rank, args.roots).cpu().tolist()
     level = torch.empty(n, dtype=torch.int32, device="cuda")
@@ -413,24 +416,34 @@ def main():
     teps = [e / t for e, t in zip(edges, times)]
     my_hmean = hmean(teps)
     my_total_s = sum(times)
-    # roofline of the bottom-up step kernel (the dominant kernel): algorithmic
-    # bytes per launch over its CUDA-event duration
-    # (dense word-per-warp layers; the sparse list layers are reported apart)
-    bu_bytes = bu_ms = 0.0
+    # roofline of the hub sweep kernel (bu_hub_kernel, the first pass of the
+    # dense bottom-up layers and the dominant kernel): algorithmic bytes per
+    # launch over its own CUDA-event duration. Per launch: the visited words
+    # read, the next / pend / visited words written (n/2 bytes together), one
+    # 8-byte head record per probed vertex (unvisited, degree >= 1) and the
+    # parent and level of each vertex its hub finds (8 bytes).
+    hub_bytes = hub_ms = 0.0
+    scan_ms = 0.0
     bl_bytes = bl_ms = 0.0
+    bu1_bytes = bu1_ms = 0.0
     td_bytes = td_ms = 0.0
-    n_bu = n_bl = 0
+    n_hub = n_bl = n_bu1 = 0
     for _, _, st in recs:
         for L in st.layers:
-            if L["direction"] == 1 and L["converted"] != 2:
-                bu_bytes += n / 4 + 8 * L["n_u"] + 4 * L["examined"] + 8 * L["found"]
-                bu_ms += L["ms_main"]
-                n_bu += 1
-            elif L["direction"] == 1:
-                active = L["n_u"] - (n - deg1)
+            active = L["n_u"] - (n - deg1)  # unvisited vertices of degree >= 1
+            if L["direction"] == 1 and L["converted"] == 3:
+                hub_bytes += n / 2 + 8 * active + 8 * L["hub_found"]
+                hub_ms += L["ms_sweep"]
+                scan_ms += L["ms_main"] - L["ms_sweep"]
+                n_hub += 1
+            elif L["direction"] == 1 and L["converted"] == 2:
                 bl_bytes += n / 8 + 12 * active + 4 * L["examined"] + 16 * L["found"]
                 bl_ms += L["ms_main"]
                 n_bl += 1
+            elif L["direction"] == 1:
+                bu1_bytes += n / 4 + 8 * L["n_u"] + 4 * L["examined"] + 8 * L["found"]
+                bu1_ms += L["ms_main"]
+                n_bu1 += 1
             else:
                 td_bytes += 20 * L["n_f"] + 4 * L["m_f"] + 28 * L["found"]
                 td_ms += L["ms_main"]
@@ -464,7 +477,7 @@ def main():
             dist.destroy_process_group()
         return
     peak, peak_kind = peaks()
-    achieved = (bu_bytes / (bu_ms / 1e3)) / 1e9 if bu_ms > 0 else 0.0
+    achieved = (hub_bytes / (hub_ms / 1e3)) / 1e9 if hub_ms > 0 else 0.0
     m_c = statistics.median(edges)
     b_sweep = 4 * nnz + 8 * (n + 1) + 2 * n / 8 + 8 * n
     roof_teps = m_c * peak * 1e9 / b_sweep
@@ -479,15 +492,18 @@ def main():
                    "graph_seed": args.graph_seed, "root_seed": args.root_seed,
                    "l2": "inputs larger than L2 (CSR of scale 26 is ~8 GB)",
                    "policy": "edge alpha=14 beta=24", "bu_probe": cfg.bu_probe},
-        "roofline": {"bound": "hbm", "kernel": "bu_kernel", "achieved": achieved,
+        "roofline": {"bound": "hbm", "kernel": "bu_hub_kernel", "achieved": achieved,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": measured_traffic(scale, ef),
-                     "algorithmic_bytes_per_launch": bu_bytes / max(1, n_bu),
-                     "avg_launch_ms": bu_ms / max(1, n_bu)},
+                     "algorithmic_bytes_per_launch": hub_bytes / max(1, n_hub),
+                     "avg_launch_ms": hub_ms / max(1, n_hub), "launches": n_hub},
         "sweep_roofline": {"bytes": b_sweep, "teps": roof_teps / 1e9, "unit": "GTEPS",
                            "frac": value / roof_teps if world == 1 else None},
+        "bu_scan_step": {"ms": scan_ms, "layers": n_hub},
         "bu_list_step": {"achieved_gbs": (bl_bytes / (bl_ms / 1e3)) / 1e9 if bl_ms > 0 else 0.0,
                          "ms": bl_ms, "launches": n_bl},
+        "bu_one_pass_step": {"achieved_gbs": (bu1_bytes / (bu1_ms / 1e3)) / 1e9
+                             if bu1_ms > 0 else 0.0, "ms": bu1_ms, "launches": n_bu1},
         "td_step": {"achieved_gbs": (td_bytes / (td_ms / 1e3)) / 1e9 if td_ms > 0 else 0.0,
                     "ms": td_ms},
         "aggregate_teps": sum(edges) / sum(times) / 1e9,

@@ -149,7 +149,14 @@ typedef struct bfs_config {
                                 its first entry; Alg. 2 accepts any frontier
                                 neighbour, so levels are unchanged and the
                                 parent is the hub whenever it is in the
-                                frontier); 0 = read the CSR only            */
+                                frontier). With 2, graphs with at least 8
+                                bitmap words per resident warp run each dense
+                                bottom-up layer in two passes: a sweep that
+                                tests every unvisited vertex's hub, then a
+                                row scan of the compacted hub misses, one
+                                thread each (n/8 more bytes); smaller graphs
+                                test the hub inside the one-pass scan.
+                                0 = read the CSR only                        */
     int32_t prune_components;/* 1 = vertices outside the root's connected
                                 component start as visited, so bottom-up
                                 layers skip them (results unchanged; only the
@@ -170,7 +177,7 @@ typedef struct bfs_config {
                                 device, between bounded grid barriers (no host
                                 round trip per layer; per-layer times are not
                                 recorded); 0 = host loop; 2 (default) = the
-                                device loop for n <= 2^23, where the host round
+                                device loop for n <= 2^25, where the host round
                                 trips weigh most, the host loop above         */
     int32_t reserved[2];
 } bfs_config;
@@ -225,7 +232,9 @@ typedef struct bfs_layer_stats {
     int32_t direction;  /* 0 = top-down, 1 = bottom-up                          */
     int32_t converted;  /* top-down: 1 = the frontier bitmap was turned into a
                            queue; bottom-up: 2 = the layer ran on the compacted
-                           list of vertices still to find (bu_list_percent)   */
+                           list of vertices still to find (bu_list_percent),
+                           3 = it ran in two passes (hub sweep, then the row
+                           scans of the hub misses; bu_head = 2)              */
     int64_t n_f;        /* vertices in the frontier                            */
     int64_t m_f;        /* sum of their degrees                                */
     int64_t n_u;        /* vertices not yet visited                            */
@@ -235,7 +244,11 @@ typedef struct bfs_layer_stats {
                            bottom-up                                           */
     int64_t found;      /* vertices of the next layer                          */
     float ms_total;     /* layer time, when cfg.timing = 1 (else 0)            */
-    float ms_main;      /* time of the layer's main step kernel                */
+    float ms_main;      /* time of the layer's main step kernel(s)            */
+    float ms_sweep;     /* converted = 3: time of the hub sweep pass alone    */
+    float pad;
+    int64_t hub_found;  /* converted = 3: vertices found by their hub (host
+                           loop only; 0 in the device loop)                    */
 } bfs_layer_stats;
 
 /* Copies up to `cap` layer records of the last run into `out`; *layers gets

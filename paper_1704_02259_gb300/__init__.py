@@ -50,7 +50,9 @@ class LayerStats(ctypes.Structure):
     _fields_ = [("direction", ctypes.c_int32), ("converted", ctypes.c_int32),
                 ("n_f", ctypes.c_int64), ("m_f", ctypes.c_int64), ("n_u", ctypes.c_int64),
                 ("m_u", ctypes.c_int64), ("examined", ctypes.c_int64), ("found", ctypes.c_int64),
-                ("ms_total", ctypes.c_float), ("ms_main", ctypes.c_float)]
+                ("ms_total", ctypes.c_float), ("ms_main", ctypes.c_float),
+                ("ms_sweep", ctypes.c_float), ("pad", ctypes.c_float),
+                ("hub_found", ctypes.c_int64)]
 
 
 class BatchConfig(ctypes.Structure):

@@ -167,32 +167,44 @@ __global__ void init_kernel(int64_t n, int64_t nw_pad, int32_t root,
     if (t0 == 0) queue[0] = root;
 }
 
-__device__ __forceinline__ void block_add3(int64_t a, int64_t b, int64_t c,
+__device__ __forceinline__ void block_add4(int64_t a, int64_t b, int64_t c, int64_t e,
                                            unsigned long long *dst_a,
                                            unsigned long long *dst_b,
-                                           unsigned long long *dst_c) {
-    __shared__ long long red[3][kBlock / 32];
+                                           unsigned long long *dst_c,
+                                           unsigned long long *dst_e) {
+    __shared__ long long red[4][kBlock / 32];
     a = warp_sum(a);
     b = warp_sum(b);
     c = warp_sum(c);
+    e = warp_sum(e);
     const unsigned lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0) {
         red[0][w] = a;
         red[1][w] = b;
         red[2][w] = c;
+        red[3][w] = e;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        long long s0 = 0, s1 = 0, s2 = 0;
+        long long s0 = 0, s1 = 0, s2 = 0, s3 = 0;
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
             s0 += red[0][i];
             s1 += red[1][i];
             s2 += red[2][i];
+            s3 += red[3][i];
         }
         if (dst_a && s0) atomicAdd(dst_a, (unsigned long long)s0);
         if (dst_b && s1) atomicAdd(dst_b, (unsigned long long)s1);
         if (dst_c && s2) atomicAdd(dst_c, (unsigned long long)s2);
+        if (dst_e && s3) atomicAdd(dst_e, (unsigned long long)s3);
     }
+}
+
+__device__ __forceinline__ void block_add3(int64_t a, int64_t b, int64_t c,
+                                           unsigned long long *dst_a,
+                                           unsigned long long *dst_b,
+                                           unsigned long long *dst_c) {
+    block_add4(a, b, c, 0, dst_a, dst_b, dst_c, nullptr);
 }
 
 // State shared by the top-down expansion paths.
@@ -972,7 +984,8 @@ __device__ __forceinline__ void bu_hub_phase(
             }
         }
     }
-    block_add3(my_nf, my_mf, my_ex, slot_next + T_NF, slot_next + T_MF, slot_next + T_EXAM);
+    block_add4(my_nf, my_mf, my_ex, my_nf, slot_next + T_NF, slot_next + T_MF,
+               slot_next + T_EXAM, slot_next + T_HUB);
 }
 
 __global__ void __launch_bounds__(kBlock, 4) bu_hub_kernel(
@@ -1128,6 +1141,7 @@ struct SsPersist {
     const int32_t *idx;
     const int2 *head;  // head records for the bottom-up probe, or null
     int hskip;
+    uint32_t *pend;    // two-pass bottom-up (hub records): hub misses, else null
     int64_t n, nnz, nw, nw_pad, deg0;
     uint32_t *visited, *bm_a, *bm_b;
     int32_t *q_a, *q_b, *big;
@@ -1219,6 +1233,25 @@ __global__ void __launch_bounds__(kBlock, 4) bfs_persistent_kernel(SsPersist p) 
                                     p.visited, front, next, p.parent, p.level, d + 1,
                                     p.cfg.bu_probe, (unsigned long long *)sn, sz);
                 converted = 2;
+            } else if (p.pend && p.nw >= 8 * td_warps) {
+                // two passes: hub probes over the words, then the rows of the
+                // vertices whose hub missed, one lane each
+                bu_hub_phase<true>(p.head, p.nw_pad, p.visited, front, next, p.pend, p.parent,
+                                   p.level, d + 1, (unsigned long long *)sn, sz);
+                if (!grid_barrier(p.bar, p.err, expected, p.timeout_ns)) {
+                    status = BFS_ERR_TIMEOUT;
+                    break;
+                }
+                bits_list_phase<true>(p.pend, 0u, p.nw, q_next, (unsigned long long *)(sc + T_ULIST));
+                if (!grid_barrier(p.bar, p.err, expected, p.timeout_ns)) {
+                    status = BFS_ERR_TIMEOUT;
+                    break;
+                }
+                bu_list_phase<true>(p.off, p.idx, nullptr, 0, q_next,
+                                    (const unsigned long long *)(sc + T_ULIST), p.visited, front,
+                                    next, p.parent, p.level, d + 1, p.cfg.bu_probe,
+                                    (unsigned long long *)sn, sz);
+                converted = 3;
             } else {
                 if (p.head)
                     bu_phase<2, 4, true, true>(p.off, p.idx, p.head, p.nw_pad, p.visited, front,
@@ -1262,7 +1295,7 @@ __global__ void __launch_bounds__(kBlock, 4) bfs_persistent_kernel(SsPersist p) 
 }
 
 constexpr size_t kPctlSsBytes = (size_t)kSsMaxRecords * 8 * 8 + 64;
-constexpr int64_t kDeviceLoopAutoMaxN = 1ll << 23;  // device_loop = 2: on up to this n
+constexpr int64_t kDeviceLoopAutoMaxN = 1ll << 25;  // device_loop = 2: on up to this n
 
 // Runs the traversal as one cooperative launch of bfs_persistent_kernel and
 // reads back the per-layer records (init_kernel has already run on `st`).
@@ -1307,6 +1340,8 @@ bfs_status run_device_loop(bfs_graph *g, int32_t *level, int32_t *parent, cudaSt
     p.cfg = g->cfg;
     p.head = g->cfg.bu_head ? g->head : nullptr;
     p.hskip = g->cfg.bu_head == 1 ? 1 : 0;
+    if (g->cfg.bu_head == 2 && !g->pend) GB_CK(cudaMalloc(&g->pend, (size_t)g->nw_pad * 4));
+    p.pend = g->cfg.bu_head == 2 ? g->pend : nullptr;
     p.timeout_ns = 2000000000ull;  // 2 s per barrier wait
     void *args[] = {&p};
     // Grid sized to the graph: barrier cost grows with the block count, and a
@@ -1685,7 +1720,7 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
             int64_t *slot_cur = g->trace + (d % kRing) * kFields;
             int64_t *slot_next = g->trace + ((d + 1) % kRing) * kFields;
             int64_t *slot_zero = g->trace + ((d + 2) % kRing) * kFields;
-            const size_t e0 = (size_t)d * 3;
+            const size_t e0 = (size_t)d * 4;
             if (timing) GB_CK(cudaEventRecord(event(e0), st));
             if (!cur_bu) {
                 if (!have_queue) {
@@ -1746,7 +1781,8 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                               hskip, q_next, (const unsigned long long *)(slot_cur + T_ULIST),
                               g->visited, front, next, parent, level, d + 1, cfg.bu_probe,
                               (unsigned long long *)slot_next, slot_zero);
-                } else if (cfg.bu_head == 2) {
+                } else if (cfg.bu_head == 2 &&
+                           g->nw >= (int64_t)8 * sm_count() * g->bu_hub_blocks_per_sm * (kBlock / 32)) {
                     // two passes: hub probes over the words, then the rows of
                     // the vertices whose hub missed, one lane each
                     ls.converted = 3;
@@ -1754,6 +1790,7 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                     GB_LAUNCH(bu_hub_kernel, grid_cap(g->nw_pad, kBlock / 32 * 8, g->bu_hub_blocks_per_sm),
                               kBlock, 0, st, g->head, g->nw_pad, g->visited, front, next, g->pend,
                               parent, level, d + 1, (unsigned long long *)slot_next, slot_zero);
+                    if (timing) GB_CK(cudaEventRecord(event(e0 + 3), st));
                     GB_LAUNCH(bits_list_kernel, grid_cap(g->nw, kBlock * 4, 8), kBlock, 0, st,
                               g->pend, 0u, g->nw, q_next,
                               (unsigned long long *)(slot_cur + T_ULIST));
@@ -1778,6 +1815,7 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
             const int64_t found = g->h_slot[T_NF], m_new = g->h_slot[T_MF];
             ls.examined = cur_bu ? g->h_slot[T_EXAM] : m_f;
             ls.found = found;
+            if (ls.converted == 3 && cur_bu) ls.hub_found = g->h_slot[T_HUB];
             g->last.push_back(ls);
             n_u -= found;
             m_u -= m_new;
@@ -1789,11 +1827,14 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
         g->last_component_edges = degree_sum / 2;
         if (timing) {
             for (size_t d = 0; d < g->last.size(); ++d) {
-                float t0 = 0, t1 = 0;
-                cudaEventElapsedTime(&t0, g->events[3 * d], g->events[3 * d + 2]);
-                cudaEventElapsedTime(&t1, g->events[3 * d + 1], g->events[3 * d + 2]);
+                float t0 = 0, t1 = 0, t2 = 0;
+                cudaEventElapsedTime(&t0, g->events[4 * d], g->events[4 * d + 2]);
+                cudaEventElapsedTime(&t1, g->events[4 * d + 1], g->events[4 * d + 2]);
+                if (g->last[d].direction == 1 && g->last[d].converted == 3)
+                    cudaEventElapsedTime(&t2, g->events[4 * d + 1], g->events[4 * d + 3]);
                 g->last[d].ms_total = t0;
                 g->last[d].ms_main = t1;
+                g->last[d].ms_sweep = t2;
             }
         }
     }

@@ -11,7 +11,7 @@ namespace gbfs {
 
 constexpr int kRing = 64;  // trace ring slots (layers)
 constexpr int kFields = 8;
-enum TraceField { T_NF = 0, T_MF = 1, T_EXAM = 2, T_CONV = 3, T_BIG = 4, T_ULIST = 5 };
+enum TraceField { T_NF = 0, T_MF = 1, T_EXAM = 2, T_CONV = 3, T_BIG = 4, T_ULIST = 5, T_HUB = 6 };
 constexpr int kBlock = 256;
 constexpr int kBigBatch = 1024;
 constexpr int64_t kQueueModeMaxEdges = 1 << 18;
