@@ -266,13 +266,16 @@ BFS_API bfs_status bfs_last_run_stats(const bfs_graph *g, bfs_layer_stats *out, 
 /* vertex ORs its neighbours' frontier words and stops once every lane it  */
 /* still lacks is found: the paper's early exit, per lane set) or the      */
 /* top-down step of Alg. 1 (frontier words ORed into neighbours' next      */
-/* words), chosen per layer by the edge form of the Alg. 3 switch.         */
+/* words), chosen per layer by the edge form of the Alg. 3 switch. A root  */
+/* whose frontier empties has finished and leaves the set of live lanes.   */
+/* Levels are written once, at the end, from the frontier words that every */
+/* layer keeps in a ring of slots.                                         */
 /* ---------------------------------------------------------------------- */
 typedef struct bfs_batch_config {
     double alpha;         /* top-down -> bottom-up iff e_f > e_u / alpha, where
                              e_f = degree sum of vertices with a frontier bit
                              and e_u = degree sum of vertices still lacking
-                             some root's bit                                  */
+                             some live root's bit                             */
     double beta;          /* bottom-up -> top-down iff v_f < n / beta         */
     int32_t lane_probe;   /* bottom-up: neighbours a lane scans alone before
                              the warp-cooperative OR-reduction takes over     */
@@ -281,7 +284,13 @@ typedef struct bfs_batch_config {
     int32_t use_graph;    /* 1 = run the layers as one CUDA graph with a
                              device-side loop (no per-layer host round trip) */
     int32_t timing;       /* 1 = record CUDA events per layer                 */
-    int32_t reserved[8];
+    int32_t layer_slots;  /* frontier slots of the level ring, 2..16 (each
+                             n * W 64-bit words); 0 = as many as a quarter of
+                             the free device memory holds when the bitsets are
+                             allocated, 4..16. A traversal with more layers
+                             than slots writes the levels of the full slots
+                             before reusing them (correct, slower)           */
+    int32_t reserved[7];
 } bfs_batch_config;
 
 BFS_API void bfs_batch_config_default(bfs_batch_config *cfg);
@@ -293,9 +302,10 @@ BFS_API bfs_status bfs_graph_get_batch_config(const bfs_graph *g, bfs_batch_conf
  *   levels_out   device, caller-owned, k*n int8, row i = levels from roots[i]
  *                (level[v] = hop distance, -1 when unreachable)
  * A level above 127 does not fit: the traversal stops after writing level
- * 127 and returns BFS_ERR_DEPTH (no value wraps). The bitsets (three arrays
- * of n * ceil(k/64 rounded to 1, 2, 4 or 8) 64-bit words) are allocated on
- * first use and kept by the graph. Synchronous, like bfs_run. */
+ * 127 and returns BFS_ERR_DEPTH (no value wraps). The bitsets (seen and the
+ * frontier slots, each n * W 64-bit words with W = ceil(k/64) rounded to 1,
+ * 2, 4 or 8) are allocated on first use and kept by the graph. Synchronous,
+ * like bfs_run. */
 BFS_API bfs_status bfs_run_batch(bfs_graph *g, const int32_t *roots, int32_t k,
                                  int8_t *levels_out, void *stream);
 
@@ -306,7 +316,8 @@ typedef struct bfs_batch_layer_stats {
     int64_t v_f;         /* vertices holding at least one frontier bit        */
     int64_t e_f;         /* their degree sum                                  */
     int64_t pairs;       /* (root, vertex) pairs in the frontier              */
-    int64_t v_u;         /* vertices still lacking some root's bit            */
+    int64_t v_u;         /* vertices of degree >= 1 still lacking some live
+                            root's bit (live: its frontier is not empty)      */
     int64_t e_u;         /* their degree sum                                  */
     float ms;            /* layer time when cfg.timing = 1                    */
     float pad2;

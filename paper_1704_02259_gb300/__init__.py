@@ -59,7 +59,7 @@ class BatchConfig(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_double),
                 ("lane_probe", ctypes.c_int32), ("big_degree", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("timing", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 8)]
+                ("layer_slots", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
 class BatchLayerStats(ctypes.Structure):

@@ -1,22 +1,33 @@
 // msbfs.cu -- batched multi-source BFS: up to 512 roots share one traversal.
 //
 // Root i owns bit i of a per-vertex bitset of W 64-bit words (W = 1, 2, 4 or
-// 8): seen[v] (roots that reached v), cur[v] (roots whose frontier holds v)
-// and nxt[v] (roots reaching v in this layer). A layer is
-//   bottom-up (Alg. 2 on bit lanes): every vertex still lacking some roots
-//     ORs the frontier words of its neighbours, in CSR order, and stops as
-//     soon as every lacking root is found -- the paper's early exit, taken
+// 8): seen[v] (roots that reached v) and, per layer j, the frontier words
+// fr_j[v] (roots that reached v at distance exactly j). A layer is
+//   bottom-up (Alg. 2 on bit lanes): every vertex still lacking some live
+//     root ORs the frontier words of its neighbours, in CSR order, and stops
+//     as soon as every lacking root is found -- the paper's early exit, taken
 //     per lane set. A lane scans `lane_probe` neighbours alone; longer rows
 //     are finished by the warp with a 64-bit OR reduction over 32 neighbours
-//     per round. The vertex's own thread then updates seen, nxt and the int8
-//     level rows, so no separate pass is needed;
+//     per round;
 //   top-down (Alg. 1 on bit lanes): the vertices holding frontier bits are
 //     compacted into a list (heavy ones into a grid-spread list), their
-//     frontier words are ORed into each neighbour's nxt with 64-bit
+//     frontier words are ORed into each neighbour's next words with 64-bit
 //     atomicOr, and a dense pass keeps the bits not yet seen.
+// A root whose frontier is empty has finished; it leaves the live-lane mask
+// (the OR of the layer's new bits), so no vertex waits for it any longer and
+// the early exit stays effective when some roots sit in small components.
 // The direction is the edge form of the Alg. 3 switch over vertex counts:
 // e_f is the degree sum of vertices holding a frontier bit, e_u that of
-// vertices still lacking some root.
+// vertices still lacking some live root.
+//
+// Levels are not written per layer: the frontier words of every layer stay
+// in a ring of `lcap` slots, and one pass at the end turns them into the
+// int8 level rows, a warp storing 32 consecutive bytes of a row per
+// instruction (whole sectors, -1 where no layer holds the bit). Should a
+// traversal need more layers than slots, the full slots are turned into
+// levels the same way before the ring wraps, and later layers write only
+// their reached pairs.
+
 #include <stdio.h>
 #include <string.h>
 
@@ -25,12 +36,15 @@
 #include "graph.cuh"
 
 struct MsState {
-    int W = 0;
+    int W = 0;     // lane words the bitsets are sized for
+    int lcap = 0;  // frontier slots
     int64_t n = 0;
-    unsigned long long *seen = nullptr, *cur = nullptr, *nxt = nullptr;
+    unsigned long long *seen = nullptr;  // [n][W]
+    unsigned long long *fr = nullptr;    // [lcap][n][W]; layer j in slot j % lcap
+    unsigned long long *live = nullptr;  // [3][8] live-lane masks, ring by layer
     int32_t *list = nullptr, *big = nullptr, *roots = nullptr;
     int64_t *trace = nullptr;
-    int64_t *h_slot = nullptr;  // pinned
+    int64_t *h_slot = nullptr;  // pinned: one trace slot (8) and one live mask (8)
     bfs_batch_config cfg;
     std::vector<bfs_batch_layer_stats> last;
     int64_t last_pairs = 0;
@@ -52,8 +66,8 @@ void free_ms_state(bfs_graph *g) {
     if (!g || !g->ms) return;
     MsState *m = g->ms;
     cudaFree(m->seen);
-    cudaFree(m->cur);
-    cudaFree(m->nxt);
+    cudaFree(m->fr);
+    cudaFree(m->live);
     cudaFree(m->list);
     cudaFree(m->big);
     cudaFree(m->roots);
@@ -72,11 +86,18 @@ void free_ms_state(bfs_graph *g) {
 namespace {
 
 // Trace slot fields; the step kernels add fields 0-5 with one block_add.
-enum MsField { M_NV = 0, M_MF = 1, M_PAIRS = 2, M_FULLN = 3, M_FULLDEG = 4, M_EXAM = 5,
+//   M_NV, M_MF      vertices holding a bit of the new frontier, degree sum
+//   M_PAIRS         (root, vertex) pairs of the new frontier
+//   M_LACKN/DEG     vertices (degree >= 1) still lacking some live root after
+//                   the layer, degree sum (the next layer's v_u, e_u)
+//   M_EXAM          edges examined
+//   M_LIST, M_BIG   top-down compaction counts (of the slot's own layer)
+enum MsField { M_NV = 0, M_MF = 1, M_PAIRS = 2, M_LACKN = 3, M_LACKDEG = 4, M_EXAM = 5,
                M_LIST = 6, M_BIG = 7 };
 constexpr int kMsBlock = 256;
 constexpr int kMsBigBatch = 1024;
 constexpr int kMaxRoots = 512;
+constexpr int kMaxSlots = 16;
 
 template <int W>
 struct Lanes {
@@ -99,66 +120,83 @@ __device__ __forceinline__ void load_lanes(const unsigned long long *p,
     }
 }
 
+template <int W>
+__device__ __forceinline__ Lanes<W> load_live(const unsigned long long *p) {
+    Lanes<W> a;
+#pragma unroll
+    for (int i = 0; i < W; ++i) a.w[i] = __ldcg(p + i);
+    return a;
+}
+
 __device__ __forceinline__ unsigned long long warp_or64(unsigned long long x) {
     const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)x);
     const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(x >> 32));
     return ((unsigned long long)hi << 32) | lo;
 }
 
-// Sums NV counters over the block and adds them to dst[0..NV) with one
-// atomic each.
-template <int NV>
-__device__ __forceinline__ void block_add(int64_t (&v)[NV], unsigned long long *dst) {
-    __shared__ long long red[NV][kMsBlock / 32];
+// Sums the 6 step counters over the block and adds them to dst[0..6), and
+// ORs the block's new bits into the next live mask: one atomic per counter
+// and lane word.
+template <int W>
+__device__ __forceinline__ void block_finish(int64_t (&v)[6], const unsigned long long (&nb)[W],
+                                             unsigned long long *dst,
+                                             unsigned long long *live_next) {
+    __shared__ long long red[6][kMsBlock / 32];
+    __shared__ unsigned long long lv[W];
     const unsigned lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x < W) lv[threadIdx.x] = 0ull;
 #pragma unroll
-    for (int i = 0; i < NV; ++i) {
+    for (int i = 0; i < 6; ++i) {
         const int64_t s = warp_sum(v[i]);
         if (lane == 0) red[i][w] = s;
     }
     __syncthreads();
-    if (threadIdx.x < NV) {
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        const unsigned long long x = warp_or64(nb[i]);
+        if (lane == 0 && x) atomicOr(lv + i, x);
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
         long long s = 0;
         for (int j = 0; j < (int)(blockDim.x >> 5); ++j) s += red[threadIdx.x][j];
         if (s) atomicAdd(dst + threadIdx.x, (unsigned long long)s);
     }
+    if (threadIdx.x < W && lv[threadIdx.x]) atomicOr(live_next + threadIdx.x, lv[threadIdx.x]);
 }
 
-// levels = -1 (16-byte stores when aligned), seen = cur = 0.
-__global__ void ms_fill_kernel(int8_t *__restrict__ levels, int64_t total, int aligned,
-                               unsigned long long *__restrict__ seen,
-                               unsigned long long *__restrict__ cur, int64_t nwords) {
+// seen = 0 and the first frontier slot = 0.
+__global__ void ms_fill_kernel(unsigned long long *__restrict__ seen,
+                               unsigned long long *__restrict__ fr0, int64_t nwords) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (aligned) {
-        const int64_t nv = total / 16;
-        int4 *l4 = reinterpret_cast<int4 *>(levels);
-        for (int64_t i = t0; i < nv; i += stride) l4[i] = make_int4(-1, -1, -1, -1);
-        for (int64_t i = nv * 16 + t0; i < total; i += stride) levels[i] = -1;
-    } else {
-        for (int64_t i = t0; i < total; i += stride) levels[i] = -1;
-    }
-    for (int64_t i = t0; i < nwords; i += stride) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nwords; i += stride) {
         seen[i] = 0ull;
-        cur[i] = 0ull;
+        fr0[i] = 0ull;
     }
 }
 
-// Roots: lane l sets bit l of its root's seen and cur words and level 0.
-// Slot 0 of the trace gets the first frontier's counters (distinct root
-// vertices, their degrees, pairs = k, roots that are already complete).
+// Roots: lane l sets bit l of its root's seen and frontier words. Slot 0 of
+// the trace gets the first frontier's counters (distinct root vertices, their
+// degrees, pairs = k, and the vertices of degree >= 1 still lacking a root:
+// all of them but the root vertices that every root starts from). The live
+// mask ring starts as the k lanes.
 template <int W>
 __global__ void __launch_bounds__(kMaxRoots) ms_roots_kernel(
-    const int32_t *__restrict__ roots, int k, int64_t n, const int64_t *__restrict__ off,
-    Lanes<W> act, unsigned long long *__restrict__ seen, unsigned long long *__restrict__ cur,
-    int8_t *__restrict__ levels, int64_t *__restrict__ trace) {
+    const int32_t *__restrict__ roots, int k, int64_t n, int64_t nondeg0, int64_t nnz,
+    const int64_t *__restrict__ off, Lanes<W> act, unsigned long long *__restrict__ seen,
+    unsigned long long *__restrict__ fr0, unsigned long long *__restrict__ live,
+    int64_t *__restrict__ trace) {
     __shared__ long long red[5][kMaxRoots / 32];
     const int l = threadIdx.x;
     if (l < k) {
         const int64_t v = roots[l];
         atomicOr(seen + v * W + (l >> 6), 1ull << (l & 63));
-        atomicOr(cur + v * W + (l >> 6), 1ull << (l & 63));
-        levels[(int64_t)l * n + v] = 0;
+        atomicOr(fr0 + v * W + (l >> 6), 1ull << (l & 63));
+    }
+    if (l < 8) {
+        live[l] = l < W ? act.w[l] : 0ull;
+        live[8 + l] = 0ull;
+        live[16 + l] = 0ull;
     }
     __syncthreads();
     int64_t c[5] = {0, 0, 0, 0, 0};
@@ -173,7 +211,7 @@ __global__ void __launch_bounds__(kMaxRoots) ms_roots_kernel(
             bool full = true;
 #pragma unroll
             for (int i = 0; i < W; ++i) full = full && seen[(int64_t)v * W + i] == act.w[i];
-            if (full) {
+            if (full && d > 0) {
                 c[3] = 1;
                 c[4] = d;
             }
@@ -186,64 +224,75 @@ __global__ void __launch_bounds__(kMaxRoots) ms_roots_kernel(
         if (lane == 0) red[i][w] = s;
     }
     __syncthreads();
-    if (threadIdx.x < 5) {
+    if (threadIdx.x < 8) {
         long long s = 0;
-        for (int j = 0; j < (int)(blockDim.x >> 5); ++j) s += red[threadIdx.x][j];
-        trace[threadIdx.x] = threadIdx.x == M_PAIRS ? k : s;
+        if (threadIdx.x < 5)
+            for (int j = 0; j < (int)(blockDim.x >> 5); ++j) s += red[threadIdx.x][j];
+        long long out = s;
+        if (threadIdx.x == M_PAIRS) out = k;
+        if (threadIdx.x == M_LACKN) out = nondeg0 - s;
+        if (threadIdx.x == M_LACKDEG) out = nnz - s;
+        if (threadIdx.x >= 5) out = 0;
+        trace[threadIdx.x] = out;
     }
 }
 
-// Writes the newly reached bits `nw` of vertex v: seen, level rows, counters.
+// Records the newly reached bits `nw` of vertex v (degree deg >= 1): seen,
+// counters, the block's live OR; and counts v as lacking when some live
+// root has still not reached it.
 template <int W>
-__device__ __forceinline__ void ms_commit(int64_t v, int64_t n, int64_t deg,
+__device__ __forceinline__ void ms_commit(int64_t v, int64_t deg,
                                           const unsigned long long (&s)[W],
                                           const unsigned long long (&nw)[W], const Lanes<W> &act,
-                                          unsigned long long *__restrict__ seen,
-                                          int8_t *__restrict__ levels, int8_t new_level,
-                                          int64_t (&c)[6]) {
-    bool any = false, full = true;
+                                          unsigned long long *__restrict__ seen, int64_t (&c)[6],
+                                          unsigned long long (&nb)[W]) {
+    bool any = false, lacking = false;
 #pragma unroll
     for (int i = 0; i < W; ++i) {
         any = any || nw[i] != 0ull;
-        full = full && (s[i] | nw[i]) == act.w[i];
+        lacking = lacking || (act.w[i] & ~(s[i] | nw[i])) != 0ull;
     }
-    if (!any) return;
+    if (any) {
 #pragma unroll
-    for (int i = 0; i < W; ++i) {
-        if (!nw[i]) continue;
-        seen[v * W + i] = s[i] | nw[i];
-        unsigned long long x = nw[i];
-        c[2] += __popcll(x);
-        while (x) {
-            const int b = __ffsll((long long)x) - 1;
-            x &= x - 1;
-            levels[(int64_t)(i * 64 + b) * n + v] = new_level;
+        for (int i = 0; i < W; ++i) {
+            if (!nw[i]) continue;
+            seen[v * W + i] = s[i] | nw[i];
+            c[2] += __popcll(nw[i]);
+            nb[i] |= nw[i];
         }
+        c[0] += 1;
+        c[1] += deg;
     }
-    c[0] += 1;
-    c[1] += deg;
-    if (full) {
+    if (lacking) {
         c[3] += 1;
         c[4] += deg;
     }
 }
 
 // Bottom-up layer on bit lanes. Warp per 32 consecutive vertices, lane per
-// vertex. need = roots this vertex still lacks; acc = OR of the neighbours'
-// frontier words restricted to need, in CSR order, stopping once acc = need.
+// vertex. need = live roots this vertex still lacks; acc = OR of the
+// neighbours' frontier words restricted to need, in CSR order, stopping once
+// acc = need. acc is the vertex's next-frontier word set (written for every
+// vertex, so the next slot needs no clearing).
 template <int W, bool CO>
 __device__ __forceinline__ void ms_bu_phase(
     const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
     const uint32_t *__restrict__ base_vis, int64_t n, Lanes<W> act,
     unsigned long long *__restrict__ seen, const unsigned long long *__restrict__ cur,
-    unsigned long long *__restrict__ nxt, int8_t *__restrict__ levels, int8_t new_level,
-    int probe, unsigned long long *slot_next, int64_t *zero_slot) {
-    if (blockIdx.x == 0 && threadIdx.x < 8) zero_slot[threadIdx.x] = 0;
+    unsigned long long *__restrict__ nxt, int probe, unsigned long long *slot_next,
+    int64_t *zero_slot, unsigned long long *live_next, unsigned long long *live_zero) {
+    if (blockIdx.x == 0 && threadIdx.x < 8) {
+        zero_slot[threadIdx.x] = 0;
+        live_zero[threadIdx.x] = 0ull;
+    }
     const unsigned lane = lane_id();
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nwords = (n + 31) / 32;
     int64_t c[6] = {0, 0, 0, 0, 0, 0};
+    unsigned long long nb[W];
+#pragma unroll
+    for (int i = 0; i < W; ++i) nb[i] = 0ull;
     for (int64_t w = gw; w < nwords; w += tw) {
         const int64_t v = w * 32 + lane;
         const bool inb = v < n;
@@ -323,11 +372,11 @@ __device__ __forceinline__ void ms_bu_phase(
         if (inb) {
 #pragma unroll
             for (int i = 0; i < W; ++i) nxt[v * W + i] = acc[i];
-            ms_commit<W>(v, n, end - beg, s, acc, act, seen, levels, new_level, c);
+            if (!skip) ms_commit<W>(v, end - beg, s, acc, act, seen, c, nb);
         }
         c[5] += ex;
     }
-    block_add<6>(c, slot_next);
+    block_finish<W>(c, nb, slot_next, live_next);
 }
 
 // Vertices holding a frontier bit -> list (block scan, one atomic per
@@ -509,48 +558,127 @@ __device__ __forceinline__ void ms_td_big_phase(
 }
 
 // After a top-down layer: keep the bits of nxt not yet seen (they become the
-// next frontier), update seen and the level rows, count.
+// next frontier), update seen and count; every vertex of degree >= 1 is
+// checked for live roots it still lacks.
 template <int W, bool CO>
 __device__ __forceinline__ void ms_finalize_phase(
-    const int64_t *__restrict__ off, int64_t n, Lanes<W> act,
-    unsigned long long *__restrict__ seen, unsigned long long *__restrict__ nxt,
-    int8_t *__restrict__ levels, int8_t new_level, int64_t td_edges,
-    unsigned long long *slot_next, int64_t *zero_slot) {
-    if (blockIdx.x == 0 && threadIdx.x < 8) zero_slot[threadIdx.x] = 0;
+    const int64_t *__restrict__ off, const uint32_t *__restrict__ base_vis, int64_t n,
+    Lanes<W> act, unsigned long long *__restrict__ seen, unsigned long long *__restrict__ nxt,
+    int64_t td_edges, unsigned long long *slot_next, int64_t *zero_slot,
+    unsigned long long *live_next, unsigned long long *live_zero) {
+    if (blockIdx.x == 0 && threadIdx.x < 8) {
+        zero_slot[threadIdx.x] = 0;
+        live_zero[threadIdx.x] = 0ull;
+    }
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int64_t c[6] = {0, 0, 0, 0, 0, 0};
+    unsigned long long nb[W];
+#pragma unroll
+    for (int i = 0; i < W; ++i) nb[i] = 0ull;
     if (blockIdx.x == 0 && threadIdx.x == 0) c[5] = td_edges;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += stride) {
+        if ((base_vis[v >> 5] >> (v & 31)) & 1u) continue;  // degree 0
         unsigned long long x[W], s[W], nw[W];
-        bool any = false;
         load_lanes<W, CO>(nxt + v * W, x);
-        if constexpr (W == 1) {
-            any = x[0] != 0ull;
-        } else {
-#pragma unroll
-            for (int i = 0; i < W; ++i) any = any || x[i] != 0ull;
-        }
-        if (!any) continue;
         load_lanes<W, CO>(seen + v * W, s);
+        bool any = false;
 #pragma unroll
         for (int i = 0; i < W; ++i) {
             nw[i] = x[i] & ~s[i] & act.w[i];
-            nxt[v * W + i] = nw[i];
+            any = any || x[i] != 0ull;
         }
-        ms_commit<W>(v, n, off[v + 1] - off[v], s, nw, act, seen, levels, new_level, c);
+        if (any) {
+#pragma unroll
+            for (int i = 0; i < W; ++i) nxt[v * W + i] = nw[i];
+        }
+        ms_commit<W>(v, off[v + 1] - off[v], s, nw, act, seen, c, nb);
     }
-    block_add<6>(c, slot_next);
+    block_finish<W>(c, nb, slot_next, live_next);
+}
+
+// Per-byte x - 1 of eight bytes in [0, 128] (0 -> 0xFF), without borrows
+// between bytes.
+__device__ __forceinline__ unsigned long long bytes_dec(unsigned long long x) {
+    constexpr unsigned long long H = 0x8080808080808080ull, L = 0x0101010101010101ull;
+    return ((x | H) - L) ^ ((x ^ ~L) & H);
+}
+
+// Level rows from the frontier slots of layers [j_lo, j_hi). A warp owns 32
+// consecutive vertices (lane = vertex) and one lane word i at a time.
+//   full = 1: every row r < k of those 32 columns is written, -1 where none of
+//     the layers holds the bit. The lane gathers the 64 levels of its vertex
+//     for word i as eight 8-byte groups (byte b = level + 1 of root 64i + b,
+//     from a 256-entry bit -> byte spread table times j + 1), then stores one
+//     byte per row: the warp's 32 bytes of a row are one coalesced store.
+//   full = 0: only the reached pairs are written (layers after an earlier
+//     full pass).
+template <int W, bool CO>
+__device__ __forceinline__ void ms_levels_phase(const unsigned long long *__restrict__ fr,
+                                                int64_t slot_words, int lcap, int j_lo, int j_hi,
+                                                int64_t n, int k, int8_t *__restrict__ levels,
+                                                int full) {
+    __shared__ unsigned long long spread[256];
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) {
+        unsigned long long s = 0;
+        for (int b = 0; b < 8; ++b)
+            if ((t >> b) & 1) s |= 1ull << (8 * b);
+        spread[t] = s;
+    }
+    __syncthreads();
+    const unsigned lane = lane_id();
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t ntiles = (n + 31) / 32;
+    for (int64_t t = gw; t < ntiles; t += tw) {
+        const int64_t v = t * 32 + lane;
+        const bool inb = v < n;
+#pragma unroll 1
+        for (int i = 0; i < W; ++i) {
+            if (i * 64 >= k) break;
+            if (full) {
+                unsigned long long acc[8];
+#pragma unroll
+                for (int g = 0; g < 8; ++g) acc[g] = 0ull;
+                for (int j = j_lo; j < j_hi; ++j) {
+                    const unsigned long long m =
+                        inb ? ld<CO>(fr + (int64_t)(j % lcap) * slot_words + v * W + i) : 0ull;
+                    if (!m) continue;
+                    const unsigned long long mul = (unsigned long long)(j + 1);
+#pragma unroll
+                    for (int g = 0; g < 8; ++g) acc[g] |= spread[(m >> (8 * g)) & 0xFF] * mul;
+                }
+#pragma unroll
+                for (int g = 0; g < 8; ++g) acc[g] = bytes_dec(acc[g]);
+                const int rows = k - i * 64 < 64 ? k - i * 64 : 64;
+                int8_t *col = levels + (int64_t)(i * 64) * n + v;
+#pragma unroll
+                for (int b = 0; b < 64; ++b) {
+                    if (b >= rows) break;
+                    if (inb) col[(int64_t)b * n] = (int8_t)(acc[b >> 3] >> (8 * (b & 7)));
+                }
+            } else if (inb) {
+                for (int j = j_lo; j < j_hi; ++j) {
+                    unsigned long long m = ld<CO>(fr + (int64_t)(j % lcap) * slot_words + v * W + i);
+                    while (m) {
+                        const int b = __ffsll((long long)m) - 1;
+                        m &= m - 1;
+                        if (i * 64 + b < k) levels[(int64_t)(i * 64 + b) * n + v] = (int8_t)j;
+                    }
+                }
+            }
+        }
+    }
 }
 
 // Kernels for the host-driven loop: one phase each.
 template <int W>
 __global__ void __launch_bounds__(kMsBlock) ms_bu_kernel(
     const int64_t *off, const int32_t *idx, const uint32_t *base_vis, int64_t n, Lanes<W> act,
-    unsigned long long *seen, const unsigned long long *cur, unsigned long long *nxt,
-    int8_t *levels, int8_t new_level, int probe, unsigned long long *slot_next,
-    int64_t *zero_slot) {
-    ms_bu_phase<W, false>(off, idx, base_vis, n, act, seen, cur, nxt, levels, new_level, probe,
-                          slot_next, zero_slot);
+    unsigned long long *seen, const unsigned long long *cur, unsigned long long *nxt, int probe,
+    unsigned long long *slot_next, int64_t *zero_slot, unsigned long long *live_next,
+    unsigned long long *live_zero) {
+    ms_bu_phase<W, false>(off, idx, base_vis, n, act, seen, cur, nxt, probe, slot_next, zero_slot,
+                          live_next, live_zero);
 }
 
 template <int W>
@@ -576,11 +704,19 @@ __global__ void __launch_bounds__(kMsBlock) ms_td_big_kernel(
 
 template <int W>
 __global__ void __launch_bounds__(kMsBlock) ms_finalize_kernel(
-    const int64_t *off, int64_t n, Lanes<W> act, unsigned long long *seen,
-    unsigned long long *nxt, int8_t *levels, int8_t new_level, int64_t td_edges,
-    unsigned long long *slot_next, int64_t *zero_slot) {
-    ms_finalize_phase<W, false>(off, n, act, seen, nxt, levels, new_level, td_edges, slot_next,
-                                zero_slot);
+    const int64_t *off, const uint32_t *base_vis, int64_t n, Lanes<W> act,
+    unsigned long long *seen, unsigned long long *nxt, int64_t td_edges,
+    unsigned long long *slot_next, int64_t *zero_slot, unsigned long long *live_next,
+    unsigned long long *live_zero) {
+    ms_finalize_phase<W, false>(off, base_vis, n, act, seen, nxt, td_edges, slot_next, zero_slot,
+                                live_next, live_zero);
+}
+
+template <int W>
+__global__ void __launch_bounds__(kMsBlock) ms_levels_kernel(
+    const unsigned long long *fr, int64_t slot_words, int lcap, int j_lo, int j_hi, int64_t n,
+    int k, int8_t *levels, int full) {
+    ms_levels_phase<W, false>(fr, slot_words, lcap, j_lo, j_hi, n, k, levels, full);
 }
 
 struct MsPersist {
@@ -588,10 +724,12 @@ struct MsPersist {
     const int32_t *idx;
     const uint32_t *base_vis;
     int64_t n, nnz;
-    unsigned long long *seen, *buf0, *buf1;
+    unsigned long long *seen, *fr, *live;
+    int64_t slot_words;
+    int lcap, k;
     int8_t *levels;
     int32_t *list, *big;
-    int64_t *trace;   // ring of kMsRing slots; slot 0 written by ms_roots_kernel
+    int64_t *trace;   // ring of kMsRingP slots; slot 0 written by ms_roots_kernel
     int64_t *layers;  // [128][8] per-layer record
     int32_t *result;  // [0] layers, [1] status
     unsigned *bar;    // barrier count, generation
@@ -607,15 +745,16 @@ constexpr int kMsFieldsP = 8;
 
 // The whole batched traversal in one cooperative launch: every block runs
 // the same layer loop and takes the same direction decision from the layer
-// counters, which grid barriers make visible between phases. Bottom-up
-// layers are one phase; top-down layers are compaction (+ clearing nxt),
-// push, and the dense keep-unseen pass.
+// counters and live mask, which grid barriers make visible between phases.
+// Bottom-up layers are one phase; top-down layers are compaction (+ clearing
+// the next slot), push, and the dense keep-unseen pass. The level rows are
+// written by a last phase (and by a flush phase when the slot ring is full).
 template <int W>
-__global__ void __launch_bounds__(kMsBlock) ms_persistent_kernel(MsPersist p, Lanes<W> act) {
+__global__ void __launch_bounds__(kMsBlock) ms_persistent_kernel(MsPersist p) {
     const unsigned expected = gridDim.x;
-    int64_t v_u = p.n - __ldcg(p.trace + M_FULLN);
-    int64_t e_u = p.nnz - __ldcg(p.trace + M_FULLDEG);
-    int cur_bu = 0, status = BFS_OK, d = 0;
+    int64_t e_u = __ldcg(p.trace + M_LACKDEG);
+    int64_t v_u = __ldcg(p.trace + M_LACKN);
+    int cur_bu = 0, status = BFS_OK, d = 0, j_lo = 0, flushed = 0;
     for (;; ++d) {
         int64_t *sc = p.trace + (d % kMsRingP) * kMsFieldsP;
         int64_t *sn = p.trace + ((d + 1) % kMsRingP) * kMsFieldsP;
@@ -625,6 +764,16 @@ __global__ void __launch_bounds__(kMsBlock) ms_persistent_kernel(MsPersist p, La
         if (d + 1 > 127) {
             status = BFS_ERR_DEPTH;
             break;
+        }
+        if (d + 1 - j_lo >= p.lcap) {  // the next slot still holds an unwritten layer
+            ms_levels_phase<W, true>(p.fr, p.slot_words, p.lcap, j_lo, d + 1, p.n, p.k, p.levels,
+                                     !flushed);
+            flushed = 1;
+            j_lo = d + 1;
+            if (!grid_barrier(p.bar, p.err, expected, p.timeout_ns)) {
+                status = BFS_ERR_TIMEOUT;
+                break;
+            }
         }
         if (!cur_bu) cur_bu = ((double)e_f > (double)e_u / p.alpha) ? 1 : 0;
         else cur_bu = ((double)v_f < (double)p.n / p.beta) ? 0 : 1;
@@ -637,17 +786,20 @@ __global__ void __launch_bounds__(kMsBlock) ms_persistent_kernel(MsPersist p, La
             rec[4] = v_u;
             rec[5] = e_u;
         }
-        unsigned long long *cur = (d & 1) ? p.buf1 : p.buf0;
-        unsigned long long *nxt = (d & 1) ? p.buf0 : p.buf1;
-        const int8_t nl = (int8_t)(d + 1);
+        const Lanes<W> act = load_live<W>(p.live + (d % 3) * 8);
+        unsigned long long *live_next = p.live + ((d + 1) % 3) * 8;
+        unsigned long long *live_zero = p.live + ((d + 2) % 3) * 8;
+        unsigned long long *cur = p.fr + (int64_t)(d % p.lcap) * p.slot_words;
+        unsigned long long *nxt = p.fr + (int64_t)((d + 1) % p.lcap) * p.slot_words;
         if (cur_bu) {
-            ms_bu_phase<W, true>(p.off, p.idx, p.base_vis, p.n, act, p.seen, cur, nxt, p.levels, nl,
-                                 p.probe, (unsigned long long *)sn, sz);
+            ms_bu_phase<W, true>(p.off, p.idx, p.base_vis, p.n, act, p.seen, cur, nxt, p.probe,
+                                 (unsigned long long *)sn, sz, live_next, live_zero);
         } else {
             ms_compact_phase<W, true>(cur, p.n, p.off, p.big_deg, p.list, p.big,
                                       (unsigned long long *)sc);
             const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-            for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n * W; i += stride)
+            for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.slot_words;
+                 i += stride)
                 nxt[i] = 0ull;
             if (!grid_barrier(p.bar, p.err, expected, p.timeout_ns)) {
                 status = BFS_ERR_TIMEOUT;
@@ -661,16 +813,19 @@ __global__ void __launch_bounds__(kMsBlock) ms_persistent_kernel(MsPersist p, La
                 status = BFS_ERR_TIMEOUT;
                 break;
             }
-            ms_finalize_phase<W, true>(p.off, p.n, act, p.seen, nxt, p.levels, nl, e_f,
-                                       (unsigned long long *)sn, sz);
+            ms_finalize_phase<W, true>(p.off, p.base_vis, p.n, act, p.seen, nxt, e_f,
+                                       (unsigned long long *)sn, sz, live_next, live_zero);
         }
         if (!grid_barrier(p.bar, p.err, expected, p.timeout_ns)) {
             status = BFS_ERR_TIMEOUT;
             break;
         }
-        v_u -= __ldcg(sn + M_FULLN);
-        e_u -= __ldcg(sn + M_FULLDEG);
+        v_u = __ldcg(sn + M_LACKN);
+        e_u = __ldcg(sn + M_LACKDEG);
     }
+    if (status != BFS_ERR_TIMEOUT)  // levels of the layers still in the ring
+        ms_levels_phase<W, true>(p.fr, p.slot_words, p.lcap, j_lo, d + 1, p.n, p.k, p.levels,
+                                 !flushed);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         p.result[0] = d;
         p.result[1] = status;
@@ -696,9 +851,13 @@ constexpr int kMsFields = 8;
 
 bool batch_cfg_ok(const bfs_batch_config &c) {
     return c.alpha > 0 && c.beta > 0 && c.lane_probe >= 0 && c.lane_probe <= 4096 &&
-           c.big_degree >= 32 && (c.use_graph == 0 || c.use_graph == 1);
+           c.big_degree >= 32 && (c.use_graph == 0 || c.use_graph == 1) &&
+           (c.layer_slots == 0 || (c.layer_slots >= 2 && c.layer_slots <= kMaxSlots));
 }
 
+// Bitsets for W lane words: seen and the frontier slot ring. The ring gets
+// cfg.layer_slots slots, or (0) as many as a quarter of the free device
+// memory holds, 4 to 16.
 bfs_status ensure_ms(bfs_graph *g, int W) {
     if (!g->ms) {
         g->ms = new MsState();
@@ -711,21 +870,36 @@ bfs_status ensure_ms(bfs_graph *g, int W) {
         GB_CK(cudaMalloc(&m->big, (size_t)g->n * 4));
         GB_CK(cudaMalloc(&m->roots, kMaxRoots * 4));
         GB_CK(cudaMalloc(&m->trace, (size_t)kMsRing * kMsFields * 8));
-        GB_CK(cudaMallocHost(&m->h_slot, kMsFields * 8));
+        GB_CK(cudaMalloc(&m->live, 3 * 8 * 8));
+        GB_CK(cudaMallocHost(&m->h_slot, 16 * 8));
     }
-    if (m->W < W) {
+    if (W == 0) return BFS_OK;
+    const int want = m->cfg.layer_slots;
+    if (m->W < W || (want > 0 && want != m->lcap)) {
         cudaFree(m->seen);
-        cudaFree(m->cur);
-        cudaFree(m->nxt);
-        m->seen = m->cur = m->nxt = nullptr;
+        cudaFree(m->fr);
+        m->seen = m->fr = nullptr;
         m->W = 0;
-        const size_t bytes = (size_t)g->n * W * 8;
-        GB_CK(cudaMalloc(&m->seen, bytes));
-        GB_CK(cudaMalloc(&m->cur, bytes));
-        GB_CK(cudaMalloc(&m->nxt, bytes));
+        m->lcap = 0;
+        const size_t slot = (size_t)g->n * W * 8;
+        int lcap = want;
+        if (lcap == 0) {
+            size_t fb = 0, tb = 0;
+            GB_CK(cudaMemGetInfo(&fb, &tb));
+            lcap = (int)std::max<size_t>(4, std::min<size_t>(kMaxSlots, fb / 4 / slot));
+        }
+        GB_CK(cudaMalloc(&m->seen, slot));
+        GB_CK(cudaMalloc(&m->fr, slot * lcap));
         m->W = W;
+        m->lcap = lcap;
     }
     return BFS_OK;
+}
+
+// Slots of the ring when it runs W lane words (a ring sized for wider words
+// holds more narrower slots).
+int ring_slots(const MsState *m, int W) {
+    return std::min(kMaxSlots, m->lcap * (m->W / W));
 }
 
 template <int W>
@@ -743,8 +917,10 @@ bfs_status run_batch_w(bfs_graph *g, const int32_t *roots, int k, int8_t *levels
     MsState *m = g->ms;
     const bfs_batch_config &cfg = m->cfg;
     const int64_t n = g->n;
-    const Lanes<W> act = active_lanes<W>(k);
-    unsigned long long *cur = m->cur, *nxt = m->nxt, *seen = m->seen;
+    Lanes<W> act = active_lanes<W>(k);
+    unsigned long long *seen = m->seen;
+    const int64_t slot_words = n * W;
+    const int lcap = ring_slots(m, W);
     const bool timing = cfg.timing != 0;
     auto event = [&](size_t i) -> cudaEvent_t {
         while (m->events.size() <= i) {
@@ -754,29 +930,41 @@ bfs_status run_batch_w(bfs_graph *g, const int32_t *roots, int k, int8_t *levels
         }
         return m->events[i];
     };
-    int bu_occ = 1, td_occ = 1;
+    int bu_occ = 1, td_occ = 1, lv_occ = 1;
     GB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu_occ, ms_bu_kernel<W>, kMsBlock, 0));
     GB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&td_occ, ms_td_kernel<W>, kMsBlock, 0));
-    const int64_t total = (int64_t)k * n;
-    const int aligned = ((uintptr_t)levels % 16) == 0;
-    GB_LAUNCH(ms_fill_kernel, grid_cap(std::max<int64_t>(total / 16, n * W), kMsBlock, 8),
-              kMsBlock, 0, st, levels, total, aligned, seen, cur, n * W);
+    GB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lv_occ, ms_levels_kernel<W>, kMsBlock, 0));
+    const int64_t ntiles = (n + 31) / 32;
+    auto write_levels = [&](int j_lo, int j_hi, int full) -> bfs_status {
+        GB_LAUNCH(ms_levels_kernel<W>, grid_cap(ntiles, kMsBlock / 32, lv_occ), kMsBlock, 0, st,
+                  m->fr, slot_words, lcap, j_lo, j_hi, n, k, levels, full);
+        return BFS_OK;
+    };
+    GB_LAUNCH(ms_fill_kernel, grid_cap(n * W, kMsBlock, 8), kMsBlock, 0, st, seen, m->fr, n * W);
     GB_CK(cudaMemsetAsync(m->trace, 0, (size_t)kMsRing * kMsFields * 8, st));
-    GB_LAUNCH(ms_roots_kernel<W>, 1, kMaxRoots, 0, st, roots, k, n, g->off, act, seen, cur,
-              levels, m->trace);
+    GB_LAUNCH(ms_roots_kernel<W>, 1, kMaxRoots, 0, st, roots, k, n, n - g->deg0, g->nnz, g->off,
+              act, seen, m->fr, m->live, m->trace);
     GB_CK(cudaMemcpyAsync(m->h_slot, m->trace, kMsFields * 8, cudaMemcpyDeviceToHost, st));
     GB_CK(cudaStreamSynchronize(st));
     int64_t v_f = m->h_slot[M_NV], e_f = m->h_slot[M_MF], pairs = k;
-    int64_t v_u = n - m->h_slot[M_FULLN], e_u = g->nnz - m->h_slot[M_FULLDEG];
+    int64_t v_u = m->h_slot[M_LACKN], e_u = m->h_slot[M_LACKDEG];
     m->last.clear();
     m->last_pairs = k;
-    int cur_bu = 0;
+    int cur_bu = 0, j_lo = 0, flushed = 0, d = 0;
     const int64_t nwords = (n + 31) / 32;
     const int bu_grid = grid_cap(nwords, kMsBlock / 32, bu_occ);
-    for (int d = 0; v_f > 0; ++d) {
+    for (d = 0; v_f > 0; ++d) {
         if (d + 1 > 127) {
+            bfs_status s = write_levels(j_lo, d + 1, !flushed);
+            if (s == BFS_OK) GB_CK(cudaStreamSynchronize(st));
             set_error("bfs_run_batch: a level above 127 does not fit in int8");
-            return BFS_ERR_DEPTH;
+            return s == BFS_OK ? BFS_ERR_DEPTH : s;
+        }
+        if (d + 1 - j_lo >= lcap) {  // the next slot still holds an unwritten layer
+            bfs_status s = write_levels(j_lo, d + 1, !flushed);
+            if (s != BFS_OK) return s;
+            flushed = 1;
+            j_lo = d + 1;
         }
         if (!cur_bu) cur_bu = ((double)e_f > (double)e_u / cfg.alpha) ? 1 : 0;
         else cur_bu = ((double)v_f < (double)n / cfg.beta) ? 0 : 1;
@@ -791,17 +979,20 @@ bfs_status run_batch_w(bfs_graph *g, const int32_t *roots, int k, int8_t *levels
         int64_t *slot_cur = m->trace + (d % kMsRing) * kMsFields;
         int64_t *slot_next = m->trace + ((d + 1) % kMsRing) * kMsFields;
         int64_t *slot_zero = m->trace + ((d + 2) % kMsRing) * kMsFields;
+        unsigned long long *live_next = m->live + ((d + 1) % 3) * 8;
+        unsigned long long *live_zero = m->live + ((d + 2) % 3) * 8;
+        unsigned long long *cur = m->fr + (int64_t)(d % lcap) * slot_words;
+        unsigned long long *nxt = m->fr + (int64_t)((d + 1) % lcap) * slot_words;
         if (timing) GB_CK(cudaEventRecord(event(2 * d), st));
-        const int8_t nl = (int8_t)(d + 1);
         if (cur_bu) {
             GB_LAUNCH(ms_bu_kernel<W>, bu_grid, kMsBlock, 0, st, g->off, g->idx, g->base_vis, n,
-                      act, seen, cur, nxt, levels, nl, cfg.lane_probe,
-                      (unsigned long long *)slot_next, slot_zero);
+                      act, seen, cur, nxt, cfg.lane_probe, (unsigned long long *)slot_next,
+                      slot_zero, live_next, live_zero);
         } else {
             GB_LAUNCH(ms_compact_kernel<W>, grid_cap(n, kMsBlock * 4, 8), kMsBlock, 0, st, cur, n,
                       g->off, (int64_t)cfg.big_degree, m->list, m->big,
                       (unsigned long long *)slot_cur);
-            GB_CK(cudaMemsetAsync(nxt, 0, (size_t)n * W * 8, st));
+            GB_CK(cudaMemsetAsync(nxt, 0, (size_t)slot_words * 8, st));
             GB_LAUNCH(ms_td_kernel<W>, grid_cap(v_f, kMsBlock, td_occ), kMsBlock, 0, st, g->off,
                       g->idx, m->list, (const unsigned long long *)slot_cur, cur, seen, nxt);
             if (e_f >= cfg.big_degree)
@@ -810,33 +1001,37 @@ bfs_status run_batch_w(bfs_graph *g, const int32_t *roots, int k, int8_t *levels
                                                                       (int64_t)sm_count() * 4)),
                           kMsBlock, 0, st, g->off, g->idx, m->big,
                           (const unsigned long long *)slot_cur, cur, seen, nxt);
-            GB_LAUNCH(ms_finalize_kernel<W>, grid_cap(n, kMsBlock, 8), kMsBlock, 0, st, g->off, n,
-                      act, seen, nxt, levels, nl, e_f, (unsigned long long *)slot_next,
-                      slot_zero);
+            GB_LAUNCH(ms_finalize_kernel<W>, grid_cap(n, kMsBlock, 8), kMsBlock, 0, st, g->off,
+                      g->base_vis, n, act, seen, nxt, e_f, (unsigned long long *)slot_next,
+                      slot_zero, live_next, live_zero);
         }
         if (timing) GB_CK(cudaEventRecord(event(2 * d + 1), st));
         GB_CK(cudaMemcpyAsync(m->h_slot, slot_next, kMsFields * 8, cudaMemcpyDeviceToHost, st));
+        GB_CK(cudaMemcpyAsync(m->h_slot + 8, live_next, 8 * 8, cudaMemcpyDeviceToHost, st));
         GB_CK(cudaStreamSynchronize(st));
         m->last.push_back(ls);
         v_f = m->h_slot[M_NV];
         e_f = m->h_slot[M_MF];
         pairs = m->h_slot[M_PAIRS];
         m->last_pairs += pairs;
-        v_u -= m->h_slot[M_FULLN];
-        e_u -= m->h_slot[M_FULLDEG];
-        std::swap(cur, nxt);
+        v_u = m->h_slot[M_LACKN];
+        e_u = m->h_slot[M_LACKDEG];
+        for (int i = 0; i < W; ++i) act.w[i] = (unsigned long long)m->h_slot[8 + i];
     }
+    bfs_status s = write_levels(j_lo, d + 1, !flushed);
+    if (s != BFS_OK) return s;
+    GB_CK(cudaStreamSynchronize(st));
     if (timing)
-        for (size_t d = 0; d < m->last.size(); ++d)
-            cudaEventElapsedTime(&m->last[d].ms, m->events[2 * d], m->events[2 * d + 1]);
+        for (size_t i = 0; i < m->last.size(); ++i)
+            cudaEventElapsedTime(&m->last[i].ms, m->events[2 * i], m->events[2 * i + 1]);
     return BFS_OK;
 }
 
 constexpr int kPctlLayers = 128;
 constexpr size_t kPctlBytes = kPctlLayers * 8 * 8 + 64;  // records, result, barrier, err
 
-// The same traversal as run_batch_w, as one CUDA graph: fill, roots and the
-// persistent kernel (a cooperative node). The graph is captured once per
+// The same traversal as run_batch_w, as one CUDA graph: clearing, roots and
+// the persistent kernel (a cooperative node). The graph is captured once per
 // (W, k, output buffer, bitset buffers, configuration) and replayed.
 template <int W>
 bfs_status run_batch_graph(bfs_graph *g, const int32_t *roots, int k, int8_t *levels,
@@ -869,8 +1064,11 @@ bfs_status run_batch_graph(bfs_graph *g, const int32_t *roots, int k, int8_t *le
         p.n = n;
         p.nnz = g->nnz;
         p.seen = m->seen;
-        p.buf0 = m->cur;
-        p.buf1 = m->nxt;
+        p.fr = m->fr;
+        p.live = m->live;
+        p.slot_words = n * W;
+        p.lcap = ring_slots(m, W);
+        p.k = k;
         p.levels = levels;
         p.list = m->list;
         p.big = m->big;
@@ -884,18 +1082,15 @@ bfs_status run_batch_graph(bfs_graph *g, const int32_t *roots, int k, int8_t *le
         p.probe = m->cfg.lane_probe;
         p.big_deg = m->cfg.big_degree;
         p.timeout_ns = 2000000000ull;  // 2 s per barrier wait
-        const int64_t total = (int64_t)k * n;
-        const int aligned = ((uintptr_t)levels % 16) == 0;
         // Captured on a private stream (capture cannot start on the legacy
         // default stream); the instantiated graph is launched on `st`.
         if (!m->cap) GB_CK(cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking));
         cudaStream_t cs = m->cap;
         GB_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-        ms_fill_kernel<<<grid_cap(std::max<int64_t>(total / 16, n * W), kMsBlock, 8), kMsBlock, 0,
-                         cs>>>(levels, total, aligned, m->seen, m->cur, n * W);
+        ms_fill_kernel<<<grid_cap(n * W, kMsBlock, 8), kMsBlock, 0, cs>>>(m->seen, m->fr, n * W);
         cudaMemsetAsync(m->trace, 0, (size_t)kMsRing * kMsFields * 8, cs);
-        ms_roots_kernel<W><<<1, kMaxRoots, 0, cs>>>(roots, k, n, g->off, act, m->seen, m->cur,
-                                                    levels, m->trace);
+        ms_roots_kernel<W><<<1, kMaxRoots, 0, cs>>>(roots, k, n, n - g->deg0, g->nnz, g->off, act,
+                                                    m->seen, m->fr, m->live, m->trace);
         cudaMemsetAsync(p.result, 0, 64, cs);
         cudaLaunchConfig_t lc;
         memset(&lc, 0, sizeof lc);
@@ -907,7 +1102,7 @@ bfs_status run_batch_graph(bfs_graph *g, const int32_t *roots, int k, int8_t *le
         at.val.cooperative = 1;
         lc.attrs = &at;
         lc.numAttrs = 1;
-        cudaError_t le = cudaLaunchKernelEx(&lc, ms_persistent_kernel<W>, p, act);
+        cudaError_t le = cudaLaunchKernelEx(&lc, ms_persistent_kernel<W>, p);
         cudaGraph_t graph = nullptr;
         cudaError_t ce = cudaStreamEndCapture(cs, &graph);
         if (le != cudaSuccess || ce != cudaSuccess) {
@@ -967,7 +1162,6 @@ bool is_device_ptr(const void *p) {
 
 }  // namespace
 }  // namespace gbfs
-
 using namespace gbfs;
 
 extern "C" BFS_API void bfs_batch_config_default(bfs_batch_config *c) {

@@ -55,10 +55,12 @@ __global__ void unpack_row_kernel(const int8_t *__restrict__ row, int64_t n,
 }
 
 // Device bytes a worker's view of an n-vertex graph holds: the single-source
-// scratch (bitmaps, queues) plus the batched lists and, for W lane words,
-// three n*W-word bitsets.
+// scratch (bitmaps, queues) plus the batched lists; view_lane_bytes adds the
+// bitsets for W lane words.
 int64_t view_base_bytes(int64_t n) { return 21 * n + (1 << 16); }
-int64_t view_lane_bytes(int64_t n, int W) { return 24 * n * (int64_t)W; }
+// seen and kViewSlots frontier slots of n * W 64-bit words
+constexpr int kViewSlots = 8;
+int64_t view_lane_bytes(int64_t n, int W) { return 8 * (1 + kViewSlots) * n * (int64_t)W; }
 int lane_words(int k) { return k <= 64 ? 1 : k <= 128 ? 2 : k <= 256 ? 4 : 8; }
 
 bool host_ptr(const void *p) {
@@ -194,6 +196,7 @@ void worker_main(bfs_server *s, int wid) {
                 bfs_batch_config bc;
                 bfs_graph_get_batch_config(g_src, &bc);
                 bc.timing = 0;
+                bc.layer_slots = kViewSlots;
                 bfs_graph_set_batch_config(v, &bc);
                 views[gi] = v;
             }

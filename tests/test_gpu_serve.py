@@ -107,7 +107,9 @@ def test_poisson_stream_reports_latency(graphs):
 def test_memory_admission_splits_and_defers(graphs):
     n = graphs[1][0]
     # room for a few rows but not for a 256-root batch with its lane state
-    budget = 21 * n + (1 << 16) + 24 * n + 4 * n + 8 * n
+    # (a worker's view: 21n + 64 KiB of scratch; one lane word: seen and 8
+    # frontier slots, 72n bytes; then 12 int8 level rows)
+    budget = 21 * n + (1 << 16) + 72 * n + 4 * n + 8 * n
     srv, ids = server_with(graphs[1:2], workers=1, max_batch=256, memory_budget=budget)
     reqs = []
     for r in range(0, 200):
