@@ -603,67 +603,117 @@ __device__ __forceinline__ unsigned long long bytes_dec(unsigned long long x) {
     return ((x | H) - L) ^ ((x ^ ~L) & H);
 }
 
-// Level rows from the frontier slots of layers [j_lo, j_hi). A warp owns 32
-// consecutive vertices (lane = vertex) and one lane word i at a time.
-//   full = 1: every row r < k of those 32 columns is written, -1 where none of
-//     the layers holds the bit. The lane gathers the 64 levels of its vertex
-//     for word i as eight 8-byte groups (byte b = level + 1 of root 64i + b,
-//     from a 256-entry bit -> byte spread table times j + 1), then stores one
-//     byte per row: the warp's 32 bytes of a row are one coalesced store.
+// Level rows from the frontier slots of layers [j_lo, j_hi), one tile of
+// C = kMsBlock / W consecutive vertices (columns) per block and step: thread
+// t owns lane word i = t % W of vertex v0 + t / W, so each layer's frontier
+// words of the tile are one contiguous load by the block.
+//   full = 1: every row r < k of the tile's columns is written, -1 where none
+//     of the layers holds the bit. A thread builds the 64 levels of its
+//     (vertex, word) as bit planes: plane p ORs the frontier words of the
+//     layers j whose j + 1 has bit p set, so bit b of plane p is bit p of
+//     level + 1 of root 64i + b. Per group of 8 roots, the 8 plane bytes are
+//     gathered by byte permutes into an 8 x 8 bit matrix whose transpose
+//     holds the 8 level + 1 bytes (then minus 1: 0 -> -1). The bytes go to a
+//     shared tile of 64W rows x C bytes, the rows of word i rotated by
+//     i * C / 8 bytes so that a warp's byte stores hit distinct banks; then
+//     each warp stores whole rows, 4 or 8 bytes per lane, 128 or 256 bytes
+//     per store instruction (whole sectors).
 //   full = 0: only the reached pairs are written (layers after an earlier
 //     full pass).
+// vec: n and the level buffer allow 8-byte aligned row stores.
 template <int W, bool CO>
 __device__ __forceinline__ void ms_levels_phase(const unsigned long long *__restrict__ fr,
                                                 int64_t slot_words, int lcap, int j_lo, int j_hi,
                                                 int64_t n, int k, int8_t *__restrict__ levels,
-                                                int full) {
-    __shared__ unsigned long long spread[256];
-    for (int t = threadIdx.x; t < 256; t += blockDim.x) {
-        unsigned long long s = 0;
-        for (int b = 0; b < 8; ++b)
-            if ((t >> b) & 1) s |= 1ull << (8 * b);
-        spread[t] = s;
-    }
-    __syncthreads();
-    const unsigned lane = lane_id();
-    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t ntiles = (n + 31) / 32;
-    for (int64_t t = gw; t < ntiles; t += tw) {
-        const int64_t v = t * 32 + lane;
-        const bool inb = v < n;
-#pragma unroll 1
-        for (int i = 0; i < W; ++i) {
-            if (i * 64 >= k) break;
-            if (full) {
-                unsigned long long acc[8];
+                                                int full, int vec) {
+    constexpr int C = kMsBlock / W;  // columns of a tile
+    constexpr int R = 64 * W;        // rows of a tile (roots)
+    constexpr int CP = C + 8;        // padded row stride in bytes
+    constexpr int SW = C / 8;        // rotation of word i's rows: i * SW bytes
+    __shared__ __align__(16) uint8_t tile[R * CP];
+    const int i = (int)(threadIdx.x % W), vl = (int)(threadIdx.x / W);
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    const int rows = k < R ? k : R;
+    const int64_t ntiles = (n + C - 1) / C;
+    for (int64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
+        const int64_t v0 = tl * C, v = v0 + vl;
+        const bool inb = v < n && i * 64 < k;
+        if (full) {
+            unsigned long long P[8];
 #pragma unroll
-                for (int g = 0; g < 8; ++g) acc[g] = 0ull;
-                for (int j = j_lo; j < j_hi; ++j) {
-                    const unsigned long long m =
-                        inb ? ld<CO>(fr + (int64_t)(j % lcap) * slot_words + v * W + i) : 0ull;
-                    if (!m) continue;
-                    const unsigned long long mul = (unsigned long long)(j + 1);
+            for (int q = 0; q < 8; ++q) P[q] = 0ull;
+            int sj = j_lo % lcap;
+            for (int j = j_lo; j < j_hi; ++j) {
+                const unsigned long long m =
+                    inb ? ld<CO>(fr + (int64_t)sj * slot_words + v * W + i) : 0ull;
+                const unsigned jj = (unsigned)(j + 1);  // the same in every thread
 #pragma unroll
-                    for (int g = 0; g < 8; ++g) acc[g] |= spread[(m >> (8 * g)) & 0xFF] * mul;
+                for (int q = 0; q < 8; ++q)
+                    if ((jj >> q) & 1u) P[q] |= m;
+                sj = sj + 1 == lcap ? 0 : sj + 1;
+            }
+            uint8_t *col = tile + (i * 64) * CP + ((vl + i * SW) % C);
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+                // byte q of x = byte g of plane q (row q of an 8 x 8 bit matrix)
+                const unsigned sel = (unsigned)(g & 3) | ((4u + (unsigned)(g & 3)) << 4);
+                unsigned w[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) w[q] = (unsigned)(P[q] >> (32 * (g >> 2)));
+                const unsigned lo = __byte_perm(__byte_perm(w[0], w[1], sel),
+                                                __byte_perm(w[2], w[3], sel), 0x5410);
+                const unsigned hi = __byte_perm(__byte_perm(w[4], w[5], sel),
+                                                __byte_perm(w[6], w[7], sel), 0x5410);
+                unsigned long long x = ((unsigned long long)hi << 32) | lo;
+                // transpose: bit t of byte q -> bit q of byte t
+                unsigned long long t = (x ^ (x >> 7)) & 0x00AA00AA00AA00AAull;
+                x = x ^ t ^ (t << 7);
+                t = (x ^ (x >> 14)) & 0x0000CCCC0000CCCCull;
+                x = x ^ t ^ (t << 14);
+                t = (x ^ (x >> 28)) & 0x00000000F0F0F0F0ull;
+                x = x ^ t ^ (t << 28);
+                x = bytes_dec(x);
+#pragma unroll
+                for (int b = 0; b < 8; ++b) col[(8 * g + b) * CP] = (uint8_t)(x >> (8 * b));
+            }
+            __syncthreads();
+            const bool whole = vec && v0 + C <= n;
+            if (whole) {
+                // each lane stores BL bytes; a store instruction covers RS rows
+                constexpr int BL = C >= 256 ? 8 : 4;
+                constexpr int LPR = C / BL;       // lanes per row
+                constexpr int RS = 32 / LPR;      // rows per store instruction
+                const int rr = (int)lane / LPR, cb = ((int)lane % LPR) * BL;
+                for (int r0 = (int)warp * RS; r0 < rows; r0 += (kMsBlock / 32) * RS) {
+                    const int r = r0 + rr;
+                    if (r >= rows) continue;
+                    // columns [cb, cb + BL) sit at (cb + rotation) % C, a
+                    // multiple of BL: the BL bytes stay together
+                    const uint8_t *src = tile + r * CP + ((cb + (r / 64) * SW) % C);
+                    int8_t *dst = levels + (int64_t)r * n + v0 + cb;
+                    if constexpr (BL == 8)
+                        *reinterpret_cast<unsigned long long *>(dst) =
+                            *reinterpret_cast<const unsigned long long *>(src);
+                    else
+                        *reinterpret_cast<uint32_t *>(dst) = *reinterpret_cast<const uint32_t *>(src);
                 }
-#pragma unroll
-                for (int g = 0; g < 8; ++g) acc[g] = bytes_dec(acc[g]);
-                const int rows = k - i * 64 < 64 ? k - i * 64 : 64;
-                int8_t *col = levels + (int64_t)(i * 64) * n + v;
-#pragma unroll
-                for (int b = 0; b < 64; ++b) {
-                    if (b >= rows) break;
-                    if (inb) col[(int64_t)b * n] = (int8_t)(acc[b >> 3] >> (8 * (b & 7)));
+            } else {
+                for (int r = (int)warp; r < rows; r += kMsBlock / 32) {
+                    int8_t *dst = levels + (int64_t)r * n + v0;
+                    const uint8_t *src = tile + r * CP;
+                    const int rot = (r / 64) * SW;
+                    for (int c = (int)lane; c < C; c += 32)
+                        if (v0 + c < n) dst[c] = (int8_t)src[(c + rot) % C];
                 }
-            } else if (inb) {
-                for (int j = j_lo; j < j_hi; ++j) {
-                    unsigned long long m = ld<CO>(fr + (int64_t)(j % lcap) * slot_words + v * W + i);
-                    while (m) {
-                        const int b = __ffsll((long long)m) - 1;
-                        m &= m - 1;
-                        if (i * 64 + b < k) levels[(int64_t)(i * 64 + b) * n + v] = (int8_t)j;
-                    }
+            }
+            __syncthreads();
+        } else if (inb) {
+            for (int j = j_lo; j < j_hi; ++j) {
+                unsigned long long m = ld<CO>(fr + (int64_t)(j % lcap) * slot_words + v * W + i);
+                while (m) {
+                    const int b = __ffsll((long long)m) - 1;
+                    m &= m - 1;
+                    if (i * 64 + b < k) levels[(int64_t)(i * 64 + b) * n + v] = (int8_t)j;
                 }
             }
         }
@@ -715,8 +765,8 @@ __global__ void __launch_bounds__(kMsBlock) ms_finalize_kernel(
 template <int W>
 __global__ void __launch_bounds__(kMsBlock) ms_levels_kernel(
     const unsigned long long *fr, int64_t slot_words, int lcap, int j_lo, int j_hi, int64_t n,
-    int k, int8_t *levels, int full) {
-    ms_levels_phase<W, false>(fr, slot_words, lcap, j_lo, j_hi, n, k, levels, full);
+    int k, int8_t *levels, int full, int vec) {
+    ms_levels_phase<W, false>(fr, slot_words, lcap, j_lo, j_hi, n, k, levels, full, vec);
 }
 
 struct MsPersist {
@@ -726,7 +776,7 @@ struct MsPersist {
     int64_t n, nnz;
     unsigned long long *seen, *fr, *live;
     int64_t slot_words;
-    int lcap, k;
+    int lcap, k, vec;
     int8_t *levels;
     int32_t *list, *big;
     int64_t *trace;   // ring of kMsRingP slots; slot 0 written by ms_roots_kernel
@@ -767,7 +817,7 @@ __global__ void __launch_bounds__(kMsBlock) ms_persistent_kernel(MsPersist p) {
         }
         if (d + 1 - j_lo >= p.lcap) {  // the next slot still holds an unwritten layer
             ms_levels_phase<W, true>(p.fr, p.slot_words, p.lcap, j_lo, d + 1, p.n, p.k, p.levels,
-                                     !flushed);
+                                     !flushed, p.vec);
             flushed = 1;
             j_lo = d + 1;
             if (!grid_barrier(p.bar, p.err, expected, p.timeout_ns)) {
@@ -795,7 +845,9 @@ __global__ void __launch_bounds__(kMsBlock) ms_persistent_kernel(MsPersist p) {
             ms_bu_phase<W, true>(p.off, p.idx, p.base_vis, p.n, act, p.seen, cur, nxt, p.probe,
                                  (unsigned long long *)sn, sz, live_next, live_zero);
         } else {
-            ms_compact_phase<W, true>(cur, p.n, p.off, p.big_deg, p.list, p.big,
+            int64_t bd = e_f / ((int64_t)gridDim.x * (kMsBlock / 32));
+            bd = bd < 64 ? 64 : (bd > p.big_deg ? p.big_deg : bd);
+            ms_compact_phase<W, true>(cur, p.n, p.off, bd, p.list, p.big,
                                       (unsigned long long *)sc);
             const int64_t stride = (int64_t)gridDim.x * blockDim.x;
             for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.slot_words;
@@ -825,7 +877,7 @@ __global__ void __launch_bounds__(kMsBlock) ms_persistent_kernel(MsPersist p) {
     }
     if (status != BFS_ERR_TIMEOUT)  // levels of the layers still in the ring
         ms_levels_phase<W, true>(p.fr, p.slot_words, p.lcap, j_lo, d + 1, p.n, p.k, p.levels,
-                                 !flushed);
+                                 !flushed, p.vec);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         p.result[0] = d;
         p.result[1] = status;
@@ -934,10 +986,11 @@ bfs_status run_batch_w(bfs_graph *g, const int32_t *roots, int k, int8_t *levels
     GB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu_occ, ms_bu_kernel<W>, kMsBlock, 0));
     GB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&td_occ, ms_td_kernel<W>, kMsBlock, 0));
     GB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lv_occ, ms_levels_kernel<W>, kMsBlock, 0));
-    const int64_t ntiles = (n + 31) / 32;
+    const int64_t ntiles = (n + kMsBlock / W - 1) / (kMsBlock / W);
+    const int vec = (n % 8 == 0 && (uintptr_t)levels % 8 == 0) ? 1 : 0;
     auto write_levels = [&](int j_lo, int j_hi, int full) -> bfs_status {
-        GB_LAUNCH(ms_levels_kernel<W>, grid_cap(ntiles, kMsBlock / 32, lv_occ), kMsBlock, 0, st,
-                  m->fr, slot_words, lcap, j_lo, j_hi, n, k, levels, full);
+        GB_LAUNCH(ms_levels_kernel<W>, grid_cap(ntiles, 1, lv_occ), kMsBlock, 0, st, m->fr,
+                  slot_words, lcap, j_lo, j_hi, n, k, levels, full, vec);
         return BFS_OK;
     };
     GB_LAUNCH(ms_fill_kernel, grid_cap(n * W, kMsBlock, 8), kMsBlock, 0, st, seen, m->fr, n * W);
@@ -953,6 +1006,7 @@ bfs_status run_batch_w(bfs_graph *g, const int32_t *roots, int k, int8_t *levels
     int cur_bu = 0, j_lo = 0, flushed = 0, d = 0;
     const int64_t nwords = (n + 31) / 32;
     const int bu_grid = grid_cap(nwords, kMsBlock / 32, bu_occ);
+    const int64_t td_warps = (int64_t)sm_count() * td_occ * (kMsBlock / 32);
     for (d = 0; v_f > 0; ++d) {
         if (d + 1 > 127) {
             bfs_status s = write_levels(j_lo, d + 1, !flushed);
@@ -989,13 +1043,16 @@ bfs_status run_batch_w(bfs_graph *g, const int32_t *roots, int k, int8_t *levels
                       act, seen, cur, nxt, cfg.lane_probe, (unsigned long long *)slot_next,
                       slot_zero, live_next, live_zero);
         } else {
+            // grid-spread threshold: the frontier's edges per resident warp,
+            // clamped to [64, big_degree]
+            const int64_t big_deg = std::max<int64_t>(
+                64, std::min<int64_t>(cfg.big_degree, e_f / td_warps));
             GB_LAUNCH(ms_compact_kernel<W>, grid_cap(n, kMsBlock * 4, 8), kMsBlock, 0, st, cur, n,
-                      g->off, (int64_t)cfg.big_degree, m->list, m->big,
-                      (unsigned long long *)slot_cur);
+                      g->off, big_deg, m->list, m->big, (unsigned long long *)slot_cur);
             GB_CK(cudaMemsetAsync(nxt, 0, (size_t)slot_words * 8, st));
             GB_LAUNCH(ms_td_kernel<W>, grid_cap(v_f, kMsBlock, td_occ), kMsBlock, 0, st, g->off,
                       g->idx, m->list, (const unsigned long long *)slot_cur, cur, seen, nxt);
-            if (e_f >= cfg.big_degree)
+            if (e_f >= big_deg)
                 GB_LAUNCH(ms_td_big_kernel<W>,
                           (int)std::max<int64_t>(1, std::min<int64_t>(e_f / 2048 + 1,
                                                                       (int64_t)sm_count() * 4)),
@@ -1069,6 +1126,7 @@ bfs_status run_batch_graph(bfs_graph *g, const int32_t *roots, int k, int8_t *le
         p.slot_words = n * W;
         p.lcap = ring_slots(m, W);
         p.k = k;
+        p.vec = (n % 8 == 0 && (uintptr_t)levels % 8 == 0) ? 1 : 0;
         p.levels = levels;
         p.list = m->list;
         p.big = m->big;
