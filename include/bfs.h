@@ -134,8 +134,12 @@ typedef struct bfs_config {
     int32_t bu_words;        /* bottom-up: bitmap words a warp keeps in
                                 flight (1, 2 or 4)                             */
     int32_t td_claim;        /* top-down claim of a vertex: 0 = atomicCAS on
-                                parent[v] (-1 -> u); 1 = atomicOr on the
-                                visited bitmap word, then plain parent store  */
+                                parent[v] (-1 -> u); 1 (default) = atomicOr
+                                on the visited bitmap word, then plain parent
+                                store. With 1, the host loop and two-pass
+                                bottom-up layers, the -1 fill of level and
+                                parent is done by the first bottom-up sweep
+                                instead of before the traversal             */
     int32_t bu_head;         /* the bottom-up step first tests the neighbour
                                 held in an 8-byte record per vertex
                                 {neighbour, degree}, built on first use (8*n
@@ -279,8 +283,10 @@ typedef struct bfs_batch_config {
     double beta;          /* bottom-up -> top-down iff v_f < n / beta         */
     int32_t lane_probe;   /* bottom-up: neighbours a lane scans alone before
                              the warp-cooperative OR-reduction takes over     */
-    int32_t big_degree;   /* top-down: degree from which a vertex's edges are
-                             spread over the grid                             */
+    int32_t big_degree;   /* top-down: largest degree threshold from which a
+                             vertex's edges are spread over the grid (the
+                             threshold of a layer is its frontier's edges per
+                             resident warp, clamped to [64, big_degree])      */
     int32_t use_graph;    /* 1 = run the layers as one CUDA graph with a
                              device-side loop (no per-layer host round trip) */
     int32_t timing;       /* 1 = record CUDA events per layer                 */

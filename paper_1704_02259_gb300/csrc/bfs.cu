@@ -137,17 +137,25 @@ __global__ void reached_bits_kernel(const int32_t *__restrict__ level, int64_t n
     }
 }
 
+// write_out = 0 leaves level and parent unwritten except at the root: the
+// first hub sweep of the traversal (or out_fill_kernel) writes the rest.
 __global__ void init_kernel(int64_t n, int64_t nw_pad, int32_t root,
                             const int64_t *__restrict__ off, const uint32_t *__restrict__ base,
                             const uint32_t *__restrict__ comp_in,
                             int32_t *__restrict__ level, int32_t *__restrict__ parent,
                             uint32_t *__restrict__ visited, uint32_t *__restrict__ front,
-                            int32_t *__restrict__ queue, int64_t *__restrict__ trace) {
+                            int32_t *__restrict__ queue, int64_t *__restrict__ trace,
+                            int write_out) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    for (int64_t i = t0; i < n; i += stride) {
-        level[i] = (i == root) ? 0 : -1;
-        parent[i] = (i == root) ? root : -1;
+    if (write_out) {
+        for (int64_t i = t0; i < n; i += stride) {
+            level[i] = (i == root) ? 0 : -1;
+            parent[i] = (i == root) ? root : -1;
+        }
+    } else if (t0 == 0) {
+        level[root] = 0;
+        parent[root] = root;
     }
     const int64_t rw = root >> 5;
     const uint32_t rbit = 1u << (root & 31);
@@ -165,6 +173,23 @@ __global__ void init_kernel(int64_t n, int64_t nw_pad, int32_t root,
         trace[i] = v;
     }
     if (t0 == 0) queue[0] = root;
+}
+
+// level = parent = -1 for every vertex not reached so far (not visited, or
+// visited only as a degree-0 vertex or id past n), the root excepted: the
+// outputs of a traversal that started without write_out and has had no
+// writing hub sweep.
+__global__ void out_fill_kernel(int64_t n, int32_t root, const uint32_t *__restrict__ visited,
+                                const uint32_t *__restrict__ base,
+                                int32_t *__restrict__ level, int32_t *__restrict__ parent) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += stride) {
+        const uint32_t reached = visited[v >> 5] & ~base[v >> 5];
+        if (v != root && !((reached >> (v & 31)) & 1u)) {
+            level[v] = -1;
+            parent[v] = -1;
+        }
+    }
 }
 
 __device__ __forceinline__ void block_add4(int64_t a, int64_t b, int64_t c, int64_t e,
@@ -938,12 +963,17 @@ __device__ __forceinline__ void bu_list_phase(
 // vertex of degree 1 is not marked, since its only neighbour is the hub (its
 // one-entry scan is counted here). Every word below nw_pad is written, so
 // next and pend need no clearing.
+// With init_out (the first sweep of a traversal that skipped the -1 fill),
+// every vertex below n not reached in an earlier layer gets its outputs
+// here: the hit's values, else -1 (a later find overwrites them), so the
+// warp's stores cover whole sectors wherever no earlier-reached vertex sits.
 template <bool CO>
 __device__ __forceinline__ void bu_hub_phase(
     const int2 *__restrict__ head, int64_t nw_pad, uint32_t *__restrict__ visited,
     const uint32_t *__restrict__ front, uint32_t *__restrict__ next_bm,
     uint32_t *__restrict__ pend, int32_t *__restrict__ parent, int32_t *__restrict__ level,
-    int32_t new_level, unsigned long long *slot_next, int64_t *zero_slot) {
+    int32_t new_level, unsigned long long *slot_next, int64_t *zero_slot, int init_out,
+    const uint32_t *__restrict__ base, int64_t n, int32_t root) {
     constexpr int R = 8;
     if (blockIdx.x == 0 && threadIdx.x < kFields) zero_slot[threadIdx.x] = 0;
     const unsigned lane = lane_id();
@@ -974,6 +1004,10 @@ __device__ __forceinline__ void bu_hub_phase(
                 level[v] = new_level;
                 my_mf += h[k].y;
                 my_nf += 1;
+            } else if (init_out && v < n && v != root &&
+                       !(((vw[k] & ~__ldg(base + w0 + k)) >> lane) & 1u)) {
+                parent[v] = -1;
+                level[v] = -1;
             }
             const unsigned fb = __ballot_sync(0xffffffffu, found);
             const unsigned pb = __ballot_sync(0xffffffffu, probed && !found && h[k].y > 1);
@@ -992,9 +1026,10 @@ __global__ void __launch_bounds__(kBlock, 4) bu_hub_kernel(
     const int2 *__restrict__ head, int64_t nw_pad, uint32_t *__restrict__ visited,
     const uint32_t *__restrict__ front, uint32_t *__restrict__ next_bm,
     uint32_t *__restrict__ pend, int32_t *__restrict__ parent, int32_t *__restrict__ level,
-    int32_t new_level, unsigned long long *slot_next, int64_t *zero_slot) {
+    int32_t new_level, unsigned long long *slot_next, int64_t *zero_slot, int init_out,
+    const uint32_t *__restrict__ base, int64_t n, int32_t root) {
     bu_hub_phase<false>(head, nw_pad, visited, front, next_bm, pend, parent, level, new_level,
-                        slot_next, zero_slot);
+                        slot_next, zero_slot, init_out, base, n, root);
 }
 
 __global__ void __launch_bounds__(kBlock) bu_list_kernel(
@@ -1237,7 +1272,8 @@ __global__ void __launch_bounds__(kBlock, 4) bfs_persistent_kernel(SsPersist p) 
                 // two passes: hub probes over the words, then the rows of the
                 // vertices whose hub missed, one lane each
                 bu_hub_phase<true>(p.head, p.nw_pad, p.visited, front, next, p.pend, p.parent,
-                                   p.level, d + 1, (unsigned long long *)sn, sz);
+                                   p.level, d + 1, (unsigned long long *)sn, sz, 0, nullptr, p.n,
+                                   -1);
                 if (!grid_barrier(p.bar, p.err, expected, p.timeout_ns)) {
                     status = BFS_ERR_TIMEOUT;
                     break;
@@ -1458,6 +1494,7 @@ extern "C" BFS_API void bfs_config_default(bfs_config *c) {
     c->timing = 0;
     c->bu_words = 2;
     c->bu_head = 2;
+    c->td_claim = 1;
     c->prune_components = 0;
     c->bu_list_percent = 10;
     c->device_loop = 2;
@@ -1681,10 +1718,19 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
     g->last.clear();
     uint32_t *front = g->bm_a, *next = g->bm_b;
     int32_t *q_cur = g->q_a, *q_next = g->q_b;
+    const bool dev_loop = cfg.device_loop == 1 || (cfg.device_loop == 2 && n <= kDeviceLoopAutoMaxN);
+    // dense bottom-up layers run in two passes on hub records
+    const bool two_pass =
+        cfg.bu_head == 2 &&
+        g->nw >= (int64_t)8 * sm_count() * g->bu_hub_blocks_per_sm * (kBlock / 32);
+    // Without the CAS claim on parent nothing reads the outputs before they
+    // are written, so the -1 fill can wait for the first hub sweep (which
+    // writes every vertex not reached before it, mostly whole sectors).
+    const bool fuse_init = !dev_loop && two_pass && cfg.td_claim == 1 && !cfg.prune_components;
     GB_LAUNCH(init_kernel, grid_cap(std::max(n, g->nw_pad), kBlock, 8), kBlock, 0, st, n,
               g->nw_pad, root, g->off, g->base_vis, cfg.prune_components ? g->comp_in : nullptr,
-              level, parent, g->visited, front, q_cur, g->trace);
-    if (cfg.device_loop == 1 || (cfg.device_loop == 2 && n <= kDeviceLoopAutoMaxN)) {
+              level, parent, g->visited, front, q_cur, g->trace, fuse_init ? 0 : 1);
+    if (dev_loop) {
         const bfs_status ds = run_device_loop(g, level, parent, st);
         if (ds != BFS_OK) return ds;
     } else {
@@ -1703,6 +1749,13 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
             1, std::min<int64_t>((g->nw_pad >> 5) * (32 / bu_span_w) / (kBlock / 32) + 1,
                                  bu_full));
         const int64_t td_warps = (int64_t)sm_count() * g->td_blocks_per_sm * (kBlock / 32);
+        bool filled = !fuse_init;  // outputs of unreached vertices hold -1
+        auto fill_outputs = [&]() -> bfs_status {
+            GB_LAUNCH(out_fill_kernel, grid_cap(n, kBlock, 8), kBlock, 0, st, n, root, g->visited,
+                      g->base_vis, level, parent);
+            filled = true;
+            return BFS_OK;
+        };
         for (int d = 0; n_f > 0; ++d) {
             if (d > n) {  // a BFS has at most n layers: the counters are inconsistent
                 set_error("bfs_run: traversal did not terminate after %lld layers", (long long)n);
@@ -1771,6 +1824,10 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                 if (cfg.bu_list_percent > 0 && active * 100 <= (int64_t)cfg.bu_list_percent * n) {
                     // sparse layer: a compacted list of them, one lane each
                     ls.converted = 2;
+                    if (!filled) {
+                        const bfs_status fs = fill_outputs();
+                        if (fs != BFS_OK) return fs;
+                    }
                     GB_CK(cudaMemsetAsync(next, 0, (size_t)g->nw_pad * 4, st));
                     GB_LAUNCH(bits_list_kernel, grid_cap(g->nw, kBlock * 4, 8), kBlock, 0, st,
                               g->visited, ~0u, g->nw, q_next,
@@ -1781,15 +1838,16 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                               hskip, q_next, (const unsigned long long *)(slot_cur + T_ULIST),
                               g->visited, front, next, parent, level, d + 1, cfg.bu_probe,
                               (unsigned long long *)slot_next, slot_zero);
-                } else if (cfg.bu_head == 2 &&
-                           g->nw >= (int64_t)8 * sm_count() * g->bu_hub_blocks_per_sm * (kBlock / 32)) {
+                } else if (two_pass) {
                     // two passes: hub probes over the words, then the rows of
                     // the vertices whose hub missed, one lane each
                     ls.converted = 3;
                     if (!g->pend) GB_CK(cudaMalloc(&g->pend, (size_t)g->nw_pad * 4));
                     GB_LAUNCH(bu_hub_kernel, grid_cap(g->nw_pad, kBlock / 32 * 8, g->bu_hub_blocks_per_sm),
                               kBlock, 0, st, g->head, g->nw_pad, g->visited, front, next, g->pend,
-                              parent, level, d + 1, (unsigned long long *)slot_next, slot_zero);
+                              parent, level, d + 1, (unsigned long long *)slot_next, slot_zero,
+                              filled ? 0 : 1, g->base_vis, n, root);
+                    filled = true;
                     if (timing) GB_CK(cudaEventRecord(event(e0 + 3), st));
                     GB_LAUNCH(bits_list_kernel, grid_cap(g->nw, kBlock * 4, 8), kBlock, 0, st,
                               g->pend, 0u, g->nw, q_next,
@@ -1801,6 +1859,10 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                               next, parent, level, d + 1, cfg.bu_probe,
                               (unsigned long long *)slot_next, slot_zero);
                 } else {
+                    if (!filled) {
+                        const bfs_status fs = fill_outputs();
+                        if (fs != BFS_OK) return fs;
+                    }
                     decltype(BU1) const kernels[6] = {BU1, BU2, BU4, BU1H, BU2H, BU4H};
                     auto bu = kernels[bsel];
                     GB_LAUNCH(bu, bu_grid, kBlock, 0, st, g->off, g->idx, g->head, g->nw_pad,
@@ -1823,6 +1885,10 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
             m_f = m_new;
             std::swap(front, next);
             std::swap(q_cur, q_next);
+        }
+        if (!filled) {
+            const bfs_status fs = fill_outputs();
+            if (fs != BFS_OK) return fs;
         }
         g->last_component_edges = degree_sum / 2;
         if (timing) {
@@ -1947,7 +2013,7 @@ extern "C" BFS_API bfs_status bfs_run_noalloc(const int64_t *offsets, const int3
               base_vis);
     GB_LAUNCH(init_kernel, grid_cap(std::max(n, nw_pad), kBlock, 8), kBlock, 0, st, n, nw_pad,
               root, offsets, base_vis, nullptr, level_out, parent_out, visited, front, q_cur,
-              trace);
+              trace, 1);
     int64_t h[kFields];
     GB_CK(cudaMemcpyAsync(h, trace, sizeof h, cudaMemcpyDeviceToHost, st));
     GB_CK(cudaStreamSynchronize(st));

@@ -193,6 +193,36 @@ def test_large_top_down_layers(pat, loop):
         assert max(x["m_f"] for x in g.stats().layers) > (1 << 18)
 
 
+@pytest.mark.parametrize("cfg", [dict(), dict(forced=[0, 0, 1]), dict(forced=[1]),
+                                 dict(bu_list_percent=100), dict(forced=[0])])
+def test_outputs_written_by_first_sweep(cfg):
+    # scale 21 with the host loop: dense bottom-up layers run in two passes
+    # and (td_claim = 1) the first hub sweep writes the -1 of every vertex not
+    # reached before it; traversals without such a sweep (top-down only,
+    # list layers first, a degree-0 root, a small component) fill at the end
+    n, o_off, o_idx, g_off, g_idx = _rmat_both(21, 16, 7)
+    full = dict(device_loop=0, td_claim=1, **cfg)
+    g = gb.Graph(g_off, g_idx, config(**full))
+    deg = np.diff(o_off)
+    ref_big = oracle.bfs(o_off, o_idx, int(np.argmax(deg)))[0]
+    small = [v for v in range(n) if deg[v] > 0 and ref_big[v] < 0][:1]
+    roots = [int(r) for r in oracle.sample_roots(o_off, n, 9, 3)] + small
+    roots.append(int(np.nonzero(deg == 0)[0][0]))
+    lv = torch.full((n,), 77, dtype=torch.int32, device="cuda")
+    pa = torch.full((n,), 77, dtype=torch.int32, device="cuda")
+    for r in roots:
+        lv.fill_(77)
+        pa.fill_(77)       # stale values that must all be overwritten
+        g.run(r, lv, pa)
+        torch.cuda.synchronize()
+        got, par = lv.cpu().numpy(), pa.cpu().numpy()
+        ref, _ = oracle.bfs(o_off, o_idx, r)
+        assert np.array_equal(got, ref)
+        assert oracle.check_parents(o_off, o_idx, r, got, par) == 0
+        assert (par[ref < 0] == -1).all()
+    check_run(o_off, o_idx, g, roots[0], forced=cfg.get("forced"))
+
+
 @pytest.mark.parametrize("kind,seed", [(oracle.RMAT, 1), (oracle.ER, 3)])
 def test_scale20_all_64_roots(kind, seed):
     # R-MAT scale 20 (the paper's one-million-vertex size) and its ER control
