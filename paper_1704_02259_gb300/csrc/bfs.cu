@@ -975,6 +975,7 @@ __device__ __forceinline__ void bu_hub_phase(
     int32_t new_level, unsigned long long *slot_next, int64_t *zero_slot, int init_out,
     const uint32_t *__restrict__ base, int64_t n, int32_t root) {
     constexpr int R = 8;
+    static_assert(32 % R == 0, "a round's R words must not cross nw_pad (a multiple of 32)");
     if (blockIdx.x == 0 && threadIdx.x < kFields) zero_slot[threadIdx.x] = 0;
     const unsigned lane = lane_id();
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
