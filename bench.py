@@ -47,9 +47,11 @@ def parse():
     p.add_argument("--cpu-scale", type=int, default=20,
                    help="scale of the oracle's bounded sample graph")
     p.add_argument("--cpu-roots", type=int, default=8)
-    p.add_argument("--mode", default="single", choices=["single", "serve"],
+    p.add_argument("--mode", default="single", choices=["single", "serve", "batch"],
                    help="single: the headline line (single-source + batched); "
-                        "serve: the serving stream over 8 resident graphs")
+                        "serve: the serving stream over 8 resident graphs; "
+                        "batch: one batched configuration timed alone")
+    p.add_argument("--batch-k", type=int, default=512, help="roots per batch (--mode batch)")
     p.add_argument("--no-batch", action="store_true", help="skip the batched comparison")
     p.add_argument("--device-loop", type=int, default=2, choices=[0, 1, 2],
                    help="bfs_config.device_loop: 0 host loop, 1 device loop, 2 library default")
@@ -281,6 +283,53 @@ def batched_comparison(gb, torch, scale, seed=1, root_seed=4, ks=(64, 128, 256, 
     return out
 
 
+def run_batch_mode(args):
+    """One batched configuration timed alone (R-MAT --batch-scale, --batch-k
+    roots, the default batch configuration, host-driven layers): W untimed
+    and K timed batches, CUDA events on the stream; value = aggregate GTEPS
+    (sum of the roots' component edges per batch / batch time)."""
+    import torch
+    import paper_1704_02259_gb300 as gb
+    torch.cuda.set_device(0)
+    scale, k = args.batch_scale, args.batch_k
+    n = 1 << scale
+    off, idx = gb.rmat_graph(scale, 16, 1)
+    g = gb.Graph(off, idx)
+    roots = gb.sample_roots(off, n, 4, k)
+    lv = torch.empty(n, dtype=torch.int32, device="cuda")
+    pa = torch.empty_like(lv)
+    edges = 0
+    for r in roots.tolist():
+        g.run(r, lv, pa)
+        edges += g.stats().component_edges
+    levels = torch.empty((k, n), dtype=torch.int8, device="cuda")
+    st = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for _ in range(args.warmup):
+        g.run_batch(roots, levels)
+    launches0 = gb.launch_count()
+    ts = []
+    torch.cuda.nvtx.range_push("timed")
+    for _ in range(args.steps):
+        ev[0].record(st)
+        g.run_batch(roots, levels)
+        ev[1].record(st)
+        ev[1].synchronize()
+        ts.append(ev[0].elapsed_time(ev[1]))
+    torch.cuda.nvtx.range_pop()
+    ms = statistics.median(ts)
+    layers, pairs = g.batch_stats()
+    print(json.dumps({
+        "metric": "batched multi-source BFS, aggregate GTEPS", "mode": "batch",
+        "value": edges / ms / 1e6, "unit": "GTEPS", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": f"rmat-scale{scale}-ef16-k{k}", "k": k, "n": n,
+                   "directions": "".join("B" if L["direction"] else "T" for L in layers)},
+        "pairs_reached": pairs, "gpu_launches": gb.launch_count() - launches0}), flush=True)
+    g.close()
+
+
 def run_serve(args):
     """Serving: 8 resident R-MAT graphs (scales 14, 16, 18..23, edgefactor 16,
     seeds 10..17), Poisson arrivals at each rate, graph uniform, root uniform
@@ -340,6 +389,9 @@ def main():
     args = parse()
     if args.mode == "serve":
         run_serve(args)
+        return
+    if args.mode == "batch":
+        run_batch_mode(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
