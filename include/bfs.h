@@ -286,7 +286,9 @@ typedef struct bfs_batch_config {
     int32_t big_degree;   /* top-down: largest degree threshold from which a
                              vertex's edges are spread over the grid (the
                              threshold of a layer is its frontier's edges per
-                             resident warp, clamped to [64, big_degree])      */
+                             resident row walker -- a warp for k <= 64, a
+                             group of W lanes above -- clamped to
+                             [32, big_degree])                               */
     int32_t use_graph;    /* 1 = run the layers as one CUDA graph with a
                              device-side loop (no per-layer host round trip) */
     int32_t timing;       /* 1 = record CUDA events per layer                 */

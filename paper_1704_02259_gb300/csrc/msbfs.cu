@@ -449,9 +449,15 @@ __device__ __forceinline__ void ms_push(const unsigned long long (&cu)[W], int64
     }
 }
 
-// Top-down layer on bit lanes over the compacted list: a warp takes 32
-// entries; rows shorter than 32 are walked by their own lane, longer ones
-// by the whole warp.
+// Top-down layer on bit lanes over the compacted list.
+//   W = 1: a warp takes 32 entries; rows shorter than 32 are walked by their
+//     own lane, longer ones by the whole warp.
+//   W > 1: a group of W lanes (lane i = lane word i) takes one entry, so a
+//     pushed edge is one broadcast index load, one coalesced 8W-byte load of
+//     the neighbour's seen words and at most one atomicOr per lane; the
+//     32 / W groups of a warp take consecutive entries, 4 edges in flight;
+//     rows of 32 or more edges are walked by the whole warp, group g on
+//     edges g, g + 32 / W, ...
 template <int W, bool CO>
 __device__ __forceinline__ void ms_td_phase(
     const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
@@ -462,6 +468,64 @@ __device__ __forceinline__ void ms_td_phase(
     const unsigned lane = lane_id();
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    if constexpr (W > 1) {
+        constexpr int G = 32 / W;  // groups per warp
+        const int gid = (int)(lane / W), wi = (int)(lane % W);
+        for (int64_t base = gw * G; base < cnt; base += tw * G) {
+            const int64_t e_i = base + gid;
+            int64_t beg = 0, end = 0;
+            unsigned long long cu = 0ull;
+            if (e_i < cnt) {
+                const int64_t u = ld<CO>(list + e_i);
+                beg = off[u];
+                end = off[u + 1];
+                cu = CO ? __ldcg(cur + u * W + wi) : __ldg(cur + u * W + wi);
+            }
+            if (end - beg < 32) {
+                for (int64_t e = beg; e < end; e += 4) {
+                    int64_t v[4];
+                    unsigned long long sv[4];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) v[t] = e + t < end ? (int64_t)__ldg(idx + e + t) : -1;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        sv[t] = v[t] >= 0 ? ld<CO>(seen + v[t] * W + wi) : ~0ull;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const unsigned long long add = cu & ~sv[t];
+                        if (add) atomicOr(nxt + v[t] * W + wi, add);
+                    }
+                }
+            }
+            // rows of 32 or more: the whole warp, one row at a time
+            unsigned wm = __ballot_sync(0xffffffffu, wi == 0 && end - beg >= 32);
+            while (wm) {
+                const int L = __ffs(wm) - 1;
+                wm &= wm - 1;
+                const int64_t lb = __shfl_sync(0xffffffffu, beg, L);
+                const int64_t le = __shfl_sync(0xffffffffu, end, L);
+                const unsigned long long cL = __shfl_sync(0xffffffffu, cu, L + wi);
+                for (int64_t e0 = lb + gid; e0 < le; e0 += 4 * G) {
+                    int64_t v[4];
+                    unsigned long long sv[4];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int64_t e = e0 + (int64_t)t * G;
+                        v[t] = e < le ? (int64_t)__ldg(idx + e) : -1;
+                    }
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        sv[t] = v[t] >= 0 ? ld<CO>(seen + v[t] * W + wi) : ~0ull;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const unsigned long long add = cL & ~sv[t];
+                        if (add) atomicOr(nxt + v[t] * W + wi, add);
+                    }
+                }
+            }
+        }
+        return;
+    }
     for (int64_t base = gw * 32; base < cnt; base += tw * 32) {
         const int64_t i = base + lane;
         int64_t u = 0, beg = 0, end = 0;
@@ -542,6 +606,8 @@ __device__ __forceinline__ void ms_td_big_phase(
         if (threadIdx.x == kMsBlock - 1) pre[kMsBigBatch] = run;
         __syncthreads();
         const long long total = pre[kMsBigBatch];
+        // one thread per edge with all W words: the owner search is shared
+        // by the words (a group of W threads per edge measured slower here)
         for (long long g = gt; g < total; g += tt) {
             int lo = 0, hi = nb;
             while (hi - lo > 1) {
@@ -845,8 +911,8 @@ __global__ void __launch_bounds__(kMsBlock) ms_persistent_kernel(MsPersist p) {
             ms_bu_phase<W, true>(p.off, p.idx, p.base_vis, p.n, act, p.seen, cur, nxt, p.probe,
                                  (unsigned long long *)sn, sz, live_next, live_zero);
         } else {
-            int64_t bd = e_f / ((int64_t)gridDim.x * (kMsBlock / 32));
-            bd = bd < 64 ? 64 : (bd > p.big_deg ? p.big_deg : bd);
+            int64_t bd = e_f / ((int64_t)gridDim.x * (kMsBlock / 32) * (W > 1 ? 32 / W : 1));
+            bd = bd < 32 ? 32 : (bd > p.big_deg ? p.big_deg : bd);
             ms_compact_phase<W, true>(cur, p.n, p.off, bd, p.list, p.big,
                                       (unsigned long long *)sc);
             const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -1043,10 +1109,11 @@ bfs_status run_batch_w(bfs_graph *g, const int32_t *roots, int k, int8_t *levels
                       act, seen, cur, nxt, cfg.lane_probe, (unsigned long long *)slot_next,
                       slot_zero, live_next, live_zero);
         } else {
-            // grid-spread threshold: the frontier's edges per resident warp,
-            // clamped to [64, big_degree]
+            // grid-spread threshold: the frontier's edges per resident row
+            // walker (a warp for W = 1, a group of W lanes otherwise),
+            // clamped to [32, big_degree]
             const int64_t big_deg = std::max<int64_t>(
-                64, std::min<int64_t>(cfg.big_degree, e_f / td_warps));
+                32, std::min<int64_t>(cfg.big_degree, e_f / (td_warps * (W > 1 ? 32 / W : 1))));
             GB_LAUNCH(ms_compact_kernel<W>, grid_cap(n, kMsBlock * 4, 8), kMsBlock, 0, st, cur, n,
                       g->off, big_deg, m->list, m->big, (unsigned long long *)slot_cur);
             GB_CK(cudaMemsetAsync(nxt, 0, (size_t)slot_words * 8, st));
@@ -1225,9 +1292,11 @@ using namespace gbfs;
 extern "C" BFS_API void bfs_batch_config_default(bfs_batch_config *c) {
     if (!c) return;
     memset(c, 0, sizeof *c);
-    c->alpha = 1.0;   // the autotuner's choice on R-MAT scale 22, k = 64..512
-    c->beta = 96.0;
-    c->lane_probe = 16;
+    // the autotuner's choice on R-MAT scale 22, k = 64..512: top-down until
+    // the frontier is most of the graph, then bottom-up to the end
+    c->alpha = 1.0;
+    c->beta = 1e9;
+    c->lane_probe = 4;
     c->big_degree = 4096;
     c->use_graph = 0;
     c->timing = 0;
