@@ -539,8 +539,17 @@ __device__ __forceinline__ void ms_td_phase(
             load_lanes<W, CO>(cur + u * W, cu);
         }
         const bool wide = end - beg >= 32;
-        if (!wide)
-            for (int64_t e = beg; e < end; ++e) ms_push<W, CO>(cu, __ldg(idx + e), seen, nxt);
+        if (!wide) {
+            // 4 edges in flight per lane
+            for (int64_t e = beg; e < end; e += 4) {
+                int64_t v[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) v[t] = e + t < end ? (int64_t)__ldg(idx + e + t) : -1;
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (v[t] >= 0) ms_push<W, CO>(cu, v[t], seen, nxt);
+            }
+        }
         unsigned wm = __ballot_sync(0xffffffffu, wide);
         while (wm) {
             const int L = __ffs(wm) - 1;
