@@ -28,7 +28,10 @@
 // the step kernels into the layer's trace slot. The host reads that slot after
 // each layer and applies the Alg. 3 switch.
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -173,6 +176,18 @@ __global__ void init_kernel(int64_t n, int64_t nw_pad, int32_t root,
         trace[i] = v;
     }
     if (t0 == 0) queue[0] = root;
+}
+
+// Copies a trace slot into the mapped host block and then, after a system
+// fence, the sequence number the host waits for (one thread: the counters
+// are final, the kernels that added them came before on the stream).
+__global__ void publish_kernel(const int64_t *__restrict__ slot, int64_t *pub, int64_t seq) {
+    if (threadIdx.x == 0) {
+        volatile int64_t *vp = pub;
+        for (int i = 0; i < kFields; ++i) vp[i] = slot[i];
+        __threadfence_system();
+        vp[kFields] = seq;
+    }
 }
 
 // level = parent = -1 for every vertex not reached so far (not visited, or
@@ -1458,6 +1473,7 @@ void free_graph(bfs_graph *g) {
     cudaFree(g->level_scratch);
     cudaFree(g->trace);
     if (g->h_slot) cudaFreeHost(g->h_slot);
+    if (g->h_pub) cudaFreeHost(g->h_pub);
     for (cudaEvent_t e : g->events) cudaEventDestroy(e);
     delete g;
 }
@@ -1474,6 +1490,36 @@ bfs_status build_head(bfs_graph *g, int kind, cudaStream_t st) {
         GB_LAUNCH(hub_head_kernel, grid_cap(g->n, kBlock / 32, 8), kBlock, 0, st, g->off,
                   g->idx, g->n, g->head);
     g->head_kind = kind;
+    return BFS_OK;
+}
+
+// Publishes `slot` to the host block and waits for it there: a spin on the
+// sequence number in mapped memory instead of a copy plus a stream
+// synchronisation (a layer's host round trip is what small layers cost).
+// The spin gives up after 5 s and then synchronises the stream, which
+// returns the error of a failed kernel; the counters land in g->h_slot.
+bfs_status publish_and_wait(bfs_graph *g, const int64_t *slot, cudaStream_t st) {
+    const int64_t seq = ++g->pub_seq;
+    publish_kernel<<<1, 32, 0, st>>>(slot, g->d_pub, seq);
+    count_launch();
+    GB_CK(cudaGetLastError());
+    volatile int64_t *vp = g->h_pub;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (long spins = 0; vp[kFields] != seq; ++spins) {
+        if ((spins & 1023) == 1023) {
+            if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(5)) {
+                GB_CK(cudaStreamSynchronize(st));
+                if (vp[kFields] != seq) {
+                    set_error("bfs_run: the layer counters never arrived");
+                    return BFS_ERR_CUDA;
+                }
+                break;
+            }
+            if (spins > (1 << 16)) std::this_thread::yield();
+        }
+    }
+    std::atomic_thread_fence(std::memory_order_acquire);
+    for (int i = 0; i < kFields; ++i) g->h_slot[i] = vp[i];
     return BFS_OK;
 }
 
@@ -1558,6 +1604,9 @@ extern "C" BFS_API bfs_status bfs_graph_create(const int64_t *offsets, const int
     GB_CKG(cudaMalloc(&g->big, (size_t)n * 4));
     GB_CKG(cudaMalloc(&g->trace, (size_t)kRing * kFields * 8));
     GB_CKG(cudaMallocHost(&g->h_slot, kFields * 8));
+    GB_CKG(cudaHostAlloc((void **)&g->h_pub, (kFields + 1) * 8, cudaHostAllocMapped));
+    GB_CKG(cudaHostGetDevicePointer((void **)&g->d_pub, g->h_pub, 0));
+    g->h_pub[kFields] = 0;
     if (flags & BFS_VALIDATE) {
         int *bad = nullptr, hbad = 0;
         GB_CKG(cudaMalloc(&bad, sizeof(int)));
@@ -1735,8 +1784,10 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
         const bfs_status ds = run_device_loop(g, level, parent, st);
         if (ds != BFS_OK) return ds;
     } else {
-        GB_CK(cudaMemcpyAsync(g->h_slot, g->trace, kFields * 8, cudaMemcpyDeviceToHost, st));
-        GB_CK(cudaStreamSynchronize(st));
+        {
+            const bfs_status ps = publish_and_wait(g, g->trace, st);
+            if (ps != BFS_OK) return ps;
+        }
         int64_t n_f = 1, m_f = g->h_slot[T_MF];
         int64_t n_u = n - 1, m_u = g->nnz - m_f;
         int cur_bu = 0;
@@ -1873,8 +1924,10 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                 have_queue = false;
             }
             if (timing) GB_CK(cudaEventRecord(event(e0 + 2), st));
-            GB_CK(cudaMemcpyAsync(g->h_slot, slot_next, kFields * 8, cudaMemcpyDeviceToHost, st));
-            GB_CK(cudaStreamSynchronize(st));
+            {
+                const bfs_status ps = publish_and_wait(g, slot_next, st);
+                if (ps != BFS_OK) return ps;
+            }
             const int64_t found = g->h_slot[T_NF], m_new = g->h_slot[T_MF];
             ls.examined = cur_bu ? g->h_slot[T_EXAM] : m_f;
             ls.found = found;
@@ -1891,6 +1944,7 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
             const bfs_status fs = fill_outputs();
             if (fs != BFS_OK) return fs;
         }
+        GB_CK(cudaStreamSynchronize(st));  // outputs complete, late errors surface
         g->last_component_edges = degree_sum / 2;
         if (timing) {
             for (size_t d = 0; d < g->last.size(); ++d) {

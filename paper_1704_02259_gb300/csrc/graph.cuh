@@ -42,6 +42,10 @@ struct bfs_graph {
     int32_t *parent_scratch = nullptr, *level_scratch = nullptr;
     int64_t *trace = nullptr;
     int64_t *h_slot = nullptr;  // pinned, kFields entries
+    // mapped pinned block the host loop polls: kFields counters then a
+    // sequence number, written by publish_kernel (d_pub = device address)
+    int64_t *h_pub = nullptr, *d_pub = nullptr;
+    int64_t pub_seq = 0;
     bfs_config cfg;
     std::vector<bfs_layer_stats> last;
     int64_t last_component_edges = 0;
