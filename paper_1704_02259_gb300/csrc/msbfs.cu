@@ -31,7 +31,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
+#include <chrono>
 #include <mutex>
+#include <thread>
 
 #include "graph.cuh"
 
@@ -45,6 +48,10 @@ struct MsState {
     int32_t *list = nullptr, *big = nullptr, *roots = nullptr;
     int64_t *trace = nullptr;
     int64_t *h_slot = nullptr;  // pinned: one trace slot (8) and one live mask (8)
+    // mapped pinned block polled by the host loop: slot (8), live mask (8),
+    // sequence number; d_pub is its device address
+    int64_t *h_pub = nullptr, *d_pub = nullptr;
+    int64_t pub_seq = 0;
     bfs_batch_config cfg;
     std::vector<bfs_batch_layer_stats> last;
     int64_t last_pairs = 0;
@@ -74,6 +81,7 @@ void free_ms_state(bfs_graph *g) {
     cudaFree(m->trace);
     cudaFree(m->pctl);
     if (m->h_slot) cudaFreeHost(m->h_slot);
+    if (m->h_pub) cudaFreeHost(m->h_pub);
     if (m->h_pctl) cudaFreeHost(m->h_pctl);
     if (m->exec) cudaGraphExecDestroy(m->exec);
     if (m->graph) cudaGraphDestroy(m->graph);
@@ -999,6 +1007,9 @@ bfs_status ensure_ms(bfs_graph *g, int W) {
         GB_CK(cudaMalloc(&m->trace, (size_t)kMsRing * kMsFields * 8));
         GB_CK(cudaMalloc(&m->live, 3 * 8 * 8));
         GB_CK(cudaMallocHost(&m->h_slot, 16 * 8));
+        GB_CK(cudaHostAlloc((void **)&m->h_pub, 17 * 8, cudaHostAllocMapped));
+        GB_CK(cudaHostGetDevicePointer((void **)&m->d_pub, m->h_pub, 0));
+        m->h_pub[16] = 0;
     }
     if (W == 0) return BFS_OK;
     const int want = m->cfg.layer_slots;
@@ -1020,6 +1031,50 @@ bfs_status ensure_ms(bfs_graph *g, int W) {
         m->W = W;
         m->lcap = lcap;
     }
+    return BFS_OK;
+}
+
+// Copies a trace slot and a live mask into the mapped host block, then,
+// after a system fence, the sequence number the host waits for.
+__global__ void ms_publish_kernel(const int64_t *__restrict__ slot,
+                                  const unsigned long long *__restrict__ live, int64_t *pub,
+                                  int64_t seq) {
+    if (threadIdx.x == 0) {
+        volatile int64_t *vp = pub;
+        for (int i = 0; i < 8; ++i) vp[i] = slot[i];
+        for (int i = 0; i < 8; ++i) vp[8 + i] = (int64_t)live[i];
+        __threadfence_system();
+        vp[16] = seq;
+    }
+}
+
+// Publishes a layer's counters and live mask and spins on the sequence
+// number in mapped memory (instead of a copy and a stream synchronisation);
+// after 5 s the stream is synchronised, which returns a failed kernel's
+// error. The values land in m->h_slot[0..16).
+bfs_status ms_publish_and_wait(MsState *m, const int64_t *slot, const unsigned long long *live,
+                               cudaStream_t st) {
+    const int64_t seq = ++m->pub_seq;
+    ms_publish_kernel<<<1, 32, 0, st>>>(slot, live, m->d_pub, seq);
+    count_launch();
+    GB_CK(cudaGetLastError());
+    volatile int64_t *vp = m->h_pub;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (long spins = 0; vp[16] != seq; ++spins) {
+        if ((spins & 1023) == 1023) {
+            if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(5)) {
+                GB_CK(cudaStreamSynchronize(st));
+                if (vp[16] != seq) {
+                    set_error("bfs_run_batch: the layer counters never arrived");
+                    return BFS_ERR_CUDA;
+                }
+                break;
+            }
+            if (spins > (1 << 16)) std::this_thread::yield();
+        }
+    }
+    std::atomic_thread_fence(std::memory_order_acquire);
+    for (int i = 0; i < 16; ++i) m->h_slot[i] = vp[i];
     return BFS_OK;
 }
 
@@ -1072,8 +1127,10 @@ bfs_status run_batch_w(bfs_graph *g, const int32_t *roots, int k, int8_t *levels
     GB_CK(cudaMemsetAsync(m->trace, 0, (size_t)kMsRing * kMsFields * 8, st));
     GB_LAUNCH(ms_roots_kernel<W>, 1, kMaxRoots, 0, st, roots, k, n, n - g->deg0, g->nnz, g->off,
               act, seen, m->fr, m->live, m->trace);
-    GB_CK(cudaMemcpyAsync(m->h_slot, m->trace, kMsFields * 8, cudaMemcpyDeviceToHost, st));
-    GB_CK(cudaStreamSynchronize(st));
+    {
+        const bfs_status ps = ms_publish_and_wait(m, m->trace, m->live, st);
+        if (ps != BFS_OK) return ps;
+    }
     int64_t v_f = m->h_slot[M_NV], e_f = m->h_slot[M_MF], pairs = k;
     int64_t v_u = m->h_slot[M_LACKN], e_u = m->h_slot[M_LACKDEG];
     m->last.clear();
@@ -1139,9 +1196,10 @@ bfs_status run_batch_w(bfs_graph *g, const int32_t *roots, int k, int8_t *levels
                       slot_zero, live_next, live_zero);
         }
         if (timing) GB_CK(cudaEventRecord(event(2 * d + 1), st));
-        GB_CK(cudaMemcpyAsync(m->h_slot, slot_next, kMsFields * 8, cudaMemcpyDeviceToHost, st));
-        GB_CK(cudaMemcpyAsync(m->h_slot + 8, live_next, 8 * 8, cudaMemcpyDeviceToHost, st));
-        GB_CK(cudaStreamSynchronize(st));
+        {
+            const bfs_status ps = ms_publish_and_wait(m, slot_next, live_next, st);
+            if (ps != BFS_OK) return ps;
+        }
         m->last.push_back(ls);
         v_f = m->h_slot[M_NV];
         e_f = m->h_slot[M_MF];
