@@ -404,6 +404,11 @@ BFS_API bfs_status bfs_serve_submit(bfs_server *s, int32_t graph_id, int32_t roo
 BFS_API bfs_status bfs_serve_wait(bfs_server *s, uint64_t ticket, int64_t timeout_us,
                                   bfs_status *result);
 BFS_API bfs_status bfs_serve_stats_get(bfs_server *s, bfs_serve_stats *out);
+/* Starts the statistics afresh (counts, latencies, the queries/s window);
+ * requests in flight are counted when they complete. Graph views and their
+ * traversal state stay allocated, so a long-running server can report one
+ * interval at a time without paying their creation again. */
+BFS_API bfs_status bfs_serve_stats_reset(bfs_server *s);
 /* Stops accepting requests, drains or cancels the queue (cfg), finishes the
  * batches in flight, joins the workers and frees the server. NULL is fine. */
 BFS_API bfs_status bfs_serve_destroy(bfs_server *s);

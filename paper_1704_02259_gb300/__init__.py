@@ -114,6 +114,7 @@ SIGNATURES = {
     "bfs_serve_submit": (I32, [P, I32, I32, P, P]),
     "bfs_serve_wait": (I32, [P, U64, I64, P]),
     "bfs_serve_stats_get": (I32, [P, P]),
+    "bfs_serve_stats_reset": (I32, [P]),
     "bfs_serve_destroy": (I32, [P]),
 }
 
@@ -370,6 +371,9 @@ class Server:
         o = ServeStats()
         _check(lib().bfs_serve_stats_get(self._h, ctypes.byref(o)))
         return {f: getattr(o, f) for f, _ in ServeStats._fields_}
+
+    def reset_stats(self):
+        _check(lib().bfs_serve_stats_reset(self._h))
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

@@ -403,6 +403,19 @@ extern "C" BFS_API bfs_status bfs_serve_stats_get(bfs_server *s, bfs_serve_stats
     return BFS_OK;
 }
 
+extern "C" BFS_API bfs_status bfs_serve_stats_reset(bfs_server *s) {
+    clear_error();
+    if (!s) {
+        set_error("bfs_serve_stats_reset: null server");
+        return BFS_ERR_INVALID;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->lat_us.clear();
+    s->completed = s->failed = s->batches = s->deferred = s->roots_launched = 0;
+    s->any_submit = false;
+    return BFS_OK;
+}
+
 extern "C" BFS_API bfs_status bfs_serve_destroy(bfs_server *s) {
     clear_error();
     if (!s) return BFS_OK;

@@ -104,6 +104,24 @@ def test_poisson_stream_reports_latency(graphs):
     srv.close()
 
 
+def test_stats_reset_starts_a_new_interval(graphs):
+    srv, ids = server_with(graphs[:2], workers=2)
+    n = graphs[0][0]
+    outs = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in range(20)]
+    for i, out in enumerate(outs):
+        assert srv.wait(srv.submit(ids[0], i, out)) == 0
+    assert srv.stats()["completed"] == 20
+    srv.reset_stats()
+    st = srv.stats()
+    assert st["completed"] == 0 and st["batches"] == 0 and st["p99_us"] == 0
+    for i, out in enumerate(outs[:5]):
+        assert srv.wait(srv.submit(ids[0], 40 + i, out)) == 0
+        assert np.array_equal(out.cpu().numpy(), expected(graphs, 0, 40 + i))
+    st = srv.stats()
+    assert st["completed"] == 5 and st["p50_us"] > 0 and st["qps"] > 0
+    srv.close()
+
+
 def test_memory_admission_splits_and_defers(graphs):
     n = graphs[1][0]
     # room for a few rows but not for a 256-root batch with its lane state
