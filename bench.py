@@ -555,7 +555,8 @@ def main():
                    "edgefactor": ef, "n": n, "nnz": nnz, "roots": len(roots),
                    "graph_seed": args.graph_seed, "root_seed": args.root_seed,
                    "l2": "inputs larger than L2 (CSR of scale 26 is ~8 GB)",
-                   "policy": "edge alpha=14 beta=24", "bu_probe": cfg.bu_probe},
+                   "policy": f"edge alpha={cfg.alpha:g} beta={cfg.beta:g}",
+                   "bu_probe": cfg.bu_probe},
         "roofline": {"bound": "hbm", "kernel": "bu_hub_kernel", "achieved": achieved,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": measured_traffic(scale, ef),

@@ -186,7 +186,8 @@ typedef struct bfs_config {
     int32_t reserved[2];
 } bfs_config;
 
-/* Fills `cfg` with the defaults (edge policy, alpha 14, beta 24, ...). */
+/* Fills `cfg` with the defaults (edge policy, alpha 20, beta 200, hub head
+ * records, bitmap claims, device loop up to 2^25 vertices, ...). */
 BFS_API void bfs_config_default(bfs_config *cfg);
 
 #define BFS_DEVICE_PTRS 1u  /* offsets / indices are device pointers           */

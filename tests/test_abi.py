@@ -42,7 +42,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_config_defaults(lib):
     c = gb.default_config()
-    assert c.policy == gb.POLICY_EDGE and c.alpha == 14.0 and c.beta == 24.0
+    assert c.policy == gb.POLICY_EDGE and c.alpha == 20.0 and c.beta == 200.0
     assert 1 <= c.bu_probe <= 64 and c.td_warp_degree <= c.td_grid_degree
 
 

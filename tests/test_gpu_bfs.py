@@ -15,8 +15,11 @@ from tests.gpu_common import both_csr, config, run_gpu
 pytestmark = pytest.mark.gpu
 
 
-def check_run(o_off, o_idx, graph, root, policy=None, forced=None, alpha=14.0, beta=24.0):
-    """Runs the GPU BFS and compares it with the oracle's Alg. 3 run."""
+def check_run(o_off, o_idx, graph, root, policy=None, forced=None, alpha=None, beta=None):
+    """Runs the GPU BFS and compares it with the oracle's Alg. 3 run (under the
+    graph's own switch thresholds unless given)."""
+    alpha = graph.config.alpha if alpha is None else alpha
+    beta = graph.config.beta if beta is None else beta
     lv, pa = run_gpu(graph, root)
     ref, _ = oracle.bfs(o_off, o_idx, root)
     assert np.array_equal(lv, ref), "levels differ from the oracle"
