@@ -518,21 +518,28 @@ def main():
     else:
         value, total_s = my_hmean, my_total_s
 
-    # end to end through the public API with host buffers: the results of
-    # every root are copied back to pinned host memory inside the timed region
-    lv_h = torch.empty(n, dtype=torch.int32).pin_memory()
-    pa_h = torch.empty(n, dtype=torch.int32).pin_memory()
+    # end to end through the public API with host buffers: every root's level
+    # and parent arrays are copied back to pinned host memory inside the timed
+    # region (host_async: a root's copy overlaps the next root's traversal;
+    # the step ends when the last copy has landed)
+    bufs = [(torch.empty(n, dtype=torch.int32).pin_memory(),
+             torch.empty(n, dtype=torch.int32).pin_memory()) for _ in range(2)]
     cfg.timing = 0
+    cfg.host_async = 1
     g.set_config(cfg)
+    for i, r in enumerate(roots[:4]):       # untimed: allocate the output pairs
+        g.run(r, *bufs[i % 2])
+    g.sync()
     barrier()
-    e2e_teps = []
-    for r in roots:
-        t1 = time.perf_counter()
-        g.run(r, lv_h, pa_h)
-        dt = time.perf_counter() - t1
-        e2e_teps.append(g.stats().component_edges / dt)
+    e2e_edges = 0
+    t1 = time.perf_counter()
+    for i, r in enumerate(roots):
+        g.run(r, *bufs[i % 2])
+        e2e_edges += g.stats().component_edges
+    g.sync()
+    dt = time.perf_counter() - t1
     barrier()
-    e2e_val = hmean(e2e_teps)
+    e2e_val = e2e_edges / dt
     if dist is not None:
         e2e_val = float(gather_ranks(dist, world, [e2e_val], "cuda")[:, 0].sum())
 

@@ -183,7 +183,16 @@ typedef struct bfs_config {
                                 recorded); 0 = host loop; 2 (default) = the
                                 device loop for n <= 2^25, where the host round
                                 trips weigh most, the host loop above         */
-    int32_t reserved[2];
+    int32_t host_async;      /* with host output buffers: 1 = bfs_run returns
+                                once the traversal is done and the copy of its
+                                results to the host runs on the graph's own
+                                copy stream, overlapping the next traversal;
+                                the buffers are complete after bfs_graph_sync
+                                (two calls' copies may be in flight; the
+                                outputs of a call must stay untouched until
+                                then). 0 (default) = bfs_run returns with the
+                                copy done                                      */
+    int32_t reserved[1];
 } bfs_config;
 
 /* Fills `cfg` with the defaults (edge policy, alpha 20, beta 200, hub head
@@ -227,6 +236,10 @@ BFS_API bfs_status bfs_graph_destroy(bfs_graph *g);
  * layer are the first frontier neighbour in CSR order (Alg. 2); parents found
  * by a top-down layer are whichever frontier neighbour claimed the vertex
  * first (any valid tree, Sec. 7.1). */
+/* Waits for the host copies that bfs_run left in flight (cfg.host_async) and
+ * returns the first error among them; BFS_OK when none is pending. */
+BFS_API bfs_status bfs_graph_sync(bfs_graph *g);
+
 BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level_out, int32_t *parent_out,
                            void *stream);
 

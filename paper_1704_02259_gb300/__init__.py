@@ -43,7 +43,8 @@ class Config(ctypes.Structure):
                 ("timing", ctypes.c_int32), ("bu_words", ctypes.c_int32),
                 ("td_claim", ctypes.c_int32), ("bu_head", ctypes.c_int32),
                 ("prune_components", ctypes.c_int32), ("bu_list_percent", ctypes.c_int32),
-                ("device_loop", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("device_loop", ctypes.c_int32), ("host_async", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 class LayerStats(ctypes.Structure):
@@ -99,6 +100,7 @@ SIGNATURES = {
     "bfs_graph_info": (I32, [P, P, P, P, P]),
     "bfs_graph_destroy": (I32, [P]),
     "bfs_run": (I32, [P, I32, P, P, P]),
+    "bfs_graph_sync": (I32, [P]),
     "bfs_last_run_stats": (I32, [P, P, I32, P, P]),
     "bfs_run_noalloc": (I32, [P, P, I64, I64, I32, P, P, P]),
     "bfs_batch_config_default": (None, [P]),
@@ -260,6 +262,10 @@ class Graph:
             parent = torch.empty(self.n, dtype=torch.int32, device=level.device)
         _check(lib().bfs_run(self._h, int(root), _ptr(level), _ptr(parent), _stream(stream)))
         return level, parent
+
+    def sync(self):
+        """Waits for host copies left in flight by run() with config.host_async."""
+        _check(lib().bfs_graph_sync(self._h))
 
     def stats(self) -> RunStats:
         L = ctypes.c_int32(0)

@@ -1148,6 +1148,7 @@ bool config_ok(const bfs_config &c) {
     if (c.bu_words != 1 && c.bu_words != 2 && c.bu_words != 4) return false;
     if (c.td_claim != 0 && c.td_claim != 1) return false;
     if (c.bu_head < 0 || c.bu_head > 2) return false;
+    if (c.host_async != 0 && c.host_async != 1) return false;
     if (c.prune_components != 0 && c.prune_components != 1) return false;
     if (c.bu_list_percent < 0 || c.bu_list_percent > 100) return false;
     if (c.device_loop < 0 || c.device_loop > 2) return false;
@@ -1471,6 +1472,14 @@ void free_graph(bfs_graph *g) {
     cudaFree(g->big);
     cudaFree(g->parent_scratch);
     cudaFree(g->level_scratch);
+    if (g->copy_st) cudaStreamSynchronize(g->copy_st);
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(g->hout_level[i]);
+        cudaFree(g->hout_parent[i]);
+        if (g->hout_done[i]) cudaEventDestroy(g->hout_done[i]);
+    }
+    if (g->hout_ready) cudaEventDestroy(g->hout_ready);
+    if (g->copy_st) cudaStreamDestroy(g->copy_st);
     cudaFree(g->trace);
     if (g->h_slot) cudaFreeHost(g->h_slot);
     if (g->h_pub) cudaFreeHost(g->h_pub);
@@ -1716,7 +1725,26 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
         return BFS_ERR_INVALID;
     }
     int32_t *level = level_out, *parent = parent_out;
-    if (host_out) {
+    const bool async_out = host_out && g->cfg.host_async;
+    int slot = 0;
+    if (async_out) {
+        // device outputs used in turn: pair `slot` was last copied two calls ago
+        slot = g->hout_turn;
+        g->hout_turn ^= 1;
+        if (!g->copy_st) {
+            GB_CK(cudaStreamCreateWithFlags(&g->copy_st, cudaStreamNonBlocking));
+            GB_CK(cudaEventCreateWithFlags(&g->hout_ready, cudaEventDisableTiming));
+            for (int i = 0; i < 2; ++i)
+                GB_CK(cudaEventCreateWithFlags(&g->hout_done[i], cudaEventDisableTiming));
+        }
+        if (!g->hout_level[slot]) {
+            GB_CK(cudaMalloc(&g->hout_level[slot], (size_t)n * 4));
+            GB_CK(cudaMalloc(&g->hout_parent[slot], (size_t)n * 4));
+        }
+        GB_CK(cudaEventSynchronize(g->hout_done[slot]));
+        level = g->hout_level[slot];
+        parent = g->hout_parent[slot];
+    } else if (host_out) {
         if (!g->level_scratch) GB_CK(cudaMalloc(&g->level_scratch, (size_t)n * 4));
         level = g->level_scratch;
         parent = nullptr;
@@ -1961,12 +1989,32 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
             }
         }
     }
-    if (host_out) {
+    if (async_out) {
+        // the copy stream takes the results after the traversal; the next
+        // traversal (other output pair) overlaps it
+        GB_CK(cudaEventRecord(g->hout_ready, st));
+        GB_CK(cudaStreamWaitEvent(g->copy_st, g->hout_ready, 0));
+        GB_CK(cudaMemcpyAsync(level_out, level, (size_t)n * 4, cudaMemcpyDeviceToHost, g->copy_st));
+        if (parent_out)
+            GB_CK(cudaMemcpyAsync(parent_out, parent, (size_t)n * 4, cudaMemcpyDeviceToHost,
+                                  g->copy_st));
+        GB_CK(cudaEventRecord(g->hout_done[slot], g->copy_st));
+    } else if (host_out) {
         GB_CK(cudaMemcpyAsync(level_out, level, (size_t)n * 4, cudaMemcpyDeviceToHost, st));
         if (parent_out)
             GB_CK(cudaMemcpyAsync(parent_out, parent, (size_t)n * 4, cudaMemcpyDeviceToHost, st));
         GB_CK(cudaStreamSynchronize(st));
     }
+    return BFS_OK;
+}
+
+extern "C" BFS_API bfs_status bfs_graph_sync(bfs_graph *g) {
+    clear_error();
+    if (!g) {
+        set_error("bfs_graph_sync: null graph");
+        return BFS_ERR_INVALID;
+    }
+    if (g->copy_st) GB_CK(cudaStreamSynchronize(g->copy_st));
     return BFS_OK;
 }
 

@@ -40,6 +40,12 @@ struct bfs_graph {
                                    // degree-0 vertices and ids past n
     int32_t *q_a = nullptr, *q_b = nullptr, *big = nullptr;
     int32_t *parent_scratch = nullptr, *level_scratch = nullptr;
+    // host_async: two device output pairs used in turn, copied to the host on
+    // copy_st; hout_done[i] marks the end of pair i's copy
+    int32_t *hout_level[2] = {nullptr, nullptr}, *hout_parent[2] = {nullptr, nullptr};
+    cudaEvent_t hout_done[2] = {nullptr, nullptr}, hout_ready = nullptr;
+    cudaStream_t copy_st = nullptr;
+    int hout_turn = 0;
     int64_t *trace = nullptr;
     int64_t *h_slot = nullptr;  // pinned, kFields entries
     // mapped pinned block the host loop polls: kFields counters then a

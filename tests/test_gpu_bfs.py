@@ -253,6 +253,25 @@ def test_host_output_buffers_match_device():
     assert oracle.check_parents(o_off, o_idx, r, lv_h.numpy(), pa_h.numpy()) == 0
 
 
+@pytest.mark.parametrize("loop", [0, 1])
+def test_host_async_outputs(loop):
+    # host_async: each run returns once its traversal is done; the copies of
+    # two runs may still be in flight and all land by sync()
+    n, o_off, o_idx, g_off, g_idx = _rmat_both(14, 16, 1)
+    g = gb.Graph(g_off, g_idx, config(host_async=1, device_loop=loop))
+    roots = [int(r) for r in oracle.sample_roots(o_off, n, 3, 7)]
+    bufs = [(torch.full((n,), 55, dtype=torch.int32).pin_memory(),
+             torch.full((n,), 55, dtype=torch.int32).pin_memory()) for _ in roots]
+    for r, (lv, pa) in zip(roots, bufs):
+        g.run(r, lv, pa)
+    g.sync()
+    for r, (lv, pa) in zip(roots, bufs):
+        ref, _ = oracle.bfs(o_off, o_idx, r)
+        assert np.array_equal(lv.numpy(), ref)
+        assert oracle.check_parents(o_off, o_idx, r, lv.numpy(), pa.numpy()) == 0
+    g.sync()                                # nothing pending: returns at once
+
+
 def test_run_rejects_bad_root():
     o_off, o_idx, g = make(10, *inputs.path_edges(10))
     with pytest.raises(gb.BfsError):
