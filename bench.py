@@ -485,18 +485,25 @@ def main():
     # launch over its own CUDA-event duration. Per launch: the visited words
     # read, the next / pend / visited words written (n/2 bytes together), one
     # 8-byte head record per probed vertex (unvisited, degree >= 1) and the
-    # parent and level of each vertex its hub finds (8 bytes).
+    # parent and level of each vertex its hub finds (8 bytes); the first
+    # sweep of a traversal (which, with bitmap claims, also writes the -1
+    # outputs) writes parent and level of every vertex not reached before it
+    # (8 bytes each).
     hub_bytes = hub_ms = 0.0
     scan_ms = 0.0
     bl_bytes = bl_ms = 0.0
     bu1_bytes = bu1_ms = 0.0
     td_bytes = td_ms = 0.0
     n_hub = n_bl = n_bu1 = 0
+    fills_outputs = cfg.td_claim == 1 and not cfg.prune_components
     for _, _, st in recs:
+        first_sweep = fills_outputs
         for L in st.layers:
             active = L["n_u"] - (n - deg1)  # unvisited vertices of degree >= 1
             if L["direction"] == 1 and L["converted"] == 3:
-                hub_bytes += n / 2 + 8 * active + 8 * L["hub_found"]
+                written = L["n_u"] if first_sweep else L["hub_found"]
+                first_sweep = False
+                hub_bytes += n / 2 + 8 * active + 8 * written
                 hub_ms += L["ms_sweep"]
                 scan_ms += L["ms_main"] - L["ms_sweep"]
                 n_hub += 1
