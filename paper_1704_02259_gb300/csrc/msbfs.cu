@@ -442,27 +442,24 @@ __device__ __forceinline__ void ms_compact_phase(
     }
 }
 
-// OR the frontier words `cu` of u into neighbour v's next words, only the
-// bits v has not seen.
-template <int W, bool CO>
+// OR the frontier words `cu` of u into neighbour v's next words. The OR's
+// old value is not used (the GPU does not wait on it), and no load of v's
+// seen words filters it first: one random read per edge cost more than the
+// ORs it saved; the keep-unseen pass masks seen bits out afterwards.
+template <int W>
 __device__ __forceinline__ void ms_push(const unsigned long long (&cu)[W], int64_t v,
-                                        const unsigned long long *__restrict__ seen,
                                         unsigned long long *__restrict__ nxt) {
-    unsigned long long sv[W];
-    load_lanes<W, CO>(seen + v * W, sv);
 #pragma unroll
-    for (int i = 0; i < W; ++i) {
-        const unsigned long long add = cu[i] & ~sv[i];
-        if (add) atomicOr(nxt + v * W + i, add);
-    }
+    for (int i = 0; i < W; ++i)
+        if (cu[i]) atomicOr(nxt + v * W + i, cu[i]);
 }
 
 // Top-down layer on bit lanes over the compacted list.
 //   W = 1: a warp takes 32 entries; rows shorter than 32 are walked by their
 //     own lane, longer ones by the whole warp.
 //   W > 1: a group of W lanes (lane i = lane word i) takes one entry, so a
-//     pushed edge is one broadcast index load, one coalesced 8W-byte load of
-//     the neighbour's seen words and at most one atomicOr per lane; the
+//     pushed edge is one broadcast index load and at most one atomicOr per
+//     lane (none for a zero frontier word); the
 //     32 / W groups of a warp take consecutive entries, 4 edges in flight;
 //     rows of 32 or more edges are walked by the whole warp, group g on
 //     edges g, g + 32 / W, ...
@@ -492,17 +489,11 @@ __device__ __forceinline__ void ms_td_phase(
             if (end - beg < 32) {
                 for (int64_t e = beg; e < end; e += 4) {
                     int64_t v[4];
-                    unsigned long long sv[4];
 #pragma unroll
                     for (int t = 0; t < 4; ++t) v[t] = e + t < end ? (int64_t)__ldg(idx + e + t) : -1;
 #pragma unroll
                     for (int t = 0; t < 4; ++t)
-                        sv[t] = v[t] >= 0 ? ld<CO>(seen + v[t] * W + wi) : ~0ull;
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        const unsigned long long add = cu & ~sv[t];
-                        if (add) atomicOr(nxt + v[t] * W + wi, add);
-                    }
+                        if (v[t] >= 0 && cu) atomicOr(nxt + v[t] * W + wi, cu);
                 }
             }
             // rows of 32 or more: the whole warp, one row at a time
@@ -515,7 +506,6 @@ __device__ __forceinline__ void ms_td_phase(
                 const unsigned long long cL = __shfl_sync(0xffffffffu, cu, L + wi);
                 for (int64_t e0 = lb + gid; e0 < le; e0 += 4 * G) {
                     int64_t v[4];
-                    unsigned long long sv[4];
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
                         const int64_t e = e0 + (int64_t)t * G;
@@ -523,12 +513,7 @@ __device__ __forceinline__ void ms_td_phase(
                     }
 #pragma unroll
                     for (int t = 0; t < 4; ++t)
-                        sv[t] = v[t] >= 0 ? ld<CO>(seen + v[t] * W + wi) : ~0ull;
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        const unsigned long long add = cL & ~sv[t];
-                        if (add) atomicOr(nxt + v[t] * W + wi, add);
-                    }
+                        if (v[t] >= 0 && cL) atomicOr(nxt + v[t] * W + wi, cL);
                 }
             }
         }
@@ -555,7 +540,7 @@ __device__ __forceinline__ void ms_td_phase(
                 for (int t = 0; t < 4; ++t) v[t] = e + t < end ? (int64_t)__ldg(idx + e + t) : -1;
 #pragma unroll
                 for (int t = 0; t < 4; ++t)
-                    if (v[t] >= 0) ms_push<W, CO>(cu, v[t], seen, nxt);
+                    if (v[t] >= 0) ms_push<W>(cu, v[t], nxt);
             }
         }
         unsigned wm = __ballot_sync(0xffffffffu, wide);
@@ -567,7 +552,7 @@ __device__ __forceinline__ void ms_td_phase(
             unsigned long long cL[W];
 #pragma unroll
             for (int j = 0; j < W; ++j) cL[j] = __shfl_sync(0xffffffffu, cu[j], L);
-            for (int64_t e = lb + lane; e < le; e += 32) ms_push<W, CO>(cL, __ldg(idx + e), seen, nxt);
+            for (int64_t e = lb + lane; e < le; e += 32) ms_push<W>(cL, __ldg(idx + e), nxt);
         }
     }
 }
@@ -634,7 +619,7 @@ __device__ __forceinline__ void ms_td_big_phase(
             }
             unsigned long long cu[W];
             load_lanes<W, CO>(cur + (int64_t)u_s[lo] * W, cu);
-            ms_push<W, CO>(cu, __ldg(idx + beg_s[lo] + (g - pre[lo])), seen, nxt);
+            ms_push<W>(cu, __ldg(idx + beg_s[lo] + (g - pre[lo])), nxt);
         }
         __syncthreads();
     }
