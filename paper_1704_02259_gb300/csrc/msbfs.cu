@@ -467,8 +467,7 @@ template <int W, bool CO>
 __device__ __forceinline__ void ms_td_phase(
     const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
     const int32_t *__restrict__ list, const unsigned long long *slot_cur,
-    const unsigned long long *__restrict__ cur, const unsigned long long *__restrict__ seen,
-    unsigned long long *__restrict__ nxt) {
+    const unsigned long long *__restrict__ cur, unsigned long long *__restrict__ nxt) {
     const int64_t cnt = (int64_t)ld<CO>(slot_cur + M_LIST);
     const unsigned lane = lane_id();
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -563,8 +562,7 @@ template <int W, bool CO>
 __device__ __forceinline__ void ms_td_big_phase(
     const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
     const int32_t *__restrict__ big, const unsigned long long *slot_cur,
-    const unsigned long long *__restrict__ cur, const unsigned long long *__restrict__ seen,
-    unsigned long long *__restrict__ nxt) {
+    const unsigned long long *__restrict__ cur, unsigned long long *__restrict__ nxt) {
     __shared__ long long pre[kMsBigBatch + 1];
     __shared__ long long beg_s[kMsBigBatch];
     __shared__ int32_t u_s[kMsBigBatch];
@@ -809,15 +807,15 @@ __global__ void __launch_bounds__(kMsBlock) ms_compact_kernel(
 template <int W>
 __global__ void __launch_bounds__(kMsBlock) ms_td_kernel(
     const int64_t *off, const int32_t *idx, const int32_t *list, const unsigned long long *slot_cur,
-    const unsigned long long *cur, const unsigned long long *seen, unsigned long long *nxt) {
-    ms_td_phase<W, false>(off, idx, list, slot_cur, cur, seen, nxt);
+    const unsigned long long *cur, unsigned long long *nxt) {
+    ms_td_phase<W, false>(off, idx, list, slot_cur, cur, nxt);
 }
 
 template <int W>
 __global__ void __launch_bounds__(kMsBlock) ms_td_big_kernel(
     const int64_t *off, const int32_t *idx, const int32_t *big, const unsigned long long *slot_cur,
-    const unsigned long long *cur, const unsigned long long *seen, unsigned long long *nxt) {
-    ms_td_big_phase<W, false>(off, idx, big, slot_cur, cur, seen, nxt);
+    const unsigned long long *cur, unsigned long long *nxt) {
+    ms_td_big_phase<W, false>(off, idx, big, slot_cur, cur, nxt);
 }
 
 template <int W>
@@ -925,10 +923,8 @@ __global__ void __launch_bounds__(kMsBlock) ms_persistent_kernel(MsPersist p) {
                 status = BFS_ERR_TIMEOUT;
                 break;
             }
-            ms_td_phase<W, true>(p.off, p.idx, p.list, (const unsigned long long *)sc, cur, p.seen,
-                                 nxt);
-            ms_td_big_phase<W, true>(p.off, p.idx, p.big, (const unsigned long long *)sc, cur,
-                                     p.seen, nxt);
+            ms_td_phase<W, true>(p.off, p.idx, p.list, (const unsigned long long *)sc, cur, nxt);
+            ms_td_big_phase<W, true>(p.off, p.idx, p.big, (const unsigned long long *)sc, cur, nxt);
             if (!grid_barrier(p.bar, p.err, expected, p.timeout_ns)) {
                 status = BFS_ERR_TIMEOUT;
                 break;
@@ -1169,13 +1165,13 @@ bfs_status run_batch_w(bfs_graph *g, const int32_t *roots, int k, int8_t *levels
                       g->off, big_deg, m->list, m->big, (unsigned long long *)slot_cur);
             GB_CK(cudaMemsetAsync(nxt, 0, (size_t)slot_words * 8, st));
             GB_LAUNCH(ms_td_kernel<W>, grid_cap(v_f, kMsBlock, td_occ), kMsBlock, 0, st, g->off,
-                      g->idx, m->list, (const unsigned long long *)slot_cur, cur, seen, nxt);
+                      g->idx, m->list, (const unsigned long long *)slot_cur, cur, nxt);
             if (e_f >= big_deg)
                 GB_LAUNCH(ms_td_big_kernel<W>,
                           (int)std::max<int64_t>(1, std::min<int64_t>(e_f / 2048 + 1,
                                                                       (int64_t)sm_count() * 4)),
                           kMsBlock, 0, st, g->off, g->idx, m->big,
-                          (const unsigned long long *)slot_cur, cur, seen, nxt);
+                          (const unsigned long long *)slot_cur, cur, nxt);
             GB_LAUNCH(ms_finalize_kernel<W>, grid_cap(n, kMsBlock, 8), kMsBlock, 0, st, g->off,
                       g->base_vis, n, act, seen, nxt, e_f, (unsigned long long *)slot_next,
                       slot_zero, live_next, live_zero);
