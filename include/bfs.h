@@ -192,7 +192,14 @@ typedef struct bfs_config {
                                 outputs of a call must stay untouched until
                                 then). 0 (default) = bfs_run returns with the
                                 copy done                                      */
-    int32_t reserved[1];
+    int32_t parent_min;      /* 1 = after the traversal each reached vertex's
+                                parent becomes its smallest-id neighbour one
+                                level up: one deterministic tree among the
+                                valid ones (Sec. 7.1), the same on every run
+                                and equal to a sequential reference's.
+                                Costs a bottom-up-like pass over the reached
+                                vertices' rows (early exit when every row is
+                                sorted ascending, which is checked once)      */
 } bfs_config;
 
 /* Fills `cfg` with the defaults (edge policy, alpha 20, beta 200, hub head

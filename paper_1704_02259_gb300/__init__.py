@@ -44,7 +44,7 @@ class Config(ctypes.Structure):
                 ("td_claim", ctypes.c_int32), ("bu_head", ctypes.c_int32),
                 ("prune_components", ctypes.c_int32), ("bu_list_percent", ctypes.c_int32),
                 ("device_loop", ctypes.c_int32), ("host_async", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 1)]
+                ("parent_min", ctypes.c_int32)]
 
 
 class LayerStats(ctypes.Structure):

@@ -190,6 +190,79 @@ __global__ void publish_kernel(const int64_t *__restrict__ slot, int64_t *pub, i
     }
 }
 
+// Clears *flag when some CSR row is not in ascending order (thread per row).
+__global__ void rows_sorted_kernel(const int64_t *__restrict__ off,
+                                   const int32_t *__restrict__ idx, int64_t n, int *flag) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += stride) {
+        const int64_t b = off[v], e = off[v + 1];
+        for (int64_t q = b + 1; q < e; ++q)
+            if (idx[q] < idx[q - 1]) {
+                atomicExch(flag, 0);
+                break;
+            }
+    }
+}
+
+// Smallest-id parent one level up for every reached vertex other than the
+// root (parent_min). A lane per vertex tests the first 8 row entries; longer
+// rows still open are finished by the whole warp, 32 entries per round. With
+// ascending rows the first neighbour at level - 1 is the smallest and ends the
+// scan; otherwise the whole row is scanned for the minimum.
+__global__ void __launch_bounds__(kBlock) min_parent_kernel(
+    const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
+    const int32_t *__restrict__ level, int32_t *__restrict__ parent, int64_t n, int32_t root,
+    int sorted) {
+    constexpr int P = 8;
+    const unsigned lane = lane_id();
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = gw; w < (n + 31) / 32; w += tw) {
+        const int64_t v = w * 32 + lane;
+        const int32_t lv = v < n ? level[v] : -1;
+        const bool active = v < n && v != root && lv > 0;
+        int64_t b = 0, e = 0;
+        if (active) {
+            b = off[v];
+            e = off[v + 1];
+        }
+        int32_t best = 0x7fffffff;
+        bool done = !active;
+        for (int q = 0; q < P && !done; ++q) {
+            if (b + q >= e) break;
+            const int32_t u = __ldg(idx + b + q);
+            if (__ldg(level + u) == lv - 1) {
+                best = u < best ? u : best;
+                if (sorted) done = true;
+            }
+        }
+        unsigned pend = __ballot_sync(0xffffffffu, !done && e - b > P);
+        while (pend) {
+            const int L = __ffs(pend) - 1;
+            pend &= pend - 1;
+            const int64_t lb = __shfl_sync(0xffffffffu, b, L) + P;
+            const int64_t le = __shfl_sync(0xffffffffu, e, L);
+            const int32_t want = __shfl_sync(0xffffffffu, lv, L) - 1;
+            int32_t bL = __shfl_sync(0xffffffffu, best, L);
+            for (int64_t q0 = lb; q0 < le; q0 += 32) {
+                const int64_t q = q0 + lane;
+                const int32_t u = q < le ? __ldg(idx + q) : 0x7fffffff;
+                const bool hit = q < le && __ldg(level + u) == want;
+                int32_t c = hit ? u : 0x7fffffff;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const int32_t y = __shfl_xor_sync(0xffffffffu, c, o);
+                    c = y < c ? y : c;
+                }
+                bL = c < bL ? c : bL;
+                if (sorted && __ballot_sync(0xffffffffu, hit)) break;
+            }
+            if ((int)lane == L) best = bL;
+        }
+        if (active) parent[v] = best;
+    }
+}
+
 // level = parent = -1 for every vertex not reached so far (not visited, or
 // visited only as a degree-0 vertex or id past n), the root excepted: the
 // outputs of a traversal that started without write_out and has had no
@@ -1149,6 +1222,7 @@ bool config_ok(const bfs_config &c) {
     if (c.td_claim != 0 && c.td_claim != 1) return false;
     if (c.bu_head < 0 || c.bu_head > 2) return false;
     if (c.host_async != 0 && c.host_async != 1) return false;
+    if (c.parent_min != 0 && c.parent_min != 1) return false;
     if (c.prune_components != 0 && c.prune_components != 1) return false;
     if (c.bu_list_percent < 0 || c.bu_list_percent > 100) return false;
     if (c.device_loop < 0 || c.device_loop > 2) return false;
@@ -1988,6 +2062,23 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                 g->last[d].ms_sweep = t2;
             }
         }
+    }
+    if (cfg.parent_min) {
+        if (g->rows_sorted < 0) {  // checked once per graph
+            int *flag = nullptr;
+            int h = 1;
+            GB_CK(cudaMallocAsync(&flag, 4, st));
+            GB_CK(cudaMemcpyAsync(flag, &h, 4, cudaMemcpyHostToDevice, st));
+            GB_LAUNCH(rows_sorted_kernel, grid_cap(n, kBlock, 8), kBlock, 0, st, g->off, g->idx, n,
+                      flag);
+            GB_CK(cudaMemcpyAsync(&h, flag, 4, cudaMemcpyDeviceToHost, st));
+            GB_CK(cudaFreeAsync(flag, st));
+            GB_CK(cudaStreamSynchronize(st));
+            g->rows_sorted = h;
+        }
+        GB_LAUNCH(min_parent_kernel, grid_cap(n, kBlock, 8), kBlock, 0, st, g->off, g->idx,
+                  level, parent, n, root, g->rows_sorted);
+        if (!host_out) GB_CK(cudaStreamSynchronize(st));
     }
     if (async_out) {
         // the copy stream takes the results after the traversal; the next

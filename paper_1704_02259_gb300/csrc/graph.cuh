@@ -30,6 +30,7 @@ struct bfs_graph {
     int32_t *idx_own = nullptr;
     uint32_t *visited = nullptr, *bm_a = nullptr, *bm_b = nullptr;
     uint32_t *pend = nullptr;      // vertices whose hub missed (two-pass bottom-up)
+    int rows_sorted = -1;          // every CSR row ascending: -1 not checked yet
     int bu_hub_blocks_per_sm = 0;
     int2 *head = nullptr;          // {first probe (-1 if none), degree}
     int head_kind = 0;             // what head holds: 1 first neighbour, 2 hub

@@ -325,3 +325,73 @@ def test_scale26_sampled_levels():
                 assert bool((nl == lv - 1).any())
                 p = parent[v].item()
                 assert level[p].item() == lv - 1 and bool((nb == p).any())
+
+
+def _reversed_rows(o_off, o_idx):
+    """The same graph with every CSR row in descending order."""
+    idx = o_idx.copy()
+    for v in range(len(o_off) - 1):
+        idx[o_off[v]:o_off[v + 1]] = idx[o_off[v]:o_off[v + 1]][::-1]
+    return idx
+
+
+@pytest.mark.parametrize("loop", [0, 1])
+@pytest.mark.parametrize("rows", ["sorted", "reversed"])
+def test_parent_min_matches_oracle(loop, rows):
+    # parent_min: every reached vertex's parent is its smallest neighbour one
+    # level up, whatever the direction of the layer that found it (Sec. 7.1
+    # allows any such tree; this one is unique), so parents compare exactly
+    n, o_off, o_idx, g_off, g_idx = _rmat_both(16, 16, 1)
+    if rows == "reversed":
+        o_idx = _reversed_rows(o_off, o_idx)
+        g_idx = torch.as_tensor(o_idx).cuda()
+    cases = [dict(), dict(forced=FORCED["alt"]), dict(forced=FORCED["td"]),
+             dict(bu_head=0, td_claim=0), dict(prune_components=1)]
+    roots = [int(r) for r in oracle.sample_roots(o_off, n, 2, 6)]
+    for c in cases:
+        g = gb.Graph(g_off, g_idx, config(parent_min=1, device_loop=loop, **c))
+        for r in roots:
+            lv, pa = run_gpu(g, r)
+            ref, _ = oracle.bfs(o_off, o_idx, r)
+            assert np.array_equal(lv, ref)
+            assert np.array_equal(pa, oracle.min_parent(o_off, o_idx, r, ref)), (c, r)
+
+
+@pytest.mark.parametrize("name", ["star", "grid", "hypercube", "complete", "union", "ragged"])
+def test_parent_min_closed_forms(name):
+    if name == "star":
+        n, (s, d) = 100, inputs.star_edges(100, centre=3)
+    elif name == "grid":
+        n, (s, d) = 15 * 17, inputs.grid_edges(15, 17)
+    elif name == "hypercube":
+        n, (s, d) = 256, inputs.hypercube_edges(8)
+    elif name == "complete":
+        n, (s, d) = 40, inputs.complete_edges(40)
+    elif name == "union":
+        n, s, d = inputs.union((30, *inputs.path_edges(30)), (9, *inputs.cycle_edges(9)),
+                               (5, [], []))
+    else:
+        n = 1000 + 13
+        s, d = inputs.powerlaw_edges(n, 6 * n, 5)
+    o_off, o_idx, g = make(n, s, d, parent_min=1)
+    for r in sorted({0, n // 2, n - 1}):
+        lv, pa = run_gpu(g, r)
+        ref, _ = oracle.bfs(o_off, o_idx, r)
+        assert np.array_equal(lv, ref)
+        assert np.array_equal(pa, oracle.min_parent(o_off, o_idx, r, ref))
+
+
+def test_parent_min_host_outputs():
+    n, o_off, o_idx, g_off, g_idx = _rmat_both(14, 16, 1)
+    roots = [int(r) for r in oracle.sample_roots(o_off, n, 3, 4)]
+    for extra in (dict(), dict(host_async=1)):
+        g = gb.Graph(g_off, g_idx, config(parent_min=1, **extra))
+        bufs = [(torch.full((n,), 55, dtype=torch.int32).pin_memory(),
+                 torch.full((n,), 55, dtype=torch.int32).pin_memory()) for _ in roots]
+        for r, (lv, pa) in zip(roots, bufs):
+            g.run(r, lv, pa)
+        g.sync()
+        for r, (lv, pa) in zip(roots, bufs):
+            ref, _ = oracle.bfs(o_off, o_idx, r)
+            assert np.array_equal(lv.numpy(), ref)
+            assert np.array_equal(pa.numpy(), oracle.min_parent(o_off, o_idx, r, ref))
