@@ -208,6 +208,32 @@ def cpu_baseline(args):
             "seconds": round(secs, 3)}
 
 
+def cpu_throughput(args):
+    """The oracle's throughput on all host cores, one independent root per
+    thread (the C BFS runs outside the interpreter lock): aggregate TEPS =
+    sum of component edges / wall time, the CPU comparison point for the
+    batched GPU runs. Same bounded sample graph as cpu_baseline."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    off, idx, _ = cpu_graph(args)
+    n = off.size - 1
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    roots = oracle.sample_roots(off, n, args.root_seed + 1, 2 * cores)
+
+    def one(r):
+        lv, _ = oracle.bfs(off, idx, int(r))
+        return oracle.component_edges(off, lv)
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(cores) as ex:
+        edges = sum(ex.map(one, roots))
+    dt = time.perf_counter() - t0
+    return {"value": edges / dt / 1e9, "unit": "GTEPS", "cores": cores, "kind": "oracle",
+            "sample": f"{len(roots)} independent roots, one per thread, on the cpu_baseline "
+                      f"graph (scale {args.cpu_scale}); aggregate edges / wall time",
+            "seconds": round(dt, 3)}
+
+
 def run_reference(args, rank, world):
     """--impl reference: the oracle, timed on the host cores (rank 0 only)."""
     if rank != 0:
@@ -231,6 +257,53 @@ def run_reference(args, rank, world):
             "e2e": {"value": val, "unit": "GTEPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+TABLE3_PAPER = [2879193, 30910, 34, 1.06, 2.51, 41.06]   # Table 3, per layer
+
+
+def table3_analogue(gb, torch, scale=18, ef=16, seed=1, root_seed=2):
+    """Table 3 on the GPU: every layer bottom-up from 64 roots at SCALE 18,
+    edgefactor 16; per layer, edges examined per newly visited vertex
+    (averaged over the roots that reach the layer) and the layer's device
+    time. Variants: the row scan with a per-lane probe of P entries before
+    the warp-cooperative tail (the paper's MAX_POS structure, P = 2, 8, 32),
+    and the hub probe first (this library's default bottom-up step)."""
+    n = 1 << scale
+    off, idx = gb.rmat_graph(scale, ef, seed)
+    roots = gb.sample_roots(off, n, root_seed, 64).tolist()
+    lv = torch.empty(n, dtype=torch.int32, device="cuda")
+    pa = torch.empty_like(lv)
+    out = {"workload": f"rmat-scale{scale}-ef{ef}-64roots, every layer bottom-up",
+           "paper_edges_per_visited": TABLE3_PAPER}
+    for name, head, probe in (("scan_p2", 0, 2), ("scan_p8", 0, 8), ("scan_p32", 0, 32),
+                              ("hub", 2, 8)):
+        cfg = gb.default_config()
+        cfg.policy = gb.POLICY_FORCED
+        cfg.forced_len = 1
+        cfg.forced[0] = 1
+        cfg.bu_head = head
+        cfg.bu_probe = probe
+        cfg.device_loop = 0
+        cfg.timing = 1
+        g = gb.Graph(off, idx, cfg)
+        for r in roots[:4]:
+            g.run(r, lv, pa)
+        ratio, ms = {}, {}
+        for r in roots:
+            g.run(r, lv, pa)
+            torch.cuda.synchronize()
+            layers = g.stats().layers
+            if sum(L["found"] for L in layers) < n // 100:
+                continue                    # root outside the large component
+            for d, L in enumerate(layers):
+                if L["found"] > 0:
+                    ratio.setdefault(d, []).append(L["examined"] / L["found"])
+                    ms.setdefault(d, []).append(L["ms_total"])
+        out[name] = {"edges_per_visited": [round(float(np.mean(ratio[d])), 2) for d in sorted(ratio)],
+                     "layer_ms": [round(float(np.mean(ms[d])), 4) for d in sorted(ms)]}
+        del g
+    return out
 
 
 def batched_comparison(gb, torch, scale, seed=1, root_seed=4, ks=(64, 128, 256, 512)):
@@ -596,8 +669,10 @@ def main():
     }
     if not args.no_batch and world == 1:
         line["batched"] = batched_comparison(gb, torch, args.batch_scale)
+        line["table3"] = table3_analogue(gb, torch)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args)
+        line["cpu_throughput"] = cpu_throughput(args)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -211,6 +211,14 @@ BFS_API void bfs_config_default(bfs_config *cfg);
                                must outlive the graph. Needs BFS_DEVICE_PTRS.  */
 #define BFS_VALIDATE 4u     /* check offsets[0]=0, monotone offsets,
                                offsets[n]=nnz and indices in [0, n)            */
+#define BFS_VALIDATE_SYMMETRIC 8u  /* also check, after the checks of
+                               BFS_VALIDATE (implied), that every row is
+                               strictly ascending and that every entry u of
+                               row v has its reverse entry v in row u: the
+                               bottom-up step reads a row as the vertex's
+                               in-edges, so it needs the undirected graph of
+                               Sec. 6.2 stored both ways. Costs a binary
+                               search per entry. Failure: BFS_ERR_INVALID  */
 
 /* Creates a graph from a symmetric CSR (layout above) and allocates its
  * per-traversal scratch: four n-bit bitmaps (visited, frontier, next, and

@@ -98,14 +98,23 @@ def relabel(x: int, scale: int, seed: int) -> int:
 
 def gen_edges(kind: int, scale: int, edgefactor: int, seed: int,
               a: float = 0.57, b: float = 0.19, c: float = 0.19,
-              first: int = 0, count: int | None = None):
-    """Edge list of the R-MAT (kind=RMAT) or uniform (kind=ER) generator."""
+              first: int = 0, count: int | None = None, out=None):
+    """Edge list of the R-MAT (kind=RMAT) or uniform (kind=ER) generator.
+    `out` = (src, dst): contiguous int32 arrays of at least `count` entries
+    to fill instead of new ones (lets a caller fill chunks of one list)."""
     m = edgefactor << scale
     if count is None:
         count = m - first
-    src = np.empty(max(count, 1), dtype=np.int32)
-    dst = np.empty(max(count, 1), dtype=np.int32)
-    _load().orc_gen_edges(kind, scale, seed, a, b, c, first, count, _p(src), _p(dst))
+    if out is None:
+        src = np.empty(max(count, 1), dtype=np.int32)
+        dst = np.empty(max(count, 1), dtype=np.int32)
+    else:
+        src, dst = out
+        if not (src.dtype == dst.dtype == np.int32 and src.flags.c_contiguous
+                and dst.flags.c_contiguous and min(src.size, dst.size) >= count):
+            raise ValueError("out: two contiguous int32 arrays of >= count entries")
+    if count > 0:
+        _load().orc_gen_edges(kind, scale, seed, a, b, c, first, count, _p(src), _p(dst))
     return src[:count], dst[:count]
 
 

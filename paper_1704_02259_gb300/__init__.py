@@ -27,6 +27,7 @@ POLICY_FORCED = 2
 DEVICE_PTRS = 1
 BORROW = 2
 VALIDATE = 4
+VALIDATE_SYMMETRIC = 8
 
 
 class BfsError(RuntimeError):
@@ -227,19 +228,23 @@ class Graph:
     """A CSR graph resident on the GPU (bfs_graph)."""
 
     def __init__(self, offsets: torch.Tensor, indices: torch.Tensor, config: Config | None = None,
-                 borrow: bool = True, validate: bool = False):
+                 borrow: bool = True, validate: bool | str = False):
+        """validate: True = range checks (BFS_VALIDATE); "symmetric" = also
+        ascending rows and every entry's reverse (BFS_VALIDATE_SYMMETRIC)."""
         n = offsets.numel() - 1
         nnz = indices.numel()
+        offsets = offsets.contiguous()
+        indices = indices.contiguous()
         flags = 0
         if offsets.is_cuda:
             flags |= DEVICE_PTRS
             if borrow:
                 flags |= BORROW
                 self._keep = (offsets, indices)
-        if validate:
+        if validate == "symmetric":
+            flags |= VALIDATE | VALIDATE_SYMMETRIC
+        elif validate:
             flags |= VALIDATE
-        offsets = offsets.contiguous()
-        indices = indices.contiguous()
         h = ctypes.c_void_p(0)
         _check(lib().bfs_graph_create(_ptr(offsets), _ptr(indices if nnz else None), n, nnz, flags,
                                       ctypes.byref(config) if config is not None else None,

@@ -1211,6 +1211,31 @@ __global__ void validate_kernel(const int64_t *__restrict__ off, const int32_t *
         if (idx[e] < 0 || idx[e] >= n) *bad = 1;
 }
 
+// Row-order and symmetry check (BFS_VALIDATE_SYMMETRIC), run only once the
+// offsets and indices passed validate_kernel: a warp per row; each entry u of
+// row v must exceed its predecessor and have v in row u (binary search).
+__global__ void symmetric_kernel(const int64_t *__restrict__ off,
+                                 const int32_t *__restrict__ idx, int64_t n, int *bad) {
+    const unsigned lane = lane_id();
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = gw; v < n; v += tw) {
+        const int64_t b = off[v], e = off[v + 1];
+        bool ok = true;
+        for (int64_t q = b + lane; q < e; q += 32) {
+            const int32_t u = idx[q];
+            if (q > b && idx[q - 1] >= u) ok = false;
+            int64_t lo = off[u], hi = off[u + 1];
+            while (lo < hi) {
+                const int64_t mid = lo + ((hi - lo) >> 1);
+                if (idx[mid] < v) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo == off[u + 1] || idx[lo] != v) ok = false;
+        }
+        if (!ok) atomicExch(bad, 1);
+    }
+}
 
 bool config_ok(const bfs_config &c) {
     if (c.policy < 0 || c.policy > 2) return false;
@@ -1692,7 +1717,7 @@ extern "C" BFS_API bfs_status bfs_graph_create(const int64_t *offsets, const int
     GB_CKG(cudaHostAlloc((void **)&g->h_pub, (kFields + 1) * 8, cudaHostAllocMapped));
     GB_CKG(cudaHostGetDevicePointer((void **)&g->d_pub, g->h_pub, 0));
     g->h_pub[kFields] = 0;
-    if (flags & BFS_VALIDATE) {
+    if (flags & (BFS_VALIDATE | BFS_VALIDATE_SYMMETRIC)) {
         int *bad = nullptr, hbad = 0;
         GB_CKG(cudaMalloc(&bad, sizeof(int)));
         cudaMemset(bad, 0, sizeof(int));
@@ -1700,11 +1725,21 @@ extern "C" BFS_API bfs_status bfs_graph_create(const int64_t *offsets, const int
                                                                            bad);
         count_launch();
         cudaError_t e = cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && !hbad && (flags & BFS_VALIDATE_SYMMETRIC)) {
+            // the row bounds and indices it follows were checked above
+            symmetric_kernel<<<grid_cap(n * 32, kBlock, 8), kBlock>>>(g->off, g->idx, n, bad);
+            count_launch();
+            e = cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess && hbad) hbad = 2;
+        }
         cudaFree(bad);
         GB_CKG(e);
         if (hbad) {
             free_graph(g);
-            set_error("bfs_graph_create: CSR failed validation (offsets or indices out of range)");
+            set_error(hbad == 2 ? "bfs_graph_create: CSR failed validation (a row not strictly "
+                                  "ascending, or an entry without its reverse entry)"
+                                : "bfs_graph_create: CSR failed validation (offsets or indices "
+                                  "out of range)");
             return BFS_ERR_INVALID;
         }
     }

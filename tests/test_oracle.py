@@ -453,6 +453,38 @@ def test_policy_replays_table4():
     assert got == [r[1] for r in rows]
 
 
+def test_bottom_up_edges_per_visited_vertex_table3():
+    # Every layer bottom-up from 64 roots at SCALE 18, edgefactor 16: edges
+    # examined per newly visited vertex, averaged per layer over the roots
+    # that reach the layer. Our generator is not Graph500's bit for bit, so
+    # the values are compared in bands; the layer-4 value (about one edge:
+    # almost every vertex finds a parent at its first neighbour) is tight,
+    # so a scan that did not stop at the first frontier neighbour, or a
+    # count that missed the hit edge, fails it.
+    rows = read_rows("table3_bu_edges_per_visited_scale18_ef16.txt")
+    paper = {int(r[0]): float(r[1]) for r in rows}
+    n = 1 << 18
+    s, d = oracle.gen_edges(oracle.RMAT, 18, 16, 1)
+    off, idx = csr(n, s, d)
+    per = {}
+    for r in oracle.sample_roots(off, n, 2, 64):
+        lv, _, dirs, tr = oracle.hybrid_bfs(off, idx, int(r), oracle.POLICY_FORCED, 14, 24,
+                                            forced=[1])
+        if (lv >= 0).mean() < 0.01:
+            continue                       # root outside the large component
+        assert (dirs == 1).all()
+        for layer, row in enumerate(tr, start=1):
+            if row[5] > 0:
+                per.setdefault(layer, []).append(row[4] / row[5])
+    got = {k: float(np.mean(v)) for k, v in per.items()}
+    assert set(got) <= set(paper) | {7, 8} and {1, 2, 3, 4, 5} <= set(got)
+    band = {1: 2.0, 2: 2.0, 3: 4.0, 4: 1.2, 5: 2.0, 6: 3.0}
+    for layer, f in band.items():
+        if layer in got:
+            assert paper[layer] / f <= got[layer] <= paper[layer] * f, (layer, got[layer])
+    assert got[1] > got[2] > got[3] > got[4] < got[5]
+
+
 def test_policy_edge_form_thresholds():
     n = 960                       # n / beta = 40 exactly for beta = 24
     P = oracle.POLICY_EDGE
