@@ -2,7 +2,10 @@
 the oracle's single-source levels of that root (exact)."""
 from __future__ import annotations
 
+import hashlib
+import json
 import time
+from pathlib import Path
 
 import numpy as np
 import pytest
@@ -148,20 +151,56 @@ def test_batch_autotune_keeps_results_exact():
     check(g, o_off, o_idx, roots)
 
 
-def test_batch_scale22_sampled_lanes():
-    """The batched workload: R-MAT scale 22, 512 roots in one launch; 6
-    sampled lanes compared with the oracle's BFS of those roots."""
-    scale, k = 22, 512
-    n = 1 << scale
-    off, idx = gb.rmat_graph(scale, 16, 1)
-    s, d = oracle.gen_edges(oracle.RMAT, scale, 16, 1)
-    o_off, o_idx = oracle.build_csr(n, s, d)
-    del s, d
+GOLDEN22 = Path(__file__).parent / "golden" / "rmat22_ef16_seed1_batch.json"
+
+
+def _sha(t: torch.Tensor) -> str:
+    a = t.cpu().numpy()
+    return hashlib.sha256(np.ascontiguousarray(a, dtype=a.dtype.newbyteorder("<")).data).hexdigest()
+
+
+@pytest.fixture(scope="module")
+def rmat22():
+    """The batched workload: R-MAT SCALE 22, edgefactor 16, graph seed 1, 512
+    roots of seed 4, with digests of the oracle's level row of every root
+    (tests/golden/make_rmat22_batch.py)."""
+    gold = json.loads(GOLDEN22.read_text())
+    n = 1 << gold["scale"]
+    off, idx = gb.rmat_graph(gold["scale"], gold["edgefactor"], gold["graph_seed"])
     g = gb.Graph(off, idx)
-    roots = gb.sample_roots(off, n, 4, k)
-    lv = g.run_batch(roots)
+    roots = gb.sample_roots(off, n, gold["root_seed"], len(gold["rows"]))
+    yield gold, off, idx, g, roots
+    g.close()
+
+
+def test_batch_scale22_csr_and_roots_match_oracle_digests(rmat22):
+    gold, off, idx, g, roots = rmat22
+    assert idx.numel() == gold["nnz"]
+    assert _sha(off) == gold["offsets_sha256"] and _sha(idx) == gold["indices_sha256"]
+    assert roots.tolist() == [r["root"] for r in gold["rows"]]
+
+
+@pytest.mark.parametrize("k,tuned,use_graph", [(64, 1, 0), (128, 1, 0), (256, 1, 0), (512, 1, 0),
+                                               (512, 0, 0), (512, 0, 1), (300, 0, 1)])
+def test_batch_scale22_every_lane_exact(rmat22, k, tuned, use_graph):
+    # every lane of a k-root batch, in the benchmark's launch configuration
+    # (autotuned per k) and with the default configuration on either loop,
+    # against the oracle's level row of its root
+    gold, off, idx, g, roots = rmat22
+    n = off.numel() - 1
+    rk = roots[:k]
+    if tuned:
+        g.autotune_batch(rk)
+    else:
+        set_cfg(g, use_graph=use_graph)
+    levels = torch.full((k, n), 99, dtype=torch.int8, device="cuda")
+    g.run_batch(rk, levels)
     torch.cuda.synchronize()
-    rs = roots.cpu().numpy()
-    for i in [0, 1, 63, 64, 300, 511]:
-        ref, _ = oracle.bfs(o_off, o_idx, int(rs[i]))
-        assert np.array_equal(lv[i].cpu().numpy().astype(np.int32), ref)
+    a = levels.cpu().numpy()
+    bad = [i for i in range(k)
+           if hashlib.sha256(a[i].data).hexdigest() != gold["rows"][i]["int8_levels_sha256"]]
+    assert not bad, f"{len(bad)} lanes differ from the oracle, first {bad[:8]}"
+    reached = (levels >= 0).sum(dim=1).tolist()
+    assert reached == [r["reached"] for r in gold["rows"][:k]]
+
+
