@@ -3,8 +3,11 @@ single-source levels of that root, whether it ran alone or batched into a
 mixed stream; admission, capacity and shutdown behave as documented."""
 from __future__ import annotations
 
+import hashlib
+import json
 import threading
 import time
+from pathlib import Path
 
 import numpy as np
 import pytest
@@ -193,3 +196,59 @@ def test_shutdown_drains_or_cancels(graphs):
     for r, out in enumerate(outs):
         got = out.cpu().numpy()
         assert (got == 99).all() or np.array_equal(got, expected(graphs, 1, r))
+
+
+GOLDEN_SERVE = Path(__file__).parent / "golden" / "serve8_rmat_levels.json"
+
+
+def _sha(t: torch.Tensor) -> str:
+    a = t.cpu().numpy()
+    return hashlib.sha256(np.ascontiguousarray(a, dtype=a.dtype.newbyteorder("<")).data).hexdigest()
+
+
+def test_serving_workload_full_size_matches_oracle_digests():
+    """The serving workload at full size: 8 resident R-MAT graphs (scales 14,
+    16, 18-23, edgefactor 16, seeds 10-17), the benchmark's server settings,
+    a mixed stream of 2,000 queries submitted back to back; 8 queries per
+    graph, spread through the stream, must equal the oracle's levels
+    (digests written by tests/golden/make_serve8.py), and every CSR and root
+    pool the oracle's."""
+    gold = json.loads(GOLDEN_SERVE.read_text())
+    graphs, pools = [], []
+    for gg in gold["graphs"]:
+        n = 1 << gg["scale"]
+        off, idx = gb.rmat_graph(gg["scale"], gold["edgefactor"], gg["graph_seed"])
+        assert idx.numel() == gg["nnz"]
+        assert _sha(off) == gg["offsets_sha256"] and _sha(idx) == gg["indices_sha256"]
+        pool = gb.sample_roots(off, n, gg["root_seed"], gold["pool"])
+        assert _sha(pool) == gg["pool_sha256"]
+        graphs.append(gb.Graph(off, idx))
+        pools.append(pool.cpu().numpy())
+    cfg = gb.default_serve_config()
+    cfg.workers = 4
+    cfg.max_batch = 512
+    srv = gb.Server(cfg)
+    ids = [srv.add_graph(g) for g in graphs]
+    rng = np.random.default_rng(5)
+    scratch = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g in graphs]
+    checked = [(gi, q) for gi, gg in enumerate(gold["graphs"]) for q in gg["queries"]]
+    at = {int(p): c for p, c in zip(rng.choice(2000, len(checked), replace=False), checked)}
+    tickets, outs = [], []
+    for i in range(2000):
+        if i in at:
+            gi, q = at[i]
+            out = torch.full((graphs[gi].n,), 99, dtype=torch.int32, device="cuda")
+            outs.append((gi, q, out, srv.submit(ids[gi], q["root"], out)))
+        else:
+            gi = int(rng.integers(0, len(graphs)))
+            r = int(pools[gi][rng.integers(0, len(pools[gi]))])
+            tickets.append(srv.submit(ids[gi], r, scratch[gi]))
+    assert all(srv.wait(t) == 0 for t in tickets)
+    assert all(srv.wait(t) == 0 for _, _, _, t in outs)
+    torch.cuda.synchronize()
+    for gi, q, out, _ in outs:
+        assert _sha(out) == q["levels_sha256"], f"graph {gi}, root {q['root']}"
+        assert int((out >= 0).sum().item()) == q["reached"]
+    st = srv.stats()
+    assert st["failed"] == 0 and st["mean_batch"] > 1
+    srv.close()
