@@ -3,6 +3,10 @@ oracle, parents by the tree invariants, bottom-up parents and per-layer
 counters exact against the oracle's run of Alg. 3 under the same policy."""
 from __future__ import annotations
 
+import hashlib
+import json
+from pathlib import Path
+
 import numpy as np
 import pytest
 import torch
@@ -288,43 +292,163 @@ def test_validate_rejects_bad_csr():
     off = torch.tensor([0, 2, 1], dtype=torch.int64, device="cuda")
     with pytest.raises(gb.BfsError):
         gb.Graph(off, idx, validate=True)
+    with pytest.raises(gb.BfsError):           # range checks come first
+        gb.Graph(off, idx, validate="symmetric")
 
 
-def test_scale26_sampled_levels():
-    """Full-size workload in the benchmark's launch configuration: for every
-    sampled vertex the level must satisfy the local BFS characterisation
-    (root 0; reached v: some neighbour one level up and none more than one
-    level away; unreached: all neighbours unreached), checked on 4 roots with
-    2,000 sampled vertices each, and the component edge count must equal
-    half the degree sum over reached vertices."""
-    scale = 26
-    n = 1 << scale
-    off, idx = gb.rmat_graph(scale, 16, 1)
+def _dev(off, idx):
+    return (torch.tensor(off, dtype=torch.int64, device="cuda"),
+            torch.tensor(idx, dtype=torch.int32, device="cuda"))
+
+
+@pytest.mark.parametrize("case,ok", [
+    (([0, 1, 2], [1, 0]), True),                  # one undirected edge
+    (([0, 1, 1], [1]), False),                    # 0 -> 1 without 1 -> 0
+    (([0, 2, 3, 4], [2, 1, 0, 0]), False),        # symmetric, row 0 descending
+    (([0, 2, 4], [1, 1, 0, 0]), False),           # duplicate entries
+    (([0, 1, 1], [0]), True),                     # a self-loop is its own reverse
+    (([0, 0, 0], []), True),                      # no edges
+])
+def test_validate_symmetric(case, ok):
+    off, idx = _dev(*case)
+    gb.Graph(off, idx, validate=True)             # all pass the range checks
+    if ok:
+        gb.Graph(off, idx, validate="symmetric")
+    else:
+        with pytest.raises(gb.BfsError):
+            gb.Graph(off, idx, validate="symmetric")
+
+
+def test_validate_symmetric_generated_graphs():
+    # the library's own CSR builder output is symmetric with ascending rows;
+    # dropping one direction of one edge, or reversing a row, is caught
+    n, o_off, o_idx, g_off, g_idx = _rmat_both(16, 16, 1)
+    gb.Graph(g_off, g_idx, validate="symmetric")
+    rev = torch.as_tensor(_reversed_rows(o_off, o_idx)).cuda()
+    with pytest.raises(gb.BfsError):
+        gb.Graph(g_off, rev, validate="symmetric")
+    # move the first entry u0 of some row v up to u0 + 1 (< the next entry, so
+    # the row stays ascending): v -> u0 + 1 has no reverse entry
+    for v in range(n):
+        lo, hi = o_off[v], o_off[v + 1]
+        if hi - lo >= 2 and o_idx[lo + 1] - o_idx[lo] >= 2 and o_idx[lo] + 1 != v:
+            break
+    cut = o_idx.copy()
+    cut[lo] += 1
+    w = int(cut[lo])
+    assert v not in o_idx[o_off[w]:o_off[w + 1]]
+    with pytest.raises(gb.BfsError):
+        gb.Graph(g_off, torch.as_tensor(cut).cuda(), validate="symmetric")
+
+
+GOLDEN26 = Path(__file__).parent / "golden" / "rmat26_ef16_seed1_bfs.json"
+
+
+def _sha(t: torch.Tensor) -> str:
+    a = t.cpu().numpy()
+    return hashlib.sha256(np.ascontiguousarray(a, dtype=a.dtype.newbyteorder("<")).data).hexdigest()
+
+
+@pytest.fixture(scope="module")
+def rmat26():
+    """The full-size single-source workload as the benchmark runs it: R-MAT
+    SCALE 26, edgefactor 16, graph seed 1, 64 roots of seed 2, default
+    configuration (host-driven loop at this size)."""
+    gold = json.loads(GOLDEN26.read_text())
+    n = 1 << gold["scale"]
+    off, idx = gb.rmat_graph(gold["scale"], gold["edgefactor"], gold["graph_seed"])
     g = gb.Graph(off, idx)
-    roots = gb.sample_roots(off, n, 2, 64)
-    rng = np.random.default_rng(1)
+    roots = gb.sample_roots(off, n, gold["root_seed"], 64).tolist()
+    src = torch.repeat_interleave(torch.arange(n, dtype=torch.int32, device="cuda"),
+                                  off[1:] - off[:-1])       # row of every CSR entry
+    yield gold, off, idx, g, roots, src
+    del g, src
+
+
+def _full_check(off, idx, src, root, level, parent, minimal):
+    """The BFS characterisation over every edge (any size): level[root] = 0;
+    no edge joins a reached and an unreached vertex or two levels more than
+    one apart; every reached v != root has a neighbour one level up. The
+    parent of such v is a neighbour one level up (exactly one row entry
+    equals it: rows are deduplicated), and with `minimal` the smallest one.
+    Unreached vertices hold -1 in both arrays. Returns the component edges."""
+    n = level.numel()
+    lu = level[src]
+    lv = torch.index_select(level, 0, idx)
+    assert bool(((lu >= 0) == (lv >= 0)).all()), "an edge leaves the reached set"
+    assert int((lu - lv).abs().max().item()) <= 1, "an edge spans two layers"
+    up = (lv == lu - 1) & (lu > 0)
+    cnt = torch.zeros(n, dtype=torch.int32, device="cuda").index_add_(0, src, up.int())
+    reached = level >= 0
+    inner = reached.clone()
+    inner[root] = False
+    assert level[root].item() == 0 and parent[root].item() == root
+    assert bool((cnt[inner] > 0).all()), "a reached vertex without a neighbour one level up"
+    assert bool((level[~reached] == -1).all()) and bool((parent[~reached] == -1).all())
+    is_par = (idx == parent[src]) & up
+    pc = torch.zeros(n, dtype=torch.int32, device="cuda").index_add_(0, src, is_par.int())
+    assert bool((pc[inner] == 1).all()), "a parent that is not a neighbour one level up"
+    if minimal:
+        big = torch.iinfo(torch.int32).max
+        cand = torch.where(up, idx, torch.full_like(idx, big))
+        best = torch.full((n,), big, dtype=torch.int32, device="cuda")
+        best.scatter_reduce_(0, src.long(), cand, "amin")
+        assert torch.equal(parent[inner], best[inner]), "parent is not the smallest one"
+    deg = off[1:] - off[:-1]
+    return int(deg[reached].sum().item()) // 2
+
+
+def test_scale26_csr_and_roots_match_oracle_digests(rmat26):
+    # the whole generated CSR and the 64 roots, against digests that the
+    # oracle wrote for the same seeds (tests/golden/make_rmat26_bfs.py)
+    gold, off, idx, g, roots, src = rmat26
+    assert idx.numel() == gold["nnz"]
+    assert _sha(off) == gold["offsets_sha256"]
+    assert _sha(idx) == gold["indices_sha256"]
+    assert roots == gold["roots"]
+
+
+def test_scale26_levels_and_min_parents_exact(rmat26):
+    # 8 roots: levels bit-exact against the oracle's FIFO BFS (digest), and
+    # with parent_min the whole parent array against the oracle's post-pass
+    gold, off, idx, g, roots, src = rmat26
+    n = off.numel() - 1
     level = torch.empty(n, dtype=torch.int32, device="cuda")
     parent = torch.empty(n, dtype=torch.int32, device="cuda")
-    for r in roots[:4].tolist():
+    gm = gb.Graph(off, idx, config(parent_min=1), borrow=True)
+    for e in gold["exact"]:
+        r = e["root"]
         g.run(r, level, parent)
         torch.cuda.synchronize()
-        assert level[r].item() == 0 and parent[r].item() == r
-        degs = (off[1:] - off[:-1])
-        ce = int(degs[level >= 0].sum().item()) // 2
-        assert g.stats().component_edges == ce
-        for v in rng.choice(n, 2000, replace=False).tolist():
-            a, b = off[v].item(), off[v + 1].item()
-            nb = idx[a:b]
-            lv = level[v].item()
-            nl = level[nb.long()] if b > a else torch.empty(0, dtype=torch.int32, device="cuda")
-            if lv < 0:
-                assert bool((nl < 0).all()) and parent[v].item() == -1
-            elif v != r:
-                assert bool((nl >= 0).all())
-                assert int((nl - lv).abs().max().item()) <= 1
-                assert bool((nl == lv - 1).any())
-                p = parent[v].item()
-                assert level[p].item() == lv - 1 and bool((nb == p).any())
+        assert _sha(level) == e["levels_sha256"], f"levels of root {r}"
+        ce = _full_check(off, idx, src, r, level, parent, minimal=False)
+        assert ce == e["component_edges"] == g.stats().component_edges
+        sizes = torch.bincount(level[level >= 0].long()).tolist()
+        assert sizes == e["layer_sizes"]
+        parent.fill_(7)
+        gm.run(r, level, parent)
+        torch.cuda.synchronize()
+        assert _sha(level) == e["levels_sha256"]
+        assert _sha(parent) == e["min_parent_sha256"], f"min parents of root {r}"
+
+
+def test_scale26_all_64_roots_full_check(rmat26):
+    # every root of the benchmark: the characterisation over all 2^31 CSR
+    # entries, parents included; then with parent_min, minimality too
+    gold, off, idx, g, roots, src = rmat26
+    n = off.numel() - 1
+    level = torch.empty(n, dtype=torch.int32, device="cuda")
+    parent = torch.empty(n, dtype=torch.int32, device="cuda")
+    for r in roots:
+        g.run(r, level, parent)
+        torch.cuda.synchronize()
+        ce = _full_check(off, idx, src, r, level, parent, minimal=False)
+        assert ce == g.stats().component_edges
+    gm = gb.Graph(off, idx, config(parent_min=1), borrow=True)
+    for r in roots[::4]:
+        gm.run(r, level, parent)
+        torch.cuda.synchronize()
+        _full_check(off, idx, src, r, level, parent, minimal=True)
 
 
 def _reversed_rows(o_off, o_idx):
