@@ -53,7 +53,7 @@ def parse():
                         "batch: one batched configuration timed alone")
     p.add_argument("--batch-k", type=int, default=512, help="roots per batch (--mode batch)")
     p.add_argument("--no-batch", action="store_true", help="skip the batched comparison")
-    p.add_argument("--device-loop", type=int, default=2, choices=[0, 1, 2],
+    p.add_argument("--device-loop", type=int, default=2, choices=[0, 1, 2, 3],
                    help="bfs_config.device_loop: 0 host loop, 1 device loop, 2 library default")
     p.add_argument("--batch-scale", type=int, default=22)
     p.add_argument("--serve-queries", type=int, default=10000)
@@ -510,7 +510,10 @@ def main():
     nnz = idx.numel()
     deg1 = int(((off[1:] - off[:-1]) > 0).sum().item())  # vertices of degree >= 1
     cfg = gb.default_config()
-    cfg.timing = 1
+    # events only around the hub sweeps inside the timed region (the kernel
+    # the roofline is quoted for); per-layer events for the other sections
+    # come from an untimed pass afterwards
+    cfg.timing = 2
     cfg.device_loop = args.device_loop
     g = gb.Graph(off, idx, cfg)
     roots = gb.sample_roots(off, n, args.root_seed + rank, args.roots).cpu().tolist()
@@ -578,8 +581,23 @@ def main():
                 first_sweep = False
                 hub_bytes += n / 2 + 8 * active + 8 * written
                 hub_ms += L["ms_sweep"]
-                scan_ms += L["ms_main"] - L["ms_sweep"]
                 n_hub += 1
+    # the other kernels' sections: one untimed pass over the same roots with
+    # events around every layer
+    pcfg = gb.default_config()
+    pcfg.timing = 1
+    pcfg.device_loop = args.device_loop
+    g.set_config(pcfg)
+    prof = []
+    for r in roots:
+        g.run(r, level, parent)
+        prof.append(g.stats())
+    g.set_config(cfg)
+    for st in prof:
+        for L in st.layers:
+            active = L["n_u"] - (n - deg1)
+            if L["direction"] == 1 and L["converted"] == 3:
+                scan_ms += L["ms_main"] - L["ms_sweep"]
             elif L["direction"] == 1 and L["converted"] == 2:
                 bl_bytes += n / 8 + 12 * active + 4 * L["examined"] + 16 * L["found"]
                 bl_ms += L["ms_main"]
@@ -597,6 +615,28 @@ def main():
             gather_ranks(dist, world, [my_hmean, my_total_s, wall], "cuda"))
     else:
         value, total_s = my_hmean, my_total_s
+
+    # the layer loops compared on the same roots, untimed per layer: host
+    # loop (counters polled per layer), cooperative persistent kernel, CUDA
+    # graph with device-side control flow
+    loops = {}
+    if not args.no_batch:
+        for name, mode in (("host", 0), ("persistent", 1), ("graph", 3)):
+            lc = gb.default_config()
+            lc.device_loop = mode
+            g.set_config(lc)
+            for r in roots[:4]:
+                g.run(r, level, parent)
+            ts = []
+            for r in roots:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g.run(r, level, parent)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(g.stats().component_edges / (e0.elapsed_time(e1) / 1e3))
+            loops[name] = hmean(ts) / 1e9
 
     # end to end through the public API with host buffers: every root's level
     # and parent arrays are copied back to pinned host memory inside the timed
@@ -651,13 +691,13 @@ def main():
                      "avg_launch_ms": hub_ms / max(1, n_hub), "launches": n_hub},
         "sweep_roofline": {"bytes": b_sweep, "teps": roof_teps / 1e9, "unit": "GTEPS",
                            "frac": value / roof_teps if world == 1 else None},
-        "bu_scan_step": {"ms": scan_ms, "layers": n_hub},
+        "bu_scan_step": {"ms": scan_ms, "pass": "untimed, per-layer events"},
         "bu_list_step": {"achieved_gbs": (bl_bytes / (bl_ms / 1e3)) / 1e9 if bl_ms > 0 else 0.0,
-                         "ms": bl_ms, "launches": n_bl},
+                         "ms": bl_ms, "launches": n_bl, "pass": "untimed, per-layer events"},
         "bu_one_pass_step": {"achieved_gbs": (bu1_bytes / (bu1_ms / 1e3)) / 1e9
                              if bu1_ms > 0 else 0.0, "ms": bu1_ms, "launches": n_bu1},
         "td_step": {"achieved_gbs": (td_bytes / (td_ms / 1e3)) / 1e9 if td_ms > 0 else 0.0,
-                    "ms": td_ms},
+                    "ms": td_ms, "pass": "untimed, per-layer events"},
         "aggregate_teps": sum(edges) / sum(times) / 1e9,
         "teps_min_median_max": [min(teps) / 1e9, statistics.median(teps) / 1e9, max(teps) / 1e9],
         "component_edges_median": m_c,
@@ -665,6 +705,7 @@ def main():
         "e2e": {"value": e2e_val / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": 4 * len(roots),
                 "d2h_bytes_per_step": 8 * n * len(roots)},
         "gpu_launches": launches,
+        "layer_loops_gteps": loops,
         "clocks": clk,
     }
     if not args.no_batch and world == 1:

@@ -130,7 +130,10 @@ typedef struct bfs_config {
                                 grid (the threshold used per layer is the
                                 frontier's edges per resident warp, clamped to
                                 [4*td_warp_degree, td_grid_degree])            */
-    int32_t timing;          /* 1 = record CUDA events around each layer      */
+    int32_t timing;          /* 1 = record CUDA events around each layer
+                                (ms_total, ms_main, ms_sweep); 2 = only around
+                                each hub sweep (ms_sweep), so fewer event
+                                records delay the next layer's launches      */
     int32_t bu_words;        /* bottom-up: bitmap words a warp keeps in
                                 flight (1, 2 or 4)                             */
     int32_t td_claim;        /* top-down claim of a vertex: 0 = atomicCAS on
@@ -182,7 +185,15 @@ typedef struct bfs_config {
                                 round trip per layer; per-layer times are not
                                 recorded); 0 = host loop; 2 (default) = the
                                 device loop for n <= 2^25, where the host round
-                                trips weigh most, the host loop above         */
+                                trips weigh most, the host loop above;
+                                3 = graph loop: the host loop's kernels as one
+                                CUDA graph (a WHILE node over a SWITCH node)
+                                whose one-thread step kernel takes the Alg. 3
+                                decision on the device between layers; built
+                                on first use per configuration (at most 256
+                                layers per graph launch, relaunched until the
+                                traversal ends); with timing = 1 the host
+                                loop runs instead                             */
     int32_t host_async;      /* with host output buffers: 1 = bfs_run returns
                                 once the traversal is done and the copy of its
                                 results to the host runs on the graph's own

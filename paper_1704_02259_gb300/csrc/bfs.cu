@@ -267,9 +267,11 @@ __global__ void __launch_bounds__(kBlock) min_parent_kernel(
 // visited only as a degree-0 vertex or id past n), the root excepted: the
 // outputs of a traversal that started without write_out and has had no
 // writing hub sweep.
-__global__ void out_fill_kernel(int64_t n, int32_t root, const uint32_t *__restrict__ visited,
-                                const uint32_t *__restrict__ base,
-                                int32_t *__restrict__ level, int32_t *__restrict__ parent) {
+__device__ __forceinline__ void out_fill_phase(int64_t n, int32_t root,
+                                               const uint32_t *__restrict__ visited,
+                                               const uint32_t *__restrict__ base,
+                                               int32_t *__restrict__ level,
+                                               int32_t *__restrict__ parent) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += stride) {
         const uint32_t reached = visited[v >> 5] & ~base[v >> 5];
@@ -278,6 +280,12 @@ __global__ void out_fill_kernel(int64_t n, int32_t root, const uint32_t *__restr
             parent[v] = -1;
         }
     }
+}
+
+__global__ void out_fill_kernel(int64_t n, int32_t root, const uint32_t *__restrict__ visited,
+                                const uint32_t *__restrict__ base,
+                                int32_t *__restrict__ level, int32_t *__restrict__ parent) {
+    out_fill_phase(n, root, visited, base, level, parent);
 }
 
 __device__ __forceinline__ void block_add4(int64_t a, int64_t b, int64_t c, int64_t e,
@@ -1250,7 +1258,8 @@ bool config_ok(const bfs_config &c) {
     if (c.parent_min != 0 && c.parent_min != 1) return false;
     if (c.prune_components != 0 && c.prune_components != 1) return false;
     if (c.bu_list_percent < 0 || c.bu_list_percent > 100) return false;
-    if (c.device_loop < 0 || c.device_loop > 2) return false;
+    if (c.device_loop < 0 || c.device_loop > 3) return false;
+    if (c.timing < 0 || c.timing > 2) return false;
     return true;
 }
 
@@ -1543,6 +1552,489 @@ bfs_status run_device_loop(bfs_graph *g, int32_t *level, int32_t *parent, cudaSt
     return BFS_OK;
 }
 
+// Graph loop (device_loop = 3): the layer loop as one CUDA graph whose
+// control flow stays on the device. A WHILE node repeats {gl_step_kernel,
+// SWITCH}: the step kernel closes the layer that just ran (its record and
+// the Alg. 3 counters), applies the Alg. 3 switch for the next layer and
+// picks that layer's variant, which the SWITCH node runs. The variants are
+// the host loop's kernel sequences, as wrappers that read their per-layer
+// arguments from the device-resident GlRun. There is no host round trip
+// between layers; one launch runs at most kGlCap layers, so every launch
+// ends, and the host launches again while the traversal is not done.
+enum GlCase : unsigned {
+    GL_TD = 0,         // top-down; + 1 queue rebuilt first, + 2 grid-spread vertices,
+                       //           + 4 deferred level pass   (cases 0..7)
+    GL_LIST = 8,       // sparse bottom-up layer over the list of unvisited vertices
+    GL_LIST_FILL = 9,  //   the same after the -1 fill of the outputs
+    GL_TWO = 10,       // two-pass bottom-up: hub sweep, list of misses, row scans
+    GL_ONE = 11,       // one-pass bottom-up
+    GL_ONE_FILL = 12,  //   the same after the -1 fill
+    GL_CASES = 13      // a value >= GL_CASES runs no layer
+};
+constexpr int kGlCap = 256;  // layers per graph launch
+constexpr int kGlRec = 10;   // int64 fields per layer record
+constexpr size_t kGlRunBytes = 256;
+
+struct GlRun {
+    int64_t n_f, m_f, n_u, m_u, degsum, kernels, grid_deg;
+    int64_t *sc, *sn, *sz;  // trace slots of the planned layer
+    uint32_t *front, *next;
+    int32_t *q_cur, *q_next;
+    int32_t *level, *parent;
+    int32_t d, cur_bu, have_queue, filled, status, done, pending, iter;
+    int32_t root, converted, per_warp, queue_mode, defer, init_out;
+};
+static_assert(sizeof(GlRun) <= kGlRunBytes, "GlRun must fit its slot");
+
+struct GlStatic {
+    const int64_t *off;
+    const int32_t *idx;
+    const int2 *head;  // head records (bu_head != 0), else null
+    int hskip;
+    const uint32_t *base_vis;
+    uint32_t *visited, *bm_a, *bm_b, *pend;
+    int32_t *q_a, *q_b, *big;
+    int64_t *trace;
+    int64_t *rec;  // [kSsMaxRecords][kGlRec] per-layer records
+    GlRun *run;
+    int64_t n, nnz, nw, nw_pad, deg0, td_warps;
+    int two_pass, bu_span_w;
+    bfs_config cfg;
+    cudaGraphConditionalHandle h_loop, h_case, h_fill;
+};
+
+__global__ void gl_start_kernel(GlStatic s, int32_t *level, int32_t *parent, int32_t root,
+                                int filled) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    GlRun &r = *s.run;
+    r.n_f = 1;
+    r.m_f = s.trace[T_MF];  // degree of the root (init_kernel)
+    r.n_u = s.n - 1;
+    r.m_u = s.nnz - r.m_f;
+    r.degsum = 0;
+    r.kernels = 0;
+    r.d = 0;
+    r.cur_bu = 0;
+    r.have_queue = 1;
+    r.filled = filled;
+    r.status = BFS_OK;
+    r.done = 0;
+    r.pending = 0;
+    r.iter = 0;
+    r.level = level;
+    r.parent = parent;
+    r.root = root;
+}
+
+__global__ void gl_begin_kernel(GlStatic s) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) s.run->iter = 0;
+}
+
+__global__ void gl_step_kernel(GlStatic s) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    GlRun &r = *s.run;
+    r.kernels += 1;
+    if (r.pending) {  // close the layer that just ran
+        const int64_t found = r.sn[T_NF], m_new = r.sn[T_MF];
+        if (r.d < kSsMaxRecords) {
+            int64_t *rec = s.rec + (int64_t)r.d * kGlRec;
+            rec[0] = r.cur_bu;
+            rec[1] = r.converted;
+            rec[2] = r.n_f;
+            rec[3] = r.m_f;
+            rec[4] = r.n_u;
+            rec[5] = r.m_u;
+            rec[6] = r.cur_bu ? r.sn[T_EXAM] : r.m_f;
+            rec[7] = found;
+            rec[8] = r.converted == 3 ? r.sn[T_HUB] : 0;
+            rec[9] = 0;
+        }
+        r.n_u -= found;
+        r.m_u -= m_new;
+        r.n_f = found;
+        r.m_f = m_new;
+        r.have_queue = r.cur_bu ? 0 : r.queue_mode;
+        r.d += 1;
+        r.pending = 0;
+    }
+    bool go = r.status == BFS_OK && r.n_f > 0;
+    if (go && r.d > s.n) {  // a BFS has at most n layers: the counters are inconsistent
+        r.status = BFS_ERR_CUDA;
+        go = false;
+    }
+    if (!go) {
+        const bool fill = r.status == BFS_OK && !r.filled;
+        r.done = 1;
+        if (fill) {
+            r.filled = 1;
+            r.kernels += 1;
+        }
+        cudaGraphSetConditional(s.h_case, GL_CASES);
+        cudaGraphSetConditional(s.h_fill, fill ? 1u : 0u);
+        cudaGraphSetConditional(s.h_loop, 0u);
+        return;
+    }
+    if (r.iter >= kGlCap) {  // this launch is done; the host launches the graph again
+        cudaGraphSetConditional(s.h_case, GL_CASES);
+        cudaGraphSetConditional(s.h_loop, 0u);
+        return;
+    }
+    const int d = r.d;
+    const int cur_bu = decide(s.cfg, r.cur_bu, d, s.n, r.n_f, r.m_f, r.n_u, r.m_u);
+    r.cur_bu = cur_bu;
+    r.degsum += r.m_f;
+    r.sc = s.trace + (d % kRing) * kFields;
+    r.sn = s.trace + ((d + 1) % kRing) * kFields;
+    r.sz = s.trace + ((d + 2) % kRing) * kFields;
+    r.front = (d & 1) ? s.bm_b : s.bm_a;
+    r.next = (d & 1) ? s.bm_a : s.bm_b;
+    r.q_cur = (d & 1) ? s.q_b : s.q_a;
+    r.q_next = (d & 1) ? s.q_a : s.q_b;
+    unsigned c;
+    int nk;
+    r.converted = 0;
+    if (!cur_bu) {
+        r.queue_mode = r.m_f <= kQueueModeMaxEdges ? 1 : 0;
+        r.defer = td_defer(r.queue_mode, r.n_u - s.deg0, s.nw);
+        const int64_t pw = (r.n_f + s.td_warps - 1) / s.td_warps;
+        r.per_warp = (int)(pw < 1 ? 1 : (pw > 32 ? 32 : pw));
+        int64_t gd = r.m_f / s.td_warps;
+        if (gd < 4 * (int64_t)s.cfg.td_warp_degree) gd = 4 * (int64_t)s.cfg.td_warp_degree;
+        if (gd > s.cfg.td_grid_degree) gd = s.cfg.td_grid_degree;
+        r.grid_deg = gd;
+        const int b2q = r.have_queue ? 0 : 1, big = r.m_f >= gd ? 1 : 0;
+        r.converted = b2q;
+        c = GL_TD + b2q + 2 * big + 4 * r.defer;
+        nk = 2 + b2q + big + r.defer;
+    } else {
+        const int64_t active = r.n_u - s.deg0;
+        const int fill = r.filled ? 0 : 1;
+        if (s.cfg.bu_list_percent > 0 && active * 100 <= (int64_t)s.cfg.bu_list_percent * s.n) {
+            r.converted = 2;
+            c = fill ? GL_LIST_FILL : GL_LIST;
+            nk = 3 + fill;
+        } else if (s.two_pass) {
+            r.converted = 3;
+            r.init_out = fill;
+            c = GL_TWO;
+            nk = 3;
+        } else {
+            c = fill ? GL_ONE_FILL : GL_ONE;
+            nk = 1 + fill;
+        }
+        r.filled = 1;
+    }
+    r.pending = 1;
+    r.iter += 1;
+    r.kernels += nk;
+    cudaGraphSetConditional(s.h_case, c);
+    cudaGraphSetConditional(s.h_loop, 1u);
+}
+
+// Layer kernels of the graph loop: the host loop's phases with the arguments
+// of the planned layer.
+__global__ void __launch_bounds__(kBlock) gl_b2q_kernel(GlStatic s) {
+    const GlRun &r = *s.run;
+    b2q_phase<false>(r.front, s.nw, r.q_cur, (unsigned long long *)(r.sc + T_CONV));
+}
+
+__global__ void __launch_bounds__(kBlock) gl_clear_kernel(GlStatic s) {
+    uint32_t *next = s.run->next;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < s.nw_pad; i += stride)
+        next[i] = 0u;
+}
+
+__device__ __forceinline__ TdArgs gl_td_args(const GlStatic &s, const GlRun &r) {
+    return TdArgs{s.off, s.idx, s.visited, r.next, r.parent, r.level, r.q_next,
+                  (unsigned long long *)(r.sn + T_NF), r.d + 1, r.queue_mode, s.cfg.td_claim,
+                  r.defer};
+}
+
+__global__ void __launch_bounds__(kBlock, 4) gl_td_kernel(GlStatic s) {
+    const GlRun &r = *s.run;
+    td_phase<false>(gl_td_args(s, r), r.q_cur, r.n_f, r.per_warp, s.big,
+                    (unsigned long long *)(r.sc + T_BIG), (unsigned long long *)(r.sn + T_MF),
+                    s.cfg.td_warp_degree, r.grid_deg, r.sz);
+}
+
+__global__ void __launch_bounds__(kBlock, 5) gl_td_big_kernel(GlStatic s) {
+    const GlRun &r = *s.run;
+    td_big_phase<false>(gl_td_args(s, r), s.big, (const unsigned long long *)(r.sc + T_BIG),
+                        (unsigned long long *)(r.sn + T_MF));
+}
+
+__global__ void __launch_bounds__(kBlock) gl_td_post_kernel(GlStatic s) {
+    const GlRun &r = *s.run;
+    td_post_phase<false>(s.off, r.next, s.nw, r.level, r.d + 1,
+                         (unsigned long long *)(r.sn + T_NF), (unsigned long long *)(r.sn + T_MF));
+}
+
+__global__ void gl_fill_kernel(GlStatic s) {
+    const GlRun &r = *s.run;
+    out_fill_phase(s.n, r.root, s.visited, s.base_vis, r.level, r.parent);
+}
+
+template <bool PEND>
+__global__ void __launch_bounds__(kBlock) gl_bits_list_kernel(GlStatic s) {
+    const GlRun &r = *s.run;
+    bits_list_phase<false>(PEND ? s.pend : s.visited, PEND ? 0u : ~0u, s.nw, r.q_next,
+                           (unsigned long long *)(r.sc + T_ULIST));
+}
+
+template <bool HEADED>
+__global__ void __launch_bounds__(kBlock, 5) gl_bu_list_kernel(GlStatic s) {
+    const GlRun &r = *s.run;
+    bu_list_phase<false>(s.off, s.idx, HEADED ? s.head : nullptr, HEADED ? s.hskip : 0, r.q_next,
+                         (const unsigned long long *)(r.sc + T_ULIST), s.visited, r.front, r.next,
+                         r.parent, r.level, r.d + 1, s.cfg.bu_probe, (unsigned long long *)r.sn,
+                         r.sz);
+}
+
+__global__ void __launch_bounds__(kBlock, 4) gl_bu_hub_kernel(GlStatic s) {
+    const GlRun &r = *s.run;
+    bu_hub_phase<false>(s.head, s.nw_pad, s.visited, r.front, r.next, s.pend, r.parent, r.level,
+                        r.d + 1, (unsigned long long *)r.sn, r.sz, r.init_out, s.base_vis, s.n,
+                        r.root);
+}
+
+template <int W, int CH, bool HEAD>
+__global__ void __launch_bounds__(kBlock, 4) gl_bu_kernel(GlStatic s) {
+    const GlRun &r = *s.run;
+    bu_phase<W, CH, HEAD, false>(s.off, s.idx, s.head, s.nw_pad, s.visited, r.front, r.next,
+                                 r.parent, r.level, r.d + 1, s.cfg.bu_probe,
+                                 (unsigned long long *)r.sn, r.sz, s.bu_span_w, s.hskip);
+}
+
+void destroy_graph_loop(bfs_graph *g) {
+    if (g->gl_exec) cudaGraphExecDestroy(g->gl_exec);
+    if (g->gl_graph) cudaGraphDestroy(g->gl_graph);
+    g->gl_exec = nullptr;
+    g->gl_graph = nullptr;
+}
+
+void free_graph_loop(bfs_graph *g) {
+    destroy_graph_loop(g);
+    cudaFree(g->gl_mem);
+    if (g->h_gl) cudaFreeHost(g->h_gl);
+    delete (GlStatic *)g->gl_static;
+    g->gl_mem = g->h_gl = g->gl_static = nullptr;
+}
+
+// Builds and instantiates the graph for the graph's current configuration.
+bfs_status build_graph_loop(bfs_graph *g) {
+    const bfs_config &cfg = g->cfg;
+    if (!g->gl_mem) {
+        GB_CK(cudaMalloc(&g->gl_mem, kGlRunBytes + (size_t)kSsMaxRecords * kGlRec * 8));
+        GB_CK(cudaMallocHost(&g->h_gl, kGlRunBytes + (size_t)kSsMaxRecords * kGlRec * 8));
+    }
+    if (cfg.bu_head == 2 && !g->pend) GB_CK(cudaMalloc(&g->pend, (size_t)g->nw_pad * 4));
+    const int bw = cfg.bu_words;
+    const int bsel = (bw == 4 ? 2 : bw - 1) + (cfg.bu_head ? 3 : 0);
+    const void *one_fn[6] = {(const void *)gl_bu_kernel<1, 4, false>,
+                             (const void *)gl_bu_kernel<2, 4, false>,
+                             (const void *)gl_bu_kernel<4, 2, false>,
+                             (const void *)gl_bu_kernel<1, 4, true>,
+                             (const void *)gl_bu_kernel<2, 4, true>,
+                             (const void *)gl_bu_kernel<4, 2, true>};
+    // resident blocks per SM of the graph's own kernels (their register
+    // counts differ from the host loop's kernels)
+    auto occ = [](const void *fn, int *out) -> cudaError_t {
+        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, fn, kBlock, 0);
+        if (*out < 1) *out = 1;
+        return e;
+    };
+    int o_td = 1, o_big = 1, o_list = 1, o_hub = 1, o_one = 1;
+    GB_CK(occ((const void *)gl_td_kernel, &o_td));
+    GB_CK(occ((const void *)gl_td_big_kernel, &o_big));
+    GB_CK(occ((const void *)gl_bu_list_kernel<true>, &o_list));
+    GB_CK(occ((const void *)gl_bu_hub_kernel, &o_hub));
+    GB_CK(occ(one_fn[bsel], &o_one));
+    const int64_t bu_full = (int64_t)sm_count() * o_one;
+    const int64_t td_full = (int64_t)sm_count() * o_td;
+    if (!g->gl_static) g->gl_static = new GlStatic;
+    GlStatic &s = *(GlStatic *)g->gl_static;
+    memset(&s, 0, sizeof s);
+    s.off = g->off;
+    s.idx = g->idx;
+    s.head = cfg.bu_head ? g->head : nullptr;
+    s.hskip = cfg.bu_head == 1 ? 1 : 0;
+    s.base_vis = g->base_vis;
+    s.visited = g->visited;
+    s.bm_a = g->bm_a;
+    s.bm_b = g->bm_b;
+    s.pend = g->pend;
+    s.q_a = g->q_a;
+    s.q_b = g->q_b;
+    s.big = g->big;
+    s.trace = g->trace;
+    s.run = (GlRun *)g->gl_mem;
+    s.rec = (int64_t *)((char *)g->gl_mem + kGlRunBytes);
+    s.n = g->n;
+    s.nnz = g->nnz;
+    s.nw = g->nw;
+    s.nw_pad = g->nw_pad;
+    s.deg0 = g->deg0;
+    s.td_warps = td_full * (kBlock / 32);
+    s.two_pass = cfg.bu_head == 2 &&
+                 g->nw >= (int64_t)8 * sm_count() * g->bu_hub_blocks_per_sm * (kBlock / 32);
+    s.bu_span_w = bu_span(g->nw_pad >> 5, bw, bu_full * (kBlock / 32));
+    s.cfg = cfg;
+
+    cudaGraph_t gr = nullptr;
+    GB_CK(cudaGraphCreate(&gr, 0));
+    struct Guard {
+        cudaGraph_t &gr;
+        ~Guard() {
+            if (gr) cudaGraphDestroy(gr);
+        }
+    } guard{gr};
+    GB_CK(cudaGraphConditionalHandleCreate(&s.h_loop, gr, 1, cudaGraphCondAssignDefault));
+    GB_CK(cudaGraphConditionalHandleCreate(&s.h_fill, gr, 0, cudaGraphCondAssignDefault));
+    void *args[] = {&s};
+    auto kernel = [&](cudaGraph_t in, cudaGraphNode_t *dep, const void *fn, int grid,
+                      int block) -> cudaError_t {
+        cudaKernelNodeParams kp;
+        memset(&kp, 0, sizeof kp);
+        kp.func = const_cast<void *>(fn);
+        kp.gridDim = dim3(grid);
+        kp.blockDim = dim3(block);
+        kp.kernelParams = args;
+        cudaGraphNode_t node;
+        const cudaError_t e = cudaGraphAddKernelNode(&node, in, *dep ? dep : nullptr, *dep ? 1 : 0,
+                                                     &kp);
+        *dep = node;
+        return e;
+    };
+    auto conditional = [&](cudaGraph_t in, cudaGraphNode_t *dep, cudaGraphConditionalHandle h,
+                           cudaGraphConditionalNodeType type, unsigned size,
+                           cudaGraph_t **bodies) -> cudaError_t {
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = type;
+        np.conditional.size = size;
+        cudaGraphNode_t node;
+        const cudaError_t e = cudaGraphAddNode(&node, in, *dep ? dep : nullptr, nullptr,
+                                               *dep ? 1 : 0, &np);
+        *dep = node;
+        *bodies = np.conditional.phGraph_out;
+        return e;
+    };
+    cudaGraphNode_t top = nullptr;
+    GB_CK(kernel(gr, &top, (const void *)gl_begin_kernel, 1, 32));
+    cudaGraph_t *loop_body = nullptr;
+    GB_CK(conditional(gr, &top, s.h_loop, cudaGraphCondTypeWhile, 1, &loop_body));
+    cudaGraph_t body = loop_body[0];
+    GB_CK(cudaGraphConditionalHandleCreate(&s.h_case, body, GL_CASES, cudaGraphCondAssignDefault));
+    cudaGraphNode_t step = nullptr;
+    GB_CK(kernel(body, &step, (const void *)gl_step_kernel, 1, 32));
+    cudaGraph_t *cases = nullptr;
+    GB_CK(conditional(body, &step, s.h_case, cudaGraphCondTypeSwitch, GL_CASES, &cases));
+
+    const int g_b2q = grid_cap(g->nw, kBlock * 4, 8);
+    const int g_clear = grid_cap(g->nw_pad, kBlock, 8);
+    const int g_td = (int)std::max<int64_t>(1, td_full);
+    const int g_big = (int)std::max<int64_t>(1, (int64_t)sm_count() * o_big);
+    const int g_post = grid_cap(g->nw, kBlock / 4, 8);
+    const int g_fill = grid_cap(g->n, kBlock, 8);
+    const int g_bits = grid_cap(g->nw, kBlock * 4, 8);
+    const int g_list = (int)std::max<int64_t>(1, (int64_t)sm_count() * o_list);
+    const int g_hub = grid_cap(g->nw_pad, kBlock / 32 * 8, o_hub);
+    const int g_one = (int)std::max<int64_t>(
+        1, std::min<int64_t>((g->nw_pad >> 5) * (32 / s.bu_span_w) / (kBlock / 32) + 1, bu_full));
+    for (unsigned c = 0; c < GL_CASES; ++c) {
+        cudaGraph_t b = cases[c];
+        cudaGraphNode_t t = nullptr;
+        if (c < GL_LIST) {
+            if (c & 1) GB_CK(kernel(b, &t, (const void *)gl_b2q_kernel, g_b2q, kBlock));
+            GB_CK(kernel(b, &t, (const void *)gl_clear_kernel, g_clear, kBlock));
+            GB_CK(kernel(b, &t, (const void *)gl_td_kernel, g_td, kBlock));
+            if (c & 2) GB_CK(kernel(b, &t, (const void *)gl_td_big_kernel, g_big, kBlock));
+            if (c & 4) GB_CK(kernel(b, &t, (const void *)gl_td_post_kernel, g_post, kBlock));
+        } else if (c == GL_LIST || c == GL_LIST_FILL) {
+            if (c == GL_LIST_FILL) GB_CK(kernel(b, &t, (const void *)gl_fill_kernel, g_fill, kBlock));
+            GB_CK(kernel(b, &t, (const void *)gl_clear_kernel, g_clear, kBlock));
+            GB_CK(kernel(b, &t, (const void *)gl_bits_list_kernel<false>, g_bits, kBlock));
+            GB_CK(kernel(b, &t, (const void *)gl_bu_list_kernel<true>, g_list, kBlock));
+        } else if (c == GL_TWO) {
+            GB_CK(kernel(b, &t, (const void *)gl_bu_hub_kernel, g_hub, kBlock));
+            GB_CK(kernel(b, &t, (const void *)gl_bits_list_kernel<true>, g_bits, kBlock));
+            GB_CK(kernel(b, &t, (const void *)gl_bu_list_kernel<false>, g_list, kBlock));
+        } else {
+            if (c == GL_ONE_FILL) GB_CK(kernel(b, &t, (const void *)gl_fill_kernel, g_fill, kBlock));
+            GB_CK(kernel(b, &t, one_fn[bsel], g_one, kBlock));
+        }
+    }
+    cudaGraph_t *fill_body = nullptr;
+    GB_CK(conditional(gr, &top, s.h_fill, cudaGraphCondTypeIf, 1, &fill_body));
+    cudaGraphNode_t f = nullptr;
+    GB_CK(kernel(fill_body[0], &f, (const void *)gl_fill_kernel, g_fill, kBlock));
+    GB_CK(cudaGraphInstantiate(&g->gl_exec, gr, 0));
+    g->gl_graph = gr;
+    gr = nullptr;  // owned by g now
+    return BFS_OK;
+}
+
+// Runs the traversal through the graph loop (init_kernel has already run on
+// `st`) and reads back the per-layer records.
+bfs_status run_graph_loop(bfs_graph *g, int32_t *level, int32_t *parent, int32_t root,
+                          int filled, cudaStream_t st) {
+    if (g->gl_exec && memcmp(&((const GlStatic *)g->gl_static)->cfg, &g->cfg, sizeof g->cfg) != 0)
+        destroy_graph_loop(g);  // built for another configuration
+    if (!g->gl_exec) {
+        const bfs_status bs = build_graph_loop(g);
+        if (bs != BFS_OK) return bs;
+    }
+    const GlStatic &s = *(const GlStatic *)g->gl_static;
+    GB_LAUNCH(gl_start_kernel, 1, 32, 0, st, s, level, parent, root, filled);
+    constexpr int64_t kFirst = 64;  // records fetched with the state
+    const size_t first_bytes = kGlRunBytes + (size_t)kFirst * kGlRec * 8;
+    const GlRun *hr = (const GlRun *)g->h_gl;
+    int64_t counted = 0;
+    for (int64_t launch = 0;; ++launch) {
+        if (launch > g->n / kGlCap + 2) {
+            set_error("bfs_run: graph loop did not finish after %lld launches", (long long)launch);
+            return BFS_ERR_CUDA;
+        }
+        GB_CK(cudaGraphLaunch(g->gl_exec, st));
+        GB_CK(cudaMemcpyAsync(g->h_gl, g->gl_mem, first_bytes, cudaMemcpyDeviceToHost, st));
+        GB_CK(cudaStreamSynchronize(st));
+        count_launch((int)(hr->kernels - counted) + 1);  // layer kernels and gl_begin_kernel
+        counted = hr->kernels;
+        if (hr->done || hr->status != BFS_OK) break;
+    }
+    if (hr->status != BFS_OK) {
+        set_error("bfs_run: the graph loop stopped (status %d)", hr->status);
+        return (bfs_status)hr->status;
+    }
+    const int64_t L = hr->d;
+    if (L > kFirst) {
+        const int64_t more = std::min<int64_t>(L, kSsMaxRecords) - kFirst;
+        GB_CK(cudaMemcpyAsync((char *)g->h_gl + first_bytes, (char *)g->gl_mem + first_bytes,
+                              (size_t)more * kGlRec * 8, cudaMemcpyDeviceToHost, st));
+        GB_CK(cudaStreamSynchronize(st));
+    }
+    const int64_t *recs = (const int64_t *)((const char *)g->h_gl + kGlRunBytes);
+    for (int64_t d = 0; d < L && d < kSsMaxRecords; ++d) {
+        const int64_t *rec = recs + d * kGlRec;
+        bfs_layer_stats ls;
+        memset(&ls, 0, sizeof ls);
+        ls.direction = (int32_t)rec[0];
+        ls.converted = (int32_t)rec[1];
+        ls.n_f = rec[2];
+        ls.m_f = rec[3];
+        ls.n_u = rec[4];
+        ls.m_u = rec[5];
+        ls.examined = rec[6];
+        ls.found = rec[7];
+        ls.hub_found = rec[8];
+        g->last.push_back(ls);
+    }
+    g->last_component_edges = hr->degsum / 2;
+    return BFS_OK;
+}
+
 bool is_host_ptr(const void *p) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -1563,6 +2055,7 @@ void free_graph(bfs_graph *g) {
     cudaFree(g->comp_in);
     cudaFree(g->pctl);
     if (g->h_pctl) cudaFreeHost(g->h_pctl);
+    free_graph_loop(g);
     cudaFree(g->bm_a);
     cudaFree(g->bm_b);
     cudaFree(g->pend);
@@ -1864,6 +2357,7 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
     }
     const bfs_config &cfg = g->cfg;
     const bool timing = cfg.timing != 0;
+    const bool all_events = cfg.timing == 1;  // 2: only around the hub sweeps
     auto event = [&](size_t i) -> cudaEvent_t {
         while (g->events.size() <= i) {
             cudaEvent_t e;
@@ -1908,6 +2402,8 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
     uint32_t *front = g->bm_a, *next = g->bm_b;
     int32_t *q_cur = g->q_a, *q_next = g->q_b;
     const bool dev_loop = cfg.device_loop == 1 || (cfg.device_loop == 2 && n <= kDeviceLoopAutoMaxN);
+    // the graph loop has no per-layer events: timed runs take the host loop
+    const bool graph_loop = cfg.device_loop == 3 && !timing;
     // dense bottom-up layers run in two passes on hub records
     const bool two_pass =
         cfg.bu_head == 2 &&
@@ -1922,6 +2418,9 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
     if (dev_loop) {
         const bfs_status ds = run_device_loop(g, level, parent, st);
         if (ds != BFS_OK) return ds;
+    } else if (graph_loop) {
+        const bfs_status gs = run_graph_loop(g, level, parent, root, fuse_init ? 0 : 1, st);
+        if (gs != BFS_OK) return gs;
     } else {
         {
             const bfs_status ps = publish_and_wait(g, g->trace, st);
@@ -1965,7 +2464,7 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
             int64_t *slot_next = g->trace + ((d + 1) % kRing) * kFields;
             int64_t *slot_zero = g->trace + ((d + 2) % kRing) * kFields;
             const size_t e0 = (size_t)d * 4;
-            if (timing) GB_CK(cudaEventRecord(event(e0), st));
+            if (all_events) GB_CK(cudaEventRecord(event(e0), st));
             if (!cur_bu) {
                 if (!have_queue) {
                     GB_LAUNCH(b2q_kernel, grid_cap(g->nw, kBlock * 4, 8), kBlock, 0, st, front, g->nw,
@@ -1990,7 +2489,7 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                     std::max<int64_t>(4 * (int64_t)cfg.td_warp_degree, m_f / td_warps));
                 const int td_grid = grid_cap((n_f + per_warp - 1) / per_warp, kBlock / 32,
                                              g->td_blocks_per_sm);
-                if (timing) GB_CK(cudaEventRecord(event(e0 + 1), st));
+                if (all_events) GB_CK(cudaEventRecord(event(e0 + 1), st));
                 GB_LAUNCH(td_kernel, td_grid, kBlock, 0, st, a, q_cur, n_f, per_warp, g->big,
                           (unsigned long long *)(slot_cur + T_BIG),
                           (unsigned long long *)(slot_next + T_MF), cfg.td_warp_degree, grid_deg,
@@ -2009,7 +2508,7 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                               (unsigned long long *)(slot_next + T_MF));
                 have_queue = queue_mode != 0;
             } else {
-                if (timing) GB_CK(cudaEventRecord(event(e0 + 1), st));
+                if (all_events) GB_CK(cudaEventRecord(event(e0 + 1), st));
                 // vertices still to find: unvisited and of degree > 0
                 const int64_t active = n_u - g->deg0;
                 if (cfg.bu_list_percent > 0 && active * 100 <= (int64_t)cfg.bu_list_percent * n) {
@@ -2034,6 +2533,7 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                     // the vertices whose hub missed, one lane each
                     ls.converted = 3;
                     if (!g->pend) GB_CK(cudaMalloc(&g->pend, (size_t)g->nw_pad * 4));
+                    if (timing && !all_events) GB_CK(cudaEventRecord(event(e0 + 1), st));
                     GB_LAUNCH(bu_hub_kernel, grid_cap(g->nw_pad, kBlock / 32 * 8, g->bu_hub_blocks_per_sm),
                               kBlock, 0, st, g->head, g->nw_pad, g->visited, front, next, g->pend,
                               parent, level, d + 1, (unsigned long long *)slot_next, slot_zero,
@@ -2062,7 +2562,7 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                 }
                 have_queue = false;
             }
-            if (timing) GB_CK(cudaEventRecord(event(e0 + 2), st));
+            if (all_events) GB_CK(cudaEventRecord(event(e0 + 2), st));
             {
                 const bfs_status ps = publish_and_wait(g, slot_next, st);
                 if (ps != BFS_OK) return ps;
@@ -2088,8 +2588,10 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
         if (timing) {
             for (size_t d = 0; d < g->last.size(); ++d) {
                 float t0 = 0, t1 = 0, t2 = 0;
-                cudaEventElapsedTime(&t0, g->events[4 * d], g->events[4 * d + 2]);
-                cudaEventElapsedTime(&t1, g->events[4 * d + 1], g->events[4 * d + 2]);
+                if (all_events) {
+                    cudaEventElapsedTime(&t0, g->events[4 * d], g->events[4 * d + 2]);
+                    cudaEventElapsedTime(&t1, g->events[4 * d + 1], g->events[4 * d + 2]);
+                }
                 if (g->last[d].direction == 1 && g->last[d].converted == 3)
                     cudaEventElapsedTime(&t2, g->events[4 * d + 1], g->events[4 * d + 3]);
                 g->last[d].ms_total = t0;

@@ -62,6 +62,12 @@ struct bfs_graph {
     int bu_list_blocks_per_sm = 1;
     int persist_blocks_per_sm = 0;  // device-loop kernel, 0 = not queried yet
     int64_t *pctl = nullptr, *h_pctl = nullptr;  // device-loop layer records
+    // graph loop (device_loop = 3): instantiated graph, its device state and
+    // records (gl_mem), their pinned host copy, and the kernels' fixed
+    // arguments (host heap); built on first use, dropped on a config change
+    cudaGraph_t gl_graph = nullptr;
+    cudaGraphExec_t gl_exec = nullptr;
+    void *gl_mem = nullptr, *h_gl = nullptr, *gl_static = nullptr;
     MsState *ms = nullptr;
 };
 

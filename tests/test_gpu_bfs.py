@@ -69,7 +69,7 @@ FORCED = {"td": [0], "bu": [1], "alt": [0, 1] * 32, "alt2": [1, 0] * 32,
                                   "union", "single", "ragged"])
 @pytest.mark.parametrize("pat", list(FORCED))
 @pytest.mark.parametrize("prune", [0, 1])
-@pytest.mark.parametrize("loop", [0, 1])
+@pytest.mark.parametrize("loop", [0, 1, 3])
 def test_closed_form_graphs_forced_directions(name, pat, prune, loop):
     if name == "path":
         n, (s, d) = 77, inputs.path_edges(77)
@@ -111,7 +111,8 @@ def test_policies_on_skewed_graphs(seed, policy, claim):
         n = 1 << (12 + seed // 2)
     o_off, o_idx, g = make(n, s, d, policy=policy, td_claim=claim, bu_words=[1, 2, 4][seed % 3],
                            bu_head=(seed // 2 + claim) % 3, prune_components=(seed + claim) % 2,
-                           bu_list_percent=[0, 10, 100][(seed + claim) % 3], device_loop=claim)
+                           bu_list_percent=[0, 10, 100][(seed + claim) % 3],
+                           device_loop=[0, 1, 3][(seed + 2 * claim) % 3])
     for r in oracle.sample_roots(o_off, n, seed, 4):
         check_run(o_off, o_idx, g, int(r), policy=policy)
 
@@ -141,7 +142,12 @@ def test_degree_bin_boundaries(deg, pat):
                 dict(forced=forced, bu_head=2, bu_probe=1, bu_words=4),
                 dict(forced=forced, bu_head=2, bu_list_percent=100, bu_probe=1),
                 dict(forced=forced, bu_head=2, device_loop=1),
-                dict(forced=forced, bu_head=2, device_loop=1, bu_list_percent=100)]:
+                dict(forced=forced, bu_head=2, device_loop=1, bu_list_percent=100),
+                dict(forced=forced, device_loop=3),
+                dict(forced=forced, device_loop=3, bu_list_percent=100, td_grid_degree=64),
+                dict(forced=forced, bu_head=2, device_loop=3, bu_probe=2),
+                dict(forced=forced, bu_head=1, bu_words=4, device_loop=3),
+                dict(forced=forced, bu_head=0, bu_words=1, device_loop=3, td_claim=0)]:
         o_off, o_idx, g = make(n, s, d, **cfg)
         for r in [0, 1, n - 1, deg // 2]:
             check_run(o_off, o_idx, g, r, forced=forced)
@@ -184,10 +190,17 @@ def test_rmat_scale16_all_64_roots():
         g.set_config(config(device_loop=0, bu_head=head))
         for r in roots[:16]:
             check_run(o_off, o_idx, g, int(r))
+    g.set_config(config(device_loop=3))     # the graph loop, rebuilt per configuration
+    for r in roots:
+        check_run(o_off, o_idx, g, int(r))
+    for head in (0, 1):
+        g.set_config(config(device_loop=3, bu_head=head))
+        for r in roots[:16]:
+            check_run(o_off, o_idx, g, int(r))
 
 
 @pytest.mark.parametrize("pat", ["td", "late_bu", "alt"])
-@pytest.mark.parametrize("loop", [0, 1])
+@pytest.mark.parametrize("loop", [0, 1, 3])
 def test_large_top_down_layers(pat, loop):
     # forced top-down layers with more than 2^18 frontier edges leave only the
     # next bitmap, and with many vertices still findable they defer level
@@ -202,13 +215,14 @@ def test_large_top_down_layers(pat, loop):
 
 @pytest.mark.parametrize("cfg", [dict(), dict(forced=[0, 0, 1]), dict(forced=[1]),
                                  dict(bu_list_percent=100), dict(forced=[0])])
-def test_outputs_written_by_first_sweep(cfg):
+@pytest.mark.parametrize("loop", [0, 3])
+def test_outputs_written_by_first_sweep(cfg, loop):
     # scale 21 with the host loop: dense bottom-up layers run in two passes
     # and (td_claim = 1) the first hub sweep writes the -1 of every vertex not
     # reached before it; traversals without such a sweep (top-down only,
     # list layers first, a degree-0 root, a small component) fill at the end
     n, o_off, o_idx, g_off, g_idx = _rmat_both(21, 16, 7)
-    full = dict(device_loop=0, td_claim=1, **cfg)
+    full = dict(device_loop=loop, td_claim=1, **cfg)
     g = gb.Graph(g_off, g_idx, config(**full))
     deg = np.diff(o_off)
     ref_big = oracle.bfs(o_off, o_idx, int(np.argmax(deg)))[0]
@@ -257,7 +271,7 @@ def test_host_output_buffers_match_device():
     assert oracle.check_parents(o_off, o_idx, r, lv_h.numpy(), pa_h.numpy()) == 0
 
 
-@pytest.mark.parametrize("loop", [0, 1])
+@pytest.mark.parametrize("loop", [0, 1, 3])
 def test_host_async_outputs(loop):
     # host_async: each run returns once its traversal is done; the copies of
     # two runs may still be in flight and all land by sync()
@@ -416,11 +430,20 @@ def test_scale26_levels_and_min_parents_exact(rmat26):
     level = torch.empty(n, dtype=torch.int32, device="cuda")
     parent = torch.empty(n, dtype=torch.int32, device="cuda")
     gm = gb.Graph(off, idx, config(parent_min=1), borrow=True)
+    g3 = gb.Graph(off, idx, config(device_loop=3), borrow=True)
     for e in gold["exact"]:
         r = e["root"]
+        g3.run(r, level, parent)                # the graph loop
+        torch.cuda.synchronize()
+        assert _sha(level) == e["levels_sha256"], f"graph loop levels of root {r}"
+        layers3 = g3.stats().layers
         g.run(r, level, parent)
         torch.cuda.synchronize()
         assert _sha(level) == e["levels_sha256"], f"levels of root {r}"
+        keys = ("direction", "converted", "n_f", "m_f", "n_u", "m_u", "examined", "found",
+                "hub_found")
+        assert [{k: x[k] for k in keys} for x in layers3] == \
+            [{k: x[k] for k in keys} for x in g.stats().layers]
         ce = _full_check(off, idx, src, r, level, parent, minimal=False)
         assert ce == e["component_edges"] == g.stats().component_edges
         sizes = torch.bincount(level[level >= 0].long()).tolist()
@@ -459,7 +482,7 @@ def _reversed_rows(o_off, o_idx):
     return idx
 
 
-@pytest.mark.parametrize("loop", [0, 1])
+@pytest.mark.parametrize("loop", [0, 1, 3])
 @pytest.mark.parametrize("rows", ["sorted", "reversed"])
 def test_parent_min_matches_oracle(loop, rows):
     # parent_min: every reached vertex's parent is its smallest neighbour one
@@ -519,3 +542,53 @@ def test_parent_min_host_outputs():
             ref, _ = oracle.bfs(o_off, o_idx, r)
             assert np.array_equal(lv.numpy(), ref)
             assert np.array_equal(pa.numpy(), oracle.min_parent(o_off, o_idx, r, ref))
+
+
+@pytest.mark.parametrize("pat", ["td", "bu", "alt"])
+def test_graph_loop_runs_past_its_layer_cap(pat):
+    # a path of 600 vertices has up to 599 layers: the graph loop stops every
+    # 256 layers and is launched again until the traversal ends
+    n = 600
+    o_off, o_idx, g = make(n, *inputs.path_edges(n), forced=FORCED[pat], device_loop=3)
+    for r in (0, 299, n - 1):
+        check_run(o_off, o_idx, g, r, forced=FORCED[pat])
+    g.run(0)
+    assert len(g.stats().layers) == n
+
+
+@pytest.mark.parametrize("scale", [20, 21])
+def test_graph_loop_layer_records_equal_host_loop(scale):
+    # the same decisions and the same per-layer variant (queue rebuilt,
+    # list, two-pass) and hub hits as the host-driven loop
+    n, o_off, o_idx, g_off, g_idx = _rmat_both(scale, 16, 3)
+    gh = gb.Graph(g_off, g_idx, config(device_loop=0))
+    g3 = gb.Graph(g_off, g_idx, config(device_loop=3))
+    for r in oracle.sample_roots(o_off, n, 11, 6):
+        lh, ph = run_gpu(gh, int(r))
+        l3, p3 = run_gpu(g3, int(r))
+        assert np.array_equal(lh, l3)
+        assert oracle.check_parents(o_off, o_idx, int(r), l3, p3) == 0
+        keys = ("direction", "converted", "n_f", "m_f", "n_u", "m_u", "examined", "found",
+                "hub_found")
+        assert [{k: x[k] for k in keys} for x in g3.stats().layers] == \
+            [{k: x[k] for k in keys} for x in gh.stats().layers]
+
+
+def test_timing_modes():
+    # timing 1: events around every layer; 2: only around the hub sweeps
+    n, o_off, o_idx, g_off, g_idx = _rmat_both(21, 16, 7)
+    r = int(oracle.sample_roots(o_off, n, 9, 1)[0])
+    g = gb.Graph(g_off, g_idx, config(device_loop=0, timing=1))
+    lv1, _ = run_gpu(g, r)
+    L1 = g.stats().layers
+    assert all(x["ms_total"] > 0 for x in L1)
+    assert any(x["converted"] == 3 for x in L1)
+    g.set_config(config(device_loop=0, timing=2))
+    lv2, _ = run_gpu(g, r)
+    L2 = g.stats().layers
+    assert np.array_equal(lv1, lv2)
+    for x in L2:
+        assert x["ms_total"] == 0 and x["ms_main"] == 0
+        assert (x["ms_sweep"] > 0) == (x["converted"] == 3)
+    with pytest.raises(gb.BfsError):
+        g.set_config(config(timing=3))
