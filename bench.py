@@ -52,9 +52,13 @@ def parse():
                         "serve: the serving stream over 8 resident graphs; "
                         "batch: one batched configuration timed alone")
     p.add_argument("--batch-k", type=int, default=512, help="roots per batch (--mode batch)")
-    p.add_argument("--no-batch", action="store_true", help="skip the batched comparison")
+    p.add_argument("--no-batch", action="store_true",
+                   help="skip the batched comparison, the Table 3 analogue and the layer-loop "
+                        "comparison")
     p.add_argument("--device-loop", type=int, default=2, choices=[0, 1, 2, 3],
-                   help="bfs_config.device_loop: 0 host loop, 1 device loop, 2 library default")
+                   help="bfs_config.device_loop: 0 host loop, 1 persistent device loop, "
+                        "2 library default, 3 graph loop (the timed region records hub-sweep "
+                        "events, so 3 falls back to the host loop there)")
     p.add_argument("--batch-scale", type=int, default=22)
     p.add_argument("--serve-queries", type=int, default=10000)
     p.add_argument("--serve-seconds", type=float, default=4.0,
