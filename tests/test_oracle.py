@@ -558,6 +558,38 @@ def test_min_parent_brute_force():
         assert mp[v] == exp
 
 
+def test_min_parent_closed_forms():
+    # grid rows x cols rooted at cell 0: the neighbours one level up of cell
+    # (r, c) are (r-1, c) and (r, c-1); the smaller id is the cell above
+    # unless r = 0
+    rows, cols = 9, 13
+    off, idx = csr(rows * cols, *inputs.grid_edges(rows, cols))
+    lv, _ = oracle.bfs(off, idx, 0)
+    mp = oracle.min_parent(off, idx, 0, lv)
+    for v in range(1, rows * cols):
+        assert mp[v] == (v - cols if v >= cols else v - 1)
+    # hypercube rooted at 0: v's neighbours one level up clear one set bit;
+    # the smallest clears the highest one
+    dim = 7
+    off, idx = csr(1 << dim, *inputs.hypercube_edges(dim))
+    lv, _ = oracle.bfs(off, idx, 0)
+    mp = oracle.min_parent(off, idx, 0, lv)
+    for v in range(1, 1 << dim):
+        assert mp[v] == v ^ (1 << (v.bit_length() - 1))
+    # path rooted at r: the neighbour toward r
+    n, r = 40, 17
+    off, idx = csr(n, *inputs.path_edges(n))
+    lv, _ = oracle.bfs(off, idx, r)
+    mp = oracle.min_parent(off, idx, r, lv)
+    assert mp[r] == r
+    assert all(mp[v] == (v - 1 if v > r else v + 1) for v in range(n) if v != r)
+    # the row order does not matter
+    rev = idx.copy()
+    for v in range(n):
+        rev[off[v]:off[v + 1]] = idx[off[v]:off[v + 1]][::-1]
+    assert np.array_equal(oracle.min_parent(off, rev, r, lv), mp)
+
+
 def test_component_edges_closed_forms():
     n, s, d = inputs.union((10, *inputs.path_edges(10)), (6, *inputs.complete_edges(6)))
     off, idx = csr(n, s, d)
