@@ -47,10 +47,12 @@ def parse():
     p.add_argument("--cpu-scale", type=int, default=20,
                    help="scale of the oracle's bounded sample graph")
     p.add_argument("--cpu-roots", type=int, default=8)
-    p.add_argument("--mode", default="single", choices=["single", "serve", "batch"],
+    p.add_argument("--mode", default="single", choices=["single", "serve", "batch", "study"],
                    help="single: the headline line (single-source + batched); "
                         "serve: the serving stream over 8 resident graphs; "
-                        "batch: one batched configuration timed alone")
+                        "batch: one batched configuration timed alone; "
+                        "study: the switch-policy trace (Table 2 form) and the "
+                        "scale x edgefactor sweep (Figure 3 form)")
     p.add_argument("--batch-k", type=int, default=512, help="roots per batch (--mode batch)")
     p.add_argument("--no-batch", action="store_true",
                    help="skip the batched comparison, the Table 3 analogue and the layer-loop "
@@ -360,6 +362,101 @@ def batched_comparison(gb, torch, scale, seed=1, root_seed=4, ks=(64, 128, 256, 
     return out
 
 
+def run_study(args):
+    """Two studies of the paper's evaluation, one JSON line.
+
+    table2: one root at SCALE 18, edgefactor 16, run under the vertex policy
+    read off Table 2 (f = n_u / 1024, g = n / 64 on the frontier size) and
+    under the edge policy (the defaults): per layer the frontier size v_f,
+    the unvisited count n_u, f, g, the direction taken and the layer's device
+    time, and the run's TEPS.
+    sweep: R-MAT and the Erdos-Renyi control at SCALE 14-22 and edgefactor
+    16, 32, 64 (the axes of Figure 3), 16 roots each, harmonic-mean GTEPS of
+    the hybrid (edge policy), top-down only and bottom-up from the first
+    layer on."""
+    import torch
+    import paper_1704_02259_gb300 as gb
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+
+    def timed(g, roots, level, parent):
+        for r in roots[:2]:
+            g.run(r, level, parent)
+        teps = []
+        for r in roots:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.run(r, level, parent)
+            e1.record(stream)
+            e1.synchronize()
+            teps.append(g.stats().component_edges / (e0.elapsed_time(e1) / 1e3))
+        return hmean(teps) / 1e9
+
+    def forced(pattern):
+        c = gb.default_config()
+        c.policy = gb.POLICY_FORCED
+        c.forced_len = len(pattern)
+        for i, x in enumerate(pattern):
+            c.forced[i] = x
+        return c
+
+    out = {"metric": "policy trace and scale sweep", "mode": "study", "n_gpus": 1,
+           "data": "synthetic", "dtype": "int32"}
+    # Table 2 form
+    n = 1 << 18
+    off, idx = gb.rmat_graph(18, 16, 1)
+    root = gb.sample_roots(off, n, 2, 1).tolist()[0]
+    level = torch.empty(n, dtype=torch.int32, device="cuda")
+    parent = torch.empty_like(level)
+    t2 = {"workload": "rmat-scale18-ef16, one root", "root": root}
+    for name, policy in (("vertex", gb.POLICY_VERTEX), ("edge", gb.POLICY_EDGE)):
+        c = gb.default_config()
+        c.policy = policy
+        c.device_loop = 0
+        c.timing = 1
+        g = gb.Graph(off, idx, c)
+        for _ in range(3):
+            g.run(root, level, parent)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.run(root, level, parent)
+        e1.record(stream)
+        e1.synchronize()
+        st = g.stats()
+        rows = [{"layer": d + 1, "v_f": L["n_f"], "n_u": L["n_u"], "f": L["n_u"] >> 10,
+                 "g": n >> 6, "approach": "BU" if L["direction"] else "TD",
+                 "ms": round(L["ms_total"], 4)} for d, L in enumerate(st.layers)]
+        t2[name] = {"layers": rows,
+                    "gteps": st.component_edges / (e0.elapsed_time(e1) / 1e3) / 1e9}
+        g.close()
+    out["table2"] = t2
+    del off, idx, level, parent
+    # Figure 3 form
+    sweep = []
+    for kind_name, kind in (("rmat", gb.GEN_RMAT), ("er", gb.GEN_ER)):
+        for scale in (14, 16, 18, 20, 22):
+            for ef in (16, 32, 64):
+                n = 1 << scale
+                off, idx = gb.rmat_graph(scale, ef, 1, kind=kind)
+                roots = gb.sample_roots(off, n, 2, 16).tolist()
+                level = torch.empty(n, dtype=torch.int32, device="cuda")
+                parent = torch.empty_like(level)
+                row = {"graph": kind_name, "scale": scale, "edgefactor": ef,
+                       "nnz": idx.numel()}
+                for name, cfg in (("hybrid", gb.default_config()), ("top_down", forced([0])),
+                                  ("bottom_up", forced([1]))):
+                    g = gb.Graph(off, idx, cfg)
+                    row[name + "_gteps"] = timed(g, roots, level, parent)
+                    g.close()
+                sweep.append(row)
+                del off, idx, level, parent
+                torch.cuda.empty_cache()
+    out["sweep"] = sweep
+    print(json.dumps(out), flush=True)
+
+
 def run_batch_mode(args):
     """One batched configuration timed alone (R-MAT --batch-scale, --batch-k
     roots, the default batch configuration, host-driven layers): W untimed
@@ -476,6 +573,9 @@ def run_serve(args):
 
 def main():
     args = parse()
+    if args.mode == "study":
+        run_study(args)
+        return
     if args.mode == "serve":
         run_serve(args)
         return
