@@ -77,6 +77,27 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def hub_sweep_bytes(n, probed, written):
+    """Algorithmic bytes of one hub sweep launch: the visited words read and
+    the next, pend and visited words written (n/8 bytes each), one 8-byte
+    head record per probed vertex (unvisited, degree >= 1), and 8 bytes
+    (parent, level) per written vertex: the hub hits, or in the first sweep
+    of a traversal every vertex not reached before it."""
+    return n / 2 + 8 * probed + 8 * written
+
+
+def one_sweep_bytes(n, nnz):
+    """The one-sweep model: every CSR index and row bound read once, the
+    frontier and visited bitmaps once each, level and parent written once."""
+    return 4 * nnz + 8 * (n + 1) + 2 * n / 8 + 8 * n
+
+
+def roofline_teps(m_c, peak_gbs, bytes_per_bfs):
+    """TEPS of a traversal that moves bytes_per_bfs at peak_gbs GB/s and
+    counts m_c edges."""
+    return m_c * peak_gbs * 1e9 / bytes_per_bfs
+
+
 def measured_traffic(scale, edgefactor):
     """DRAM bytes per hub sweep launch from the committed ncu summary, or None
     when the workload differs or the kernel changed since the capture (the
@@ -683,7 +704,7 @@ def main():
             if L["direction"] == 1 and L["converted"] == 3:
                 written = L["n_u"] if first_sweep else L["hub_found"]
                 first_sweep = False
-                hub_bytes += n / 2 + 8 * active + 8 * written
+                hub_bytes += hub_sweep_bytes(n, active, written)
                 hub_ms += L["ms_sweep"]
                 n_hub += 1
     # the other kernels' sections: one untimed pass over the same roots with
@@ -774,8 +795,8 @@ def main():
     peak, peak_kind = peaks()
     achieved = (hub_bytes / (hub_ms / 1e3)) / 1e9 if hub_ms > 0 else 0.0
     m_c = statistics.median(edges)
-    b_sweep = 4 * nnz + 8 * (n + 1) + 2 * n / 8 + 8 * n
-    roof_teps = m_c * peak * 1e9 / b_sweep
+    b_sweep = one_sweep_bytes(n, nnz)
+    roof_teps = roofline_teps(m_c, peak, b_sweep)
     line = {
         "metric": METRIC, "value": value / 1e9, "unit": "GTEPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
