@@ -205,15 +205,18 @@ __global__ void rows_sorted_kernel(const int64_t *__restrict__ off,
 }
 
 // Smallest-id parent one level up for every reached vertex other than the
-// root (parent_min). A lane per vertex tests the first 8 row entries; longer
-// rows still open are finished by the whole warp, 32 entries per round. With
-// ascending rows the first neighbour at level - 1 is the smallest and ends the
-// scan; otherwise the whole row is scanned for the minimum.
+// root (parent_min); a vertex at level 1 takes the root, the only vertex at
+// level 0. A lane per vertex tests the first P row entries itself,
+// B at a time (B index loads, then B level loads, all independent); rows
+// still open after P entries are finished by the whole warp, 32 entries per
+// round. With ascending rows the first neighbour at level - 1 is the
+// smallest and ends the scan; otherwise the whole row is scanned for the
+// minimum.
 __global__ void __launch_bounds__(kBlock) min_parent_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
     const int32_t *__restrict__ level, int32_t *__restrict__ parent, int64_t n, int32_t root,
     int sorted) {
-    constexpr int P = 8;
+    constexpr int P = 32, B = 8;
     const unsigned lane = lane_id();
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -226,15 +229,23 @@ __global__ void __launch_bounds__(kBlock) min_parent_kernel(
             b = off[v];
             e = off[v + 1];
         }
-        int32_t best = 0x7fffffff;
-        bool done = !active;
-        for (int q = 0; q < P && !done; ++q) {
-            if (b + q >= e) break;
-            const int32_t u = __ldg(idx + b + q);
-            if (__ldg(level + u) == lv - 1) {
-                best = u < best ? u : best;
-                if (sorted) done = true;
-            }
+        // level 1: the root is the only vertex one level up (no scan; a hub
+        // next to the root would otherwise scan its row up to the root's id)
+        int32_t best = active && lv == 1 ? root : 0x7fffffff;
+        bool done = !active || lv == 1;
+        for (int q0 = 0; q0 < P; q0 += B) {
+            if (done || b + q0 >= e) break;
+            int32_t u[B], lu[B];
+#pragma unroll
+            for (int t = 0; t < B; ++t) u[t] = b + q0 + t < e ? __ldg(idx + b + q0 + t) : -1;
+#pragma unroll
+            for (int t = 0; t < B; ++t) lu[t] = u[t] >= 0 ? __ldg(level + u[t]) : -2;
+#pragma unroll
+            for (int t = 0; t < B; ++t)
+                if (!done && lu[t] == lv - 1) {  // lv - 1 >= 0, so u[t] >= 0 here
+                    best = u[t] < best ? u[t] : best;
+                    if (sorted) done = true;
+                }
         }
         unsigned pend = __ballot_sync(0xffffffffu, !done && e - b > P);
         while (pend) {
