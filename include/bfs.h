@@ -259,18 +259,22 @@ BFS_API bfs_status bfs_graph_destroy(bfs_graph *g);
 /* Hybrid BFS from `root` (Alg. 3). level_out / parent_out are n int32 each,
  * caller-owned, either both device memory or both host memory (pageable or
  * pinned); parent_out may be NULL. With host buffers the results are copied
- * back before return. Work is ordered on `stream`; the host reads the layer
- * counters after every layer to choose the next direction, so the call
+ * back before return (cfg.host_async: the copy may still run, see
+ * bfs_graph_sync). Work is ordered on `stream`, and the direction of each
+ * layer is chosen from the layer counters by the host (host loop) or on the
+ * device (device and graph loops, cfg.device_loop); either way the call
  * returns after the traversal has finished. Parents found by a bottom-up
- * layer are the first frontier neighbour in CSR order (Alg. 2); parents found
- * by a top-down layer are whichever frontier neighbour claimed the vertex
- * first (any valid tree, Sec. 7.1). */
+ * layer are the vertex's hub when it is in the frontier (bu_head = 2), else
+ * the first frontier neighbour in CSR order (Alg. 2); parents found by a
+ * top-down layer are whichever frontier neighbour claimed the vertex first
+ * (any valid tree, Sec. 7.1); cfg.parent_min replaces them all by the
+ * smallest-id neighbour one level up. */
+BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level_out, int32_t *parent_out,
+                           void *stream);
+
 /* Waits for the host copies that bfs_run left in flight (cfg.host_async) and
  * returns the first error among them; BFS_OK when none is pending. */
 BFS_API bfs_status bfs_graph_sync(bfs_graph *g);
-
-BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level_out, int32_t *parent_out,
-                           void *stream);
 
 /* Per-layer record of the last bfs_run on this graph. Layer d is the
  * frontier of the vertices at level d. Counters follow Sec. 4: v_f (n_f),
@@ -291,11 +295,12 @@ typedef struct bfs_layer_stats {
                            bottom-up                                           */
     int64_t found;      /* vertices of the next layer                          */
     float ms_total;     /* layer time, when cfg.timing = 1 (else 0)            */
-    float ms_main;      /* time of the layer's main step kernel(s)            */
-    float ms_sweep;     /* converted = 3: time of the hub sweep pass alone    */
+    float ms_main;      /* time of the layer's main step kernel(s), timing = 1 */
+    float ms_sweep;     /* converted = 3: time of the hub sweep pass alone,
+                           timing = 1 or 2                                     */
     float pad;
-    int64_t hub_found;  /* converted = 3: vertices found by their hub (host
-                           loop only; 0 in the device loop)                    */
+    int64_t hub_found;  /* converted = 3: vertices found by their hub (host and
+                           graph loops; 0 in the persistent device loop)       */
 } bfs_layer_stats;
 
 /* Copies up to `cap` layer records of the last run into `out`; *layers gets
