@@ -86,3 +86,36 @@ def test_graph_and_run_reject_bad_arguments(lib):
     assert lib.bfs_run(None, 0, buf, buf, None) == 1
     assert lib.bfs_graph_destroy(None) == 0
     assert lib.bfs_last_run_stats(None, None, 0, None, None) == 1
+
+
+STRUCTS = {"Config": "bfs_config", "LayerStats": "bfs_layer_stats",
+           "BatchConfig": "bfs_batch_config", "BatchLayerStats": "bfs_batch_layer_stats",
+           "ServeConfig": "bfs_serve_config", "ServeStats": "bfs_serve_stats"}
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    # a C program compiled against include/bfs.h prints every field's offset
+    # and every struct's size; the ctypes classes must agree exactly
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "bfs.h"', "int main(void) {"]
+    for py, c in STRUCTS.items():
+        cls = getattr(gb, py)
+        lines.append(f'printf("{py} size %zu\\n", sizeof({c}));')
+        for name, _ in cls._fields_:
+            lines.append(f'printf("{py} {name} %zu\\n", offsetof({c}, {name}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    for line in out.splitlines():
+        py, field, value = line.split()
+        cls = getattr(gb, py)
+        got = ctypes.sizeof(cls) if field == "size" else getattr(cls, field).offset
+        assert got == int(value), (py, field, got, value)
