@@ -271,6 +271,26 @@ def first_frontier_neighbour(off, idx, lv, v):
     return None
 
 
+def trace_errors(off, ref, tr):
+    """Mismatches between the hybrid run's per-layer counters and their
+    definitions (Sec. 4, Alg. 3's getCounters), computed from the FIFO BFS
+    levels `ref`: in layer d, v_f = |layer d|, e_f = the degree sum of layer
+    d, n_u = the number of vertices outside layers 0..d (the unvisited set
+    once layer d is marked), e_u (m_u) = the degree sum of those same
+    vertices, and the layer finds |layer d+1| vertices. Returns a list of (layer, column) pairs that disagree."""
+    dg = deg(off)
+    bad = []
+    for dd in range(tr.shape[0]):
+        layer = ref == dd
+        later = (ref > dd) | (ref < 0)        # not yet visited after layer d is marked
+        want = [layer.sum(), dg[layer].sum(), later.sum(), dg[later].sum(), None,
+                (ref == dd + 1).sum()]
+        for c, w in enumerate(want):
+            if w is not None and tr[dd, c] != w:
+                bad.append((dd, c))
+    return bad
+
+
 @pytest.mark.parametrize("seed", range(12))
 def test_hybrid_levels_and_parents_under_any_policy(seed):
     rng = np.random.default_rng(seed)
@@ -296,11 +316,8 @@ def test_hybrid_levels_and_parents_under_any_policy(seed):
         assert (lv == ref).all()
         check_tree(off, idx, root, lv, pa)
         assert len(dirs) == depth + 1
+        assert trace_errors(off, ref, tr) == []
         for dd in range(depth + 1):
-            layer = np.nonzero(ref == dd)[0]
-            assert tr[dd, 0] == layer.size                         # v_f
-            assert tr[dd, 1] == deg(off)[layer].sum()               # e_f
-            assert tr[dd, 2] == (ref > dd).sum() + (ref < 0).sum()  # n_u
             if dirs[dd] == 1:
                 # bottom-up parents are the first frontier hit in CSR order
                 nxt = np.nonzero(ref == dd + 1)[0]
@@ -308,6 +325,36 @@ def test_hybrid_levels_and_parents_under_any_policy(seed):
                     assert pa[v] == first_frontier_neighbour(off, idx, ref, v)
         if forced is not None:
             assert list(dirs) == [forced[min(i, len(forced) - 1)] for i in range(depth + 1)]
+
+
+def test_trace_check_rejects_planted_counter_mistakes():
+    """The counter check above catches the plausible slips in the e_u (m_u)
+    and found columns: e_u that still holds the root's degree, e_u reduced by
+    the current frontier's degrees instead of the next one's, and found
+    off by one layer."""
+    s, d = oracle.gen_edges(oracle.RMAT, 10, 8, 3)
+    n = 1 << 10
+    off, idx = csr(n, s, d)
+    root = int(np.argmax(deg(off)))
+    ref, _ = oracle.bfs(off, idx, root)
+    lv, _, dirs, tr = oracle.hybrid_bfs(off, idx, root, oracle.POLICY_EDGE)
+    assert trace_errors(off, ref, tr) == []
+    dg = deg(off)
+    # 1: the root's degree never removed from e_u
+    t1 = tr.copy()
+    t1[:, 3] += dg[root]
+    assert {c for _, c in trace_errors(off, ref, t1)} == {3}
+    # 2: e_u reduced by the frontier being processed, not the one found
+    t2 = tr.copy()
+    m_u = int(off[-1]) - dg[root]
+    for dd in range(tr.shape[0]):
+        t2[dd, 3] = m_u
+        m_u -= tr[dd, 1] if dd > 0 else 0
+    assert any(c == 3 for _, c in trace_errors(off, ref, t2))
+    # 3: found reported as this layer's size instead of the next one's
+    t3 = tr.copy()
+    t3[:, 5] = tr[:, 0]
+    assert {c for _, c in trace_errors(off, ref, t3)} == {5}
 
 
 def test_hybrid_bottom_up_examined_edges_brute_force():
