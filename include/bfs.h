@@ -47,7 +47,8 @@ typedef enum bfs_status {
     BFS_ERR_TIMEOUT = 4,   /* a bounded device-side wait ran out            */
     BFS_ERR_DEPTH = 5,     /* an int8 level would exceed 127                */
     BFS_ERR_BUSY = 6,      /* the server has no room for the request        */
-    BFS_ERR_SHUTDOWN = 7   /* the server is shutting down                   */
+    BFS_ERR_SHUTDOWN = 7,  /* the server is shutting down                   */
+    BFS_ERR_INTERNAL = 8   /* the library's own consistency check failed   */
 } bfs_status;
 
 /* Message for the last failed call made by this thread ("" if none). */
@@ -213,6 +214,16 @@ typedef struct bfs_config {
                                 which is checked once): about 12.5 ms per BFS
                                 on a scale-26 R-MAT graph, whose hubs one level
                                 below few candidates scan long rows            */
+    int32_t hub_stream_stages; /* two-pass bottom-up layers: the hub sweep of a
+                                dense layer reads the head records of tiles of
+                                1024 vertices through bulk copies into shared
+                                memory, this many tiles in flight per block
+                                (2, 3, 4, 6 or 8); 0 = never (every sweep
+                                gathers the records of unvisited vertices).
+                                Results are the same either way              */
+    int32_t hub_stream_percent; /* a hub sweep streams when at least this
+                                percentage of n vertices is still to find
+                                (unvisited, degree > 0); 0..100              */
 } bfs_config;
 
 /* Fills `cfg` with the defaults (edge policy, alpha 20, beta 200, hub head
@@ -476,13 +487,20 @@ BFS_API bfs_status bfs_serve_destroy(bfs_server *s);
  * array compiled into the library (about 12.5 MiB on every GPU that loads
  * the library, held until the process exits).
  *   offsets, indices   device CSR (layout above), caller-owned, n <= 2^20
+ *   nnz                must equal offsets[n] (read back and checked before
+ *                      any launch: it seeds the e_u counter of the switch)
  *   level_out, parent_out   device, n int32 each, caller-owned (both needed)
- * n above 2^20 gives BFS_ERR_INVALID. The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress) with that device current.
- * Every call overwrites the part of the array it reads before reading it, so
- * nothing of a previous call leaks in; but all calls share the one array, so
- * calls whose work overlaps on the GPU (other streams, other host threads)
- * race and must be serialised by the caller. Synchronous like bfs_run.
+ * n above 2^20, or nnz != offsets[n], gives BFS_ERR_INVALID. The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture
+ * begins. Every call overwrites the part of the array it reads before
+ * reading it, so nothing of a previous call leaks in; but all calls share
+ * the one array, so calls whose work overlaps on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller.
+ * Synchronous like bfs_run: it returns after the traversal, and on an error
+ * it first drains `stream`, so no work of the call is left in flight. A
+ * traversal whose counters never reach an empty frontier within n layers
+ * returns BFS_ERR_INTERNAL.
  * Makes no cudaMalloc, cudaMallocAsync, cudaMallocHost or cudaFree call. */
 BFS_API bfs_status bfs_run_noalloc(const int64_t *offsets, const int32_t *indices, int64_t n,
                                    int64_t nnz, int32_t root, int32_t *level_out,

@@ -17,7 +17,8 @@ from . import _build
 
 BFS_OK = 0
 STATUS = {0: "BFS_OK", 1: "BFS_ERR_INVALID", 2: "BFS_ERR_OOM", 3: "BFS_ERR_CUDA",
-          4: "BFS_ERR_TIMEOUT", 5: "BFS_ERR_DEPTH", 6: "BFS_ERR_BUSY", 7: "BFS_ERR_SHUTDOWN"}
+          4: "BFS_ERR_TIMEOUT", 5: "BFS_ERR_DEPTH", 6: "BFS_ERR_BUSY", 7: "BFS_ERR_SHUTDOWN",
+          8: "BFS_ERR_INTERNAL"}
 
 GEN_RMAT = 0
 GEN_ER = 1
@@ -45,7 +46,8 @@ class Config(ctypes.Structure):
                 ("td_claim", ctypes.c_int32), ("bu_head", ctypes.c_int32),
                 ("prune_components", ctypes.c_int32), ("bu_list_percent", ctypes.c_int32),
                 ("device_loop", ctypes.c_int32), ("host_async", ctypes.c_int32),
-                ("parent_min", ctypes.c_int32)]
+                ("parent_min", ctypes.c_int32), ("hub_stream_stages", ctypes.c_int32),
+                ("hub_stream_percent", ctypes.c_int32)]
 
 
 class LayerStats(ctypes.Structure):

@@ -1140,6 +1140,187 @@ __global__ void __launch_bounds__(kBlock, 4) bu_hub_kernel(
                         slot_next, zero_slot, init_out, base, n, root);
 }
 
+// ---------------------------------------------------------------------------
+// Streaming first pass for dense sweeps. Same per-vertex work as
+// bu_hub_phase, but the head records are not gathered by the warps: the
+// block's bulk-copy engine (cp.async.bulk, completion counted in bytes on an
+// mbarrier) streams every record of a tile of kHubTileWords bitmap words
+// (1024 vertices, 8 KB), with the tile's visited and base words, into shared
+// memory S tiles ahead. The warps then only make the frontier-bit loads (L2)
+// and the stores, so the one dependent global load per vertex is the
+// frontier word, while S - 1 tiles per block stay in flight from HBM. In a
+// dense sweep (most vertices unvisited) nearly every head sector is needed
+// anyway, so reading all of them costs little; sparse sweeps keep the
+// gathering kernel above.
+// ---------------------------------------------------------------------------
+constexpr int kHubTileWords = 32;
+constexpr int kHubTileVerts = kHubTileWords * 32;
+constexpr unsigned kHubTileBytes = kHubTileVerts * sizeof(int2);
+constexpr int kHubWordsPerWarp = kHubTileWords / (kBlock / 32);
+static_assert(kHubTileWords % (kBlock / 32) == 0, "the tile's words split evenly over the warps");
+constexpr unsigned long long kHubWaitNs = 1000000000ull;  // 1 s per bounded wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+// Makes the initialised barriers visible to the async proxy (the copy engine).
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// Global -> shared bulk copy; both addresses 16-byte aligned, bytes % 16 == 0.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the given phase parity: false once timeout_ns has passed.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity,
+                                          unsigned long long timeout_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > timeout_ns) return false;
+    return true;
+}
+
+template <int S>
+constexpr size_t hub_stream_smem() {
+    return (size_t)S * (kHubTileBytes + 2 * kHubTileWords * 4) + (size_t)S * 8;
+}
+
+template <int S>
+__global__ void __launch_bounds__(kBlock) bu_hub_stream_kernel(
+    const int2 *__restrict__ head, int64_t nw_pad, uint32_t *__restrict__ visited,
+    const uint32_t *__restrict__ front, uint32_t *__restrict__ next_bm,
+    uint32_t *__restrict__ pend, int32_t *__restrict__ parent, int32_t *__restrict__ level,
+    int32_t new_level, unsigned long long *slot_next, int64_t *zero_slot, int init_out,
+    const uint32_t *__restrict__ base, int64_t n, int32_t root) {
+    extern __shared__ __align__(128) unsigned char hub_smem[];
+    int2 *sh_head = reinterpret_cast<int2 *>(hub_smem);                        // [S][1024]
+    uint32_t *sh_vis = reinterpret_cast<uint32_t *>(sh_head + S * kHubTileVerts);  // [S][32]
+    uint32_t *sh_base = sh_vis + S * kHubTileWords;                               // [S][32]
+    uint64_t *full = reinterpret_cast<uint64_t *>(sh_base + S * kHubTileWords);   // [S]
+    if (blockIdx.x == 0 && threadIdx.x < kFields) zero_slot[threadIdx.x] = 0;
+    const int64_t tiles = nw_pad / kHubTileWords;  // nw_pad is a multiple of 32
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    // thread 0 fills stage s with tile t: head records, visited and base words
+    auto issue = [&](int64_t t, int s) {
+        mbar_expect_tx(full + s, kHubTileBytes + 2 * kHubTileWords * 4);
+        bulk_g2s(sh_head + s * kHubTileVerts, head + t * kHubTileVerts, kHubTileBytes, full + s);
+        bulk_g2s(sh_vis + s * kHubTileWords, visited + t * kHubTileWords, kHubTileWords * 4,
+                 full + s);
+        bulk_g2s(sh_base + s * kHubTileWords, base + t * kHubTileWords, kHubTileWords * 4,
+                 full + s);
+    };
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(full + s, 1);
+        mbar_init_fence();
+        for (int s = 0; s < S; ++s) {
+            const int64_t t = blockIdx.x + (int64_t)s * gridDim.x;
+            if (t < tiles) issue(t, s);
+        }
+    }
+    __syncthreads();
+    int64_t my_nf = 0, my_mf = 0, my_ex = 0;
+    int64_t i = 0;
+    for (;; ++i) {
+        const int64_t t = blockIdx.x + i * gridDim.x;
+        if (t >= tiles) break;
+        const int s = (int)(i % S);
+        const bool ok = mbar_wait(full + s, (unsigned)((i / S) & 1), kHubWaitNs);
+        if (__syncthreads_or(!ok)) {
+            // a copy never completed: flag it, let this stage's and the later
+            // stages' copies land (bounded), and leave with the block
+            if (threadIdx.x == 0) {
+                atomicExch(reinterpret_cast<unsigned long long *>(slot_next + T_ERR), 1ull);
+                for (int j = 0; j < S; ++j) {
+                    const int64_t tj = blockIdx.x + (i + j) * gridDim.x;
+                    if (tj < tiles)
+                        mbar_wait(full + (int)((i + j) % S), (unsigned)(((i + j) / S) & 1),
+                                  kHubWaitNs);
+                }
+            }
+            break;
+        }
+        const int2 *th = sh_head + s * kHubTileVerts;
+        const uint32_t *tv = sh_vis + s * kHubTileWords;
+        const uint32_t *tb = sh_base + s * kHubTileWords;
+        uint32_t vw[kHubWordsPerWarp];
+        int2 h[kHubWordsPerWarp];
+        uint32_t fw[kHubWordsPerWarp];
+#pragma unroll
+        for (int k = 0; k < kHubWordsPerWarp; ++k) {
+            const int j = warp * kHubWordsPerWarp + k;
+            vw[k] = tv[j];
+            h[k] = th[j * 32 + lane];
+            const bool unv = !((vw[k] >> lane) & 1u);  // bits past n are set
+            if (!unv) h[k].x = -1;
+        }
+#pragma unroll
+        for (int k = 0; k < kHubWordsPerWarp; ++k)
+            fw[k] = h[k].x >= 0 ? __ldg(front + (h[k].x >> 5)) : 0u;
+#pragma unroll
+        for (int k = 0; k < kHubWordsPerWarp; ++k) {
+            const int j = warp * kHubWordsPerWarp + k;
+            const int64_t w = t * kHubTileWords + j;
+            const int64_t v = w * 32 + lane;
+            const bool probed = h[k].x >= 0;
+            const bool found = probed && ((fw[k] >> (h[k].x & 31)) & 1u);
+            my_ex += probed ? (found || h[k].y > 1 ? 1 : 2) : 0;
+            if (found) {
+                parent[v] = h[k].x;
+                level[v] = new_level;
+                my_mf += h[k].y;
+                my_nf += 1;
+            } else if (init_out && v < n && v != root && !(((vw[k] & ~tb[j]) >> lane) & 1u)) {
+                parent[v] = -1;
+                level[v] = -1;
+            }
+            const unsigned fb = __ballot_sync(0xffffffffu, found);
+            const unsigned pb = __ballot_sync(0xffffffffu, probed && !found && h[k].y > 1);
+            if (lane == 0) {
+                next_bm[w] = fb;
+                pend[w] = pb;
+                if (fb) visited[w] = vw[k] | fb;
+            }
+        }
+        __syncthreads();  // every warp is done with stage s
+        if (threadIdx.x == 0) {
+            const int64_t t2 = t + (int64_t)S * gridDim.x;
+            if (t2 < tiles) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(t2, s);
+            }
+        }
+    }
+    block_add4(my_nf, my_mf, my_ex, my_nf, slot_next + T_NF, slot_next + T_MF,
+               slot_next + T_EXAM, slot_next + T_HUB);
+}
+
 __global__ void __launch_bounds__(kBlock) bu_list_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
     const int2 *__restrict__ head, int hskip,
@@ -1271,7 +1452,36 @@ bool config_ok(const bfs_config &c) {
     if (c.bu_list_percent < 0 || c.bu_list_percent > 100) return false;
     if (c.device_loop < 0 || c.device_loop > 3) return false;
     if (c.timing < 0 || c.timing > 2) return false;
+    if (c.hub_stream_stages != 0 && c.hub_stream_stages != 2 && c.hub_stream_stages != 3 &&
+        c.hub_stream_stages != 4 && c.hub_stream_stages != 6 && c.hub_stream_stages != 8)
+        return false;
+    if (c.hub_stream_percent < 0 || c.hub_stream_percent > 100) return false;
     return true;
+}
+
+// The streaming hub sweep for a stage count, its dynamic shared memory, and
+// its resident blocks per SM (queried once per graph and stage count; the
+// shared-memory limit is raised where a count needs more than the default).
+using HubStreamFn = void (*)(const int2 *, int64_t, uint32_t *, const uint32_t *, uint32_t *,
+                             uint32_t *, int32_t *, int32_t *, int32_t, unsigned long long *,
+                             int64_t *, int, const uint32_t *, int64_t, int32_t);
+HubStreamFn hub_stream_fn(int stages) {
+    switch (stages) {
+        case 2: return bu_hub_stream_kernel<2>;
+        case 3: return bu_hub_stream_kernel<3>;
+        case 4: return bu_hub_stream_kernel<4>;
+        case 6: return bu_hub_stream_kernel<6>;
+        default: return bu_hub_stream_kernel<8>;
+    }
+}
+size_t hub_stream_smem_bytes(int stages) {
+    switch (stages) {
+        case 2: return hub_stream_smem<2>();
+        case 3: return hub_stream_smem<3>();
+        case 4: return hub_stream_smem<4>();
+        case 6: return hub_stream_smem<6>();
+        default: return hub_stream_smem<8>();
+    }
 }
 
 // Alg. 3 switch, read as hysteresis (Table 2 layer 5 rules out the
@@ -2094,7 +2304,13 @@ void free_graph(bfs_graph *g) {
 // 2: the hub), built with the graph when its configuration asks for them,
 // else on first use, and rebuilt when the kind changes.
 bfs_status build_head(bfs_graph *g, int kind, cudaStream_t st) {
-    if (!g->head) GB_CK(cudaMalloc(&g->head, (size_t)g->n * sizeof(int2)));
+    // nw_pad * 32 records: the streaming sweep copies whole tiles of 1024;
+    // the records past n hold {-1, -1} (no probe)
+    const size_t recs = (size_t)g->nw_pad * 32;
+    if (!g->head) {
+        GB_CK(cudaMalloc(&g->head, recs * sizeof(int2)));
+        GB_CK(cudaMemsetAsync(g->head + g->n, 0xff, (recs - (size_t)g->n) * sizeof(int2), st));
+    }
     if (kind == 1)
         GB_LAUNCH(head_kernel, grid_cap(g->n, kBlock, 8), kBlock, 0, st, g->off, g->idx, g->n,
                   g->head);
@@ -2159,6 +2375,8 @@ extern "C" BFS_API void bfs_config_default(bfs_config *c) {
     c->prune_components = 0;
     c->bu_list_percent = 10;
     c->device_loop = 2;
+    c->hub_stream_stages = 0;
+    c->hub_stream_percent = 20;
 }
 
 extern "C" BFS_API bfs_status bfs_graph_create(const int64_t *offsets, const int32_t *indices,
@@ -2459,8 +2677,10 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
         };
         for (int d = 0; n_f > 0; ++d) {
             if (d > n) {  // a BFS has at most n layers: the counters are inconsistent
-                set_error("bfs_run: traversal did not terminate after %lld layers", (long long)n);
-                return BFS_ERR_CUDA;
+                set_error("bfs_run: internal error, traversal did not terminate after %lld layers",
+                          (long long)n);
+                cudaStreamSynchronize(st);
+                return BFS_ERR_INTERNAL;
             }
             cur_bu = decide(cfg, cur_bu, d, n, n_f, m_f, n_u, m_u);
             bfs_layer_stats ls;
@@ -2544,11 +2764,32 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                     // the vertices whose hub missed, one lane each
                     ls.converted = 3;
                     if (!g->pend) GB_CK(cudaMalloc(&g->pend, (size_t)g->nw_pad * 4));
+                    const bool stream = cfg.hub_stream_stages > 0 &&
+                                        active * 100 >= (int64_t)cfg.hub_stream_percent * n;
+                    if (stream && g->hub_stream_occ_stages != cfg.hub_stream_stages) {
+                        const HubStreamFn fn = hub_stream_fn(cfg.hub_stream_stages);
+                        const size_t smem = hub_stream_smem_bytes(cfg.hub_stream_stages);
+                        GB_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem));
+                        GB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->hub_stream_occ, fn,
+                                                                            kBlock, smem));
+                        g->hub_stream_occ_stages = cfg.hub_stream_stages;
+                    }
                     if (timing && !all_events) GB_CK(cudaEventRecord(event(e0 + 1), st));
-                    GB_LAUNCH(bu_hub_kernel, grid_cap(g->nw_pad, kBlock / 32 * 8, g->bu_hub_blocks_per_sm),
-                              kBlock, 0, st, g->head, g->nw_pad, g->visited, front, next, g->pend,
-                              parent, level, d + 1, (unsigned long long *)slot_next, slot_zero,
-                              filled ? 0 : 1, g->base_vis, n, root);
+                    if (stream) {
+                        GB_LAUNCH(hub_stream_fn(cfg.hub_stream_stages),
+                                  grid_cap(g->nw_pad / kHubTileWords, 1, g->hub_stream_occ), kBlock,
+                                  hub_stream_smem_bytes(cfg.hub_stream_stages), st, g->head,
+                                  g->nw_pad, g->visited, front, next, g->pend, parent, level, d + 1,
+                                  (unsigned long long *)slot_next, slot_zero, filled ? 0 : 1,
+                                  g->base_vis, n, root);
+                    } else {
+                        GB_LAUNCH(bu_hub_kernel,
+                                  grid_cap(g->nw_pad, kBlock / 32 * 8, g->bu_hub_blocks_per_sm),
+                                  kBlock, 0, st, g->head, g->nw_pad, g->visited, front, next,
+                                  g->pend, parent, level, d + 1, (unsigned long long *)slot_next,
+                                  slot_zero, filled ? 0 : 1, g->base_vis, n, root);
+                    }
                     filled = true;
                     if (timing) GB_CK(cudaEventRecord(event(e0 + 3), st));
                     GB_LAUNCH(bits_list_kernel, grid_cap(g->nw, kBlock * 4, 8), kBlock, 0, st,
@@ -2577,6 +2818,11 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
             {
                 const bfs_status ps = publish_and_wait(g, slot_next, st);
                 if (ps != BFS_OK) return ps;
+            }
+            if (g->h_slot[T_ERR]) {
+                set_error("bfs_run: a bounded wait for a bulk copy ran out in layer %d", d);
+                GB_CK(cudaStreamSynchronize(st));
+                return BFS_ERR_TIMEOUT;
             }
             const int64_t found = g->h_slot[T_NF], m_new = g->h_slot[T_MF];
             ls.examined = cur_bu ? g->h_slot[T_EXAM] : m_f;
@@ -2731,6 +2977,20 @@ extern "C" BFS_API bfs_status bfs_run_noalloc(const int64_t *offsets, const int3
         set_error("bfs_run_noalloc: root out of range");
         return BFS_ERR_INVALID;
     }
+    cudaStream_t st = as_stream(stream);
+    {
+        // e_u starts from nnz (Sec. 4): a count that disagrees with the CSR
+        // would skew every direction decision, so it is checked before any
+        // launch (one 8-byte read of offsets[n])
+        int64_t last = -1;
+        GB_CK(cudaMemcpyAsync(&last, offsets + n, sizeof last, cudaMemcpyDeviceToHost, st));
+        GB_CK(cudaStreamSynchronize(st));
+        if (last != nnz) {
+            set_error("bfs_run_noalloc: nnz = %lld but offsets[n] = %lld", (long long)nnz,
+                      (long long)last);
+            return BFS_ERR_INVALID;
+        }
+    }
     unsigned char *base = nullptr;
     bfs_status s = noalloc_scratch(&base);
     if (s != BFS_OK) return s;
@@ -2743,87 +3003,100 @@ extern "C" BFS_API bfs_status bfs_run_noalloc(const int64_t *offsets, const int3
     int32_t *big = q_next + kNoAllocMaxN;
     int64_t *trace = (int64_t *)(big + kNoAllocMaxN);
 
-    cudaStream_t st = as_stream(stream);
     bfs_config cfg;
     bfs_config_default(&cfg);
-    const int64_t nw_pad = (((n + 31) / 32 + 31) / 32) * 32;
+    const int64_t nw = (n + 31) / 32;
+    const int64_t nw_pad = ((nw + 31) / 32) * 32;
     int bu_occ = 1, td_occ = 1;
     GB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu_occ, BU2, kBlock, 0));
     GB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&td_occ, td_kernel, kBlock, 0));
-    // Every buffer the traversal reads before writing is set here: the base
-    // and visited bitmaps, the frontier bitmap, the first queue entry and the
-    // whole trace ring (init_kernel), so nothing of a previous call leaks in.
-    GB_LAUNCH(base_vis_kernel, grid_cap(nw_pad, kBlock, 8), kBlock, 0, st, offsets, n, nw_pad,
-              base_vis);
-    GB_LAUNCH(init_kernel, grid_cap(std::max(n, nw_pad), kBlock, 8), kBlock, 0, st, n, nw_pad,
-              root, offsets, base_vis, nullptr, level_out, parent_out, visited, front, q_cur,
-              trace, 1);
-    int64_t h[kFields];
-    GB_CK(cudaMemcpyAsync(h, trace, sizeof h, cudaMemcpyDeviceToHost, st));
-    GB_CK(cudaStreamSynchronize(st));
-    int64_t n_f = 1, m_f = h[T_MF];
-    int64_t n_u = n - 1, m_u = nnz - m_f;
-    int cur_bu = 0;
-    bool have_queue = true;
+    // bottom-up warp tasks sized to cover the machine, as in bfs_run's host loop
+    const int64_t bu_full = (int64_t)sm_count() * std::max(1, bu_occ);
+    const int span = bu_span(nw_pad >> 5, 2, bu_full * (kBlock / 32));
     const int bu_grid = (int)std::max<int64_t>(
-        1, std::min<int64_t>(nw_pad / 32 / (kBlock / 32) + 1, (int64_t)sm_count() * bu_occ));
+        1, std::min<int64_t>((nw_pad >> 5) * (32 / span) / (kBlock / 32) + 1, bu_full));
     const int64_t td_warps = (int64_t)sm_count() * td_occ * (kBlock / 32);
-    for (int d = 0; n_f > 0; ++d) {
-        if (d > n) {
-            set_error("bfs_run_noalloc: traversal did not terminate after %lld layers",
-                      (long long)n);
-            return BFS_ERR_CUDA;
-        }
-        cur_bu = decide(cfg, cur_bu, d, n, n_f, m_f, n_u, m_u);
-        int64_t *slot_cur = trace + (d % kRing) * kFields;
-        int64_t *slot_next = trace + ((d + 1) % kRing) * kFields;
-        int64_t *slot_zero = trace + ((d + 2) % kRing) * kFields;
-        if (!cur_bu) {
-            if (!have_queue)
-                GB_LAUNCH(b2q_kernel, grid_cap((n + 31) / 32, kBlock * 4, 8), kBlock, 0, st, front,
-                          (n + 31) / 32, q_cur, (unsigned long long *)(slot_cur + T_CONV));
-            GB_CK(cudaMemsetAsync(next, 0, (size_t)nw_pad * 4, st));
-            const int queue_mode = m_f <= kQueueModeMaxEdges ? 1 : 0;
-            const int defer = td_defer(queue_mode, n_u, (n + 31) / 32);
-            TdArgs a{offsets, indices, visited, next, parent_out, level_out, q_next,
-                     (unsigned long long *)(slot_next + T_NF), d + 1, queue_mode, cfg.td_claim,
-                     defer};
-            const int per_warp = (int)std::min<int64_t>(
-                32, std::max<int64_t>(1, (n_f + td_warps - 1) / td_warps));
-            const int64_t grid_deg = std::min<int64_t>(
-                cfg.td_grid_degree,
-                std::max<int64_t>(4 * (int64_t)cfg.td_warp_degree, m_f / td_warps));
-            GB_LAUNCH(td_kernel, grid_cap((n_f + per_warp - 1) / per_warp, kBlock / 32, td_occ),
-                      kBlock, 0, st, a, q_cur, n_f, per_warp, big,
-                      (unsigned long long *)(slot_cur + T_BIG),
-                      (unsigned long long *)(slot_next + T_MF), cfg.td_warp_degree, grid_deg,
-                      slot_zero);
-            if (m_f >= grid_deg)
-                GB_LAUNCH(td_big_kernel,
-                          (int)std::max<int64_t>(1, std::min<int64_t>(m_f / 4096 + 1,
-                                                                      (int64_t)sm_count() * td_occ)),
-                          kBlock, 0, st, a, big, (const unsigned long long *)(slot_cur + T_BIG),
-                          (unsigned long long *)(slot_next + T_MF));
-            if (defer)
-                GB_LAUNCH(td_post_kernel, grid_cap((n + 31) / 32, kBlock / 4, 8), kBlock, 0, st,
-                          offsets, next, (n + 31) / 32, level_out, d + 1,
-                          (unsigned long long *)(slot_next + T_NF),
-                          (unsigned long long *)(slot_next + T_MF));
-            have_queue = queue_mode != 0;
-        } else {
-            GB_LAUNCH(BU2, bu_grid, kBlock, 0, st, offsets, indices, nullptr, nw_pad, visited,
-                      front, next, parent_out, level_out, d + 1, cfg.bu_probe,
-                      (unsigned long long *)slot_next, slot_zero, 32, 0);
-            have_queue = false;
-        }
-        GB_CK(cudaMemcpyAsync(h, slot_next, sizeof h, cudaMemcpyDeviceToHost, st));
+
+    // The traversal proper. On any error the stream is drained before the
+    // status is returned, so no kernel of this call still writes the shared
+    // array or the caller's outputs afterwards.
+    auto traverse = [&]() -> bfs_status {
+        // Every buffer the traversal reads before writing is set here: the
+        // base and visited bitmaps, the frontier bitmap, the first queue entry
+        // and the whole trace ring (init_kernel), so nothing of a previous
+        // call leaks in.
+        GB_LAUNCH(base_vis_kernel, grid_cap(nw_pad, kBlock, 8), kBlock, 0, st, offsets, n,
+                  nw_pad, base_vis);
+        GB_LAUNCH(init_kernel, grid_cap(std::max(n, nw_pad), kBlock, 8), kBlock, 0, st, n,
+                  nw_pad, root, offsets, base_vis, nullptr, level_out, parent_out, visited,
+                  front, q_cur, trace, 1);
+        int64_t h[kFields];
+        GB_CK(cudaMemcpyAsync(h, trace, sizeof h, cudaMemcpyDeviceToHost, st));
         GB_CK(cudaStreamSynchronize(st));
-        n_u -= h[T_NF];
-        m_u -= h[T_MF];
-        n_f = h[T_NF];
-        m_f = h[T_MF];
-        std::swap(front, next);
-        std::swap(q_cur, q_next);
-    }
-    return BFS_OK;
+        int64_t n_f = 1, m_f = h[T_MF];
+        int64_t n_u = n - 1, m_u = nnz - m_f;
+        int cur_bu = 0;
+        bool have_queue = true;
+        for (int d = 0; n_f > 0; ++d) {
+            if (d > n) {  // a BFS has at most n layers: the counters are inconsistent
+                set_error("bfs_run_noalloc: internal error, traversal did not terminate "
+                          "after %lld layers",
+                          (long long)n);
+                return BFS_ERR_INTERNAL;
+            }
+            cur_bu = decide(cfg, cur_bu, d, n, n_f, m_f, n_u, m_u);
+            int64_t *slot_cur = trace + (d % kRing) * kFields;
+            int64_t *slot_next = trace + ((d + 1) % kRing) * kFields;
+            int64_t *slot_zero = trace + ((d + 2) % kRing) * kFields;
+            if (!cur_bu) {
+                if (!have_queue)
+                    GB_LAUNCH(b2q_kernel, grid_cap(nw, kBlock * 4, 8), kBlock, 0, st, front, nw,
+                              q_cur, (unsigned long long *)(slot_cur + T_CONV));
+                GB_CK(cudaMemsetAsync(next, 0, (size_t)nw_pad * 4, st));
+                const int queue_mode = m_f <= kQueueModeMaxEdges ? 1 : 0;
+                const int defer = td_defer(queue_mode, n_u, nw);
+                TdArgs a{offsets, indices, visited, next, parent_out, level_out, q_next,
+                         (unsigned long long *)(slot_next + T_NF), d + 1, queue_mode,
+                         cfg.td_claim, defer};
+                const int per_warp = (int)std::min<int64_t>(
+                    32, std::max<int64_t>(1, (n_f + td_warps - 1) / td_warps));
+                const int64_t grid_deg = std::min<int64_t>(
+                    cfg.td_grid_degree,
+                    std::max<int64_t>(4 * (int64_t)cfg.td_warp_degree, m_f / td_warps));
+                GB_LAUNCH(td_kernel, grid_cap((n_f + per_warp - 1) / per_warp, kBlock / 32, td_occ),
+                          kBlock, 0, st, a, q_cur, n_f, per_warp, big,
+                          (unsigned long long *)(slot_cur + T_BIG),
+                          (unsigned long long *)(slot_next + T_MF), cfg.td_warp_degree, grid_deg,
+                          slot_zero);
+                if (m_f >= grid_deg)
+                    GB_LAUNCH(td_big_kernel,
+                              (int)std::max<int64_t>(
+                                  1, std::min<int64_t>(m_f / 4096 + 1, (int64_t)sm_count() * td_occ)),
+                              kBlock, 0, st, a, big, (const unsigned long long *)(slot_cur + T_BIG),
+                              (unsigned long long *)(slot_next + T_MF));
+                if (defer)
+                    GB_LAUNCH(td_post_kernel, grid_cap(nw, kBlock / 4, 8), kBlock, 0, st, offsets,
+                              next, nw, level_out, d + 1, (unsigned long long *)(slot_next + T_NF),
+                              (unsigned long long *)(slot_next + T_MF));
+                have_queue = queue_mode != 0;
+            } else {
+                GB_LAUNCH(BU2, bu_grid, kBlock, 0, st, offsets, indices, nullptr, nw_pad, visited,
+                          front, next, parent_out, level_out, d + 1, cfg.bu_probe,
+                          (unsigned long long *)slot_next, slot_zero, span, 0);
+                have_queue = false;
+            }
+            GB_CK(cudaMemcpyAsync(h, slot_next, sizeof h, cudaMemcpyDeviceToHost, st));
+            GB_CK(cudaStreamSynchronize(st));
+            n_u -= h[T_NF];
+            m_u -= h[T_MF];
+            n_f = h[T_NF];
+            m_f = h[T_MF];
+            std::swap(front, next);
+            std::swap(q_cur, q_next);
+        }
+        return BFS_OK;
+    };
+    s = traverse();
+    if (s != BFS_OK) cudaStreamSynchronize(st);  // its own error, if any, is already recorded
+    return s;
 }

@@ -11,7 +11,10 @@ namespace gbfs {
 
 constexpr int kRing = 64;  // trace ring slots (layers)
 constexpr int kFields = 8;
-enum TraceField { T_NF = 0, T_MF = 1, T_EXAM = 2, T_CONV = 3, T_BIG = 4, T_ULIST = 5, T_HUB = 6 };
+enum TraceField {
+    T_NF = 0, T_MF = 1, T_EXAM = 2, T_CONV = 3, T_BIG = 4, T_ULIST = 5, T_HUB = 6,
+    T_ERR = 7  // set by a kernel whose bounded wait ran out
+};
 constexpr int kBlock = 256;
 constexpr int kBigBatch = 1024;
 constexpr int64_t kQueueModeMaxEdges = 1 << 18;
@@ -32,6 +35,8 @@ struct bfs_graph {
     uint32_t *pend = nullptr;      // vertices whose hub missed (two-pass bottom-up)
     int rows_sorted = -1;          // every CSR row ascending: -1 not checked yet
     int bu_hub_blocks_per_sm = 0;
+    int hub_stream_occ = 0;        // resident blocks per SM of the streaming sweep
+    int hub_stream_occ_stages = 0; // ... for this stage count (0 = not queried)
     int2 *head = nullptr;          // {first probe (-1 if none), degree}
     int head_kind = 0;             // what head holds: 1 first neighbour, 2 hub
     uint32_t *comp_in = nullptr;   // vertices in the component of comp_rep

@@ -51,12 +51,12 @@ def test_two_gloo_ranks_combine():
 def test_reference_arm_prints_on_rank0_only():
     env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                        "--steps", "1", "--warmup", "0", "--cpu-scale", "12"],
+                        "--steps", "3", "--warmup", "1", "--scale", "12"],
                        capture_output=True, text=True, env=env, timeout=300)
     assert r.returncode == 0 and r.stdout.strip() == ""
     env = dict(os.environ, RANK="0", WORLD_SIZE="1", LOCAL_RANK="0")
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                        "--steps", "1", "--warmup", "0", "--cpu-scale", "12"],
+                        "--steps", "3", "--warmup", "1", "--scale", "12"],
                        capture_output=True, text=True, env=env, timeout=300)
     assert r.returncode == 0
     line = json.loads(r.stdout.strip().splitlines()[-1])
@@ -65,7 +65,17 @@ def test_reference_arm_prints_on_rank0_only():
     sys.path.insert(0, ROOT)
     import bench
     assert line["metric"] == bench.METRIC and line["unit"] == "GTEPS"
-    assert line["higher_is_better"] is True and line["config"]["workload"] == "rmat-scale26-ef16-64roots"
+    assert line["higher_is_better"] is True
+    # the workload it ran is the one it names: the GPU arm's config for the
+    # same arguments, on the graph the oracle built
+    import argparse
+    args = argparse.Namespace(scale=12, edgefactor=16, roots=64, graph_seed=1, root_seed=2)
+    import oracle
+    s, d = oracle.gen_edges(oracle.RMAT, 12, 16, 1)
+    off, idx = oracle.build_csr(1 << 12, s, d)
+    assert line["config"] == bench.workload_config(args, 1 << 12, int(idx.size))
+    assert line["config"]["workload"] == "rmat-scale12-ef16-64roots"
+    assert line["steps"] == 3 and line["warmup"] == 1 and line["cpu_baseline"]["roots"] == 3
     for k in ("n_gpus", "steps", "warmup", "ms_per_step", "scaling", "vs_baseline", "dtype", "data"):
         assert k in line, k
     cb = line["cpu_baseline"]
