@@ -79,12 +79,13 @@ def peaks():
 
 
 def hub_sweep_bytes(n, probed, written):
-    """Algorithmic bytes of one hub sweep launch: the visited words read and
-    the next, pend and visited words written (n/8 bytes each), one 8-byte
-    head record per probed vertex (unvisited, degree >= 1), and 8 bytes
-    (parent, level) per written vertex: the hub hits, or in the first sweep
-    of a traversal every vertex not reached before it."""
-    return n / 2 + 8 * probed + 8 * written
+    """Algorithmic bytes of one hub sweep launch (compact records): the
+    visited words read and the next, pend and visited words written (n/8
+    bytes each), the base and rank words read (n/4), one 4-byte hub record
+    per probed vertex (unvisited, degree >= 1), and 8 bytes (parent, level)
+    per written vertex: the hub hits, or in the first sweep of a traversal
+    every vertex not reached before it."""
+    return 3 * n / 4 + 4 * probed + 8 * written
 
 
 def one_sweep_bytes(n, nnz):
@@ -99,29 +100,65 @@ def roofline_teps(m_c, peak_gbs, bytes_per_bfs):
     return m_c * peak_gbs * 1e9 / bytes_per_bfs
 
 
-def measured_traffic(scale, edgefactor):
-    """DRAM bytes per hub sweep launch from the committed ncu summary, or None
-    when the workload differs or the kernel changed since the capture (the
-    summary records the SHA-1 of the bu_hub_phase source text)."""
+def batch_bytes(n, k, layers):
+    """The batched byte model (W = k/64 lane words of 8 bytes): per layer,
+    4 bytes per CSR entry read (the examined count), one 8W-byte lane-word
+    gather or OR per entry, and the seen, frontier and next words of every
+    vertex (3 x 8W x n); once per batch the k x n int8 level rows."""
+    W = max(1, (k + 63) // 64)
+    total = 0.0
+    for L in layers:
+        total += 4 * L["examined"] + 8 * W * L["examined"] + 3 * 8 * W * n
+    return total + k * n
+
+
+# source text each recorded ncu capture belongs to (start, end markers in bfs.cu)
+KERNEL_TEXT = {
+    "bu_hubc_stream_kernel": ("// Streaming sweep, one pipeline per warp",
+                              "// Per-vertex step of the compact gather sweep"),
+    "bu_hubc_kernel": ("// Per-vertex step of the compact gather sweep",
+                       "__global__ void __launch_bounds__(kBlock) bu_list_kernel("),
+}
+
+
+def kernel_source_sha1(name):
     import hashlib
-    path = os.path.join(HERE, "profiles", "bu_hub_kernel_dram_rmat26.md")
-    if (scale, edgefactor) != (26, 16) or not os.path.exists(path):
+    src = open(os.path.join(HERE, "paper_1704_02259_gb300", "csrc", "bfs.cu")).read()
+    a = src.find(KERNEL_TEXT[name][0])
+    b = src.find(KERNEL_TEXT[name][1], a + 1)
+    if a < 0 or b < 0:
+        return None
+    return hashlib.sha1(src[a:b].encode()).hexdigest()
+
+
+def measured_traffic(name, scale, edgefactor, launches, first):
+    """DRAM bytes per launch of a hub sweep kernel, from its committed ncu
+    summary (profiles/<kernel>_rmat24.md: dram__bytes_read.sum +
+    dram__bytes_write.sum of captured first sweeps and later sweeps at R-MAT
+    scale 24), weighted by this run's mix of first and later sweeps and
+    scaled to the run's n (the sweep's bytes grow with n: every bitmap word,
+    record and output is per vertex). None when there is no summary, the
+    edgefactor differs, or the kernel's source text changed since the
+    capture (the summary records its SHA-1)."""
+    path = os.path.join(HERE, "profiles", f"{name}_rmat24.md")
+    if name not in KERNEL_TEXT or edgefactor != 16 or not os.path.exists(path) or launches < 1:
         return None
     vals = {}
     with open(path) as f:
         for line in f:
-            if ":" in line and line.split(":")[0] in ("traffic_bytes_per_launch",
-                                                      "kernel_source_sha1"):
+            if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip()
-    src = open(os.path.join(HERE, "paper_1704_02259_gb300", "csrc", "bfs.cu")).read()
-    a = src.find("// First pass of the two-pass bottom-up step")
-    b = src.find("__global__ void __launch_bounds__(kBlock, 4) bu_hub_kernel(", a)
-    if a < 0 or b < 0:
+    if kernel_source_sha1(name) != vals.get("kernel_source_sha1"):
         return None
-    if hashlib.sha1(src[a:b].encode()).hexdigest() != vals.get("kernel_source_sha1"):
+    try:
+        t1 = float(vals["traffic_first_sweep_bytes"])
+        t2 = float(vals["traffic_later_sweep_bytes"])
+        cap = int(vals["capture_scale"])
+    except (KeyError, ValueError):
         return None
-    return float(vals["traffic_bytes_per_launch"]) if "traffic_bytes_per_launch" in vals else None
+    per = (first * t1 + (launches - first) * t2) / launches
+    return per * 2.0 ** (scale - cap)
 
 
 class ClockSampler:
@@ -460,11 +497,18 @@ def batched_comparison(gb, torch, scale, seed=1, root_seed=4, ks=(64, 128, 256, 
             ev[1].synchronize()
             ts.append(ev[0].elapsed_time(ev[1]))
         t = statistics.median(ts)
+        layers, _ = g.batch_stats()
+        bb = batch_bytes(n, k, layers)
+        peak, peak_kind = peaks()
         out["per_k"].append({
             "k": k, "batch_ms": t, "sequential_ms": t_seq,
             "batch_gteps": edges / t / 1e6, "sequential_gteps": edges / t_seq / 1e6,
             "speedup": t_seq / t, "alpha": best.alpha, "beta": best.beta,
-            "lane_probe": best.lane_probe})
+            "lane_probe": best.lane_probe,
+            "roofline": {"bound": "hbm", "bytes": bb, "achieved": bb / (t / 1e3) / 1e9,
+                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": bb / (t / 1e3) / 1e9 / peak,
+                         "directions": "".join("B" if L["direction"] else "T" for L in layers)}})
     out["gpu_launches_batched"] = gb.launch_count() - launches0
     g.close()
     return out
@@ -612,13 +656,12 @@ def run_batch_mode(args):
     g.close()
 
 
-def run_serve(args):
+def serve_sweep(gb, torch, rates, queries, seconds, seed=5):
     """Serving: 8 resident R-MAT graphs (scales 14, 16, 18..23, edgefactor 16,
     seeds 10..17), Poisson arrivals at each rate, graph uniform, root uniform
-    among degree >= 1 vertices; p50/p99 latency and queries/s per rate."""
-    import torch
-    import paper_1704_02259_gb300 as gb
-    torch.cuda.set_device(0)
+    among degree >= 1 vertices; p50/p99 latency and queries/s per rate.
+    Each rate sends min(queries, rate * seconds) queries to one long-running
+    server whose workers were warmed by a burst first."""
     scales = [14, 16, 18, 19, 20, 21, 22, 23]
     graphs, roots, pools = [], [], []
     csr_bytes = 0
@@ -632,10 +675,8 @@ def run_serve(args):
     cfg = gb.default_serve_config()
     cfg.workers = 4
     cfg.max_batch = 512
-    rng = np.random.default_rng(5)
+    rng = np.random.default_rng(seed)
     results = []
-    # one long-running server: a warm-up burst creates the workers' graph
-    # views and traversal state, then each rate is measured from a reset
     srv = gb.Server(cfg)
     ids = [srv.add_graph(g) for g in graphs]
     warm = []
@@ -647,9 +688,9 @@ def run_serve(args):
         for t in warm:
             srv.wait(t)
         warm = []
-    for rate in [100, 300, 1000, 3000, 10000, 20000]:
+    for rate in rates:
         srv.reset_stats()
-        nq = int(min(args.serve_queries, rate * args.serve_seconds))
+        nq = int(min(queries, rate * seconds))
         gsel = rng.integers(0, len(graphs), size=nq)
         gaps = rng.exponential(1.0 / rate, size=nq)
         tickets = []
@@ -668,15 +709,61 @@ def run_serve(args):
                         "p99_ms": st["p99_us"] / 1e3, "achieved_qps": st["qps"],
                         "mean_batch": st["mean_batch"], "batches": st["batches"],
                         "failed": bad})
+    srv.close()
+    for g in graphs:
+        g.close()
+    meta = {"workload": "8 R-MAT graphs, scales 14,16,18-23, ef 16, Poisson stream",
+            "csr_bytes": csr_bytes, "workers": cfg.workers, "max_batch": cfg.max_batch}
+    return results, meta
+
+
+def run_serve(args):
+    """--mode serve: the serving sweep over arrival rates 100 to 20,000/s."""
+    import torch
+    import paper_1704_02259_gb300 as gb
+    torch.cuda.set_device(0)
+    results, meta = serve_sweep(gb, torch, [100, 300, 1000, 3000, 10000, 20000],
+                                args.serve_queries, args.serve_seconds)
     line = {"metric": "serving latency p50/p99 and queries/s", "mode": "serve",
             "value": max(r["achieved_qps"] for r in results), "unit": "queries/s",
             "n_gpus": 1, "higher_is_better": True, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": "8 R-MAT graphs, scales 14,16,18-23, ef 16, Poisson stream",
-                       "csr_bytes": csr_bytes, "workers": cfg.workers,
-                       "max_batch": cfg.max_batch},
-            "rates": results}
-    srv.close()
+            "config": meta, "rates": results}
     print(json.dumps(line), flush=True)
+
+
+def small_config(gb, torch, scale, kind=None, seed=1, root_seed=2, roots=64):
+    """A smaller single-source configuration timed as the headline is (per
+    root CUDA events, harmonic mean of per-root TEPS) with the library's
+    default configuration, plus its one-sweep roofline fraction."""
+    n = 1 << scale
+    kind = gb.GEN_RMAT if kind is None else kind
+    off, idx = gb.rmat_graph(scale, 16, seed, kind=kind)
+    g = gb.Graph(off, idx)
+    rl = gb.sample_roots(off, n, root_seed, roots).cpu().tolist()
+    lv = torch.empty(n, dtype=torch.int32, device="cuda")
+    pa = torch.empty_like(lv)
+    st = torch.cuda.current_stream()
+    for r in rl[:4]:
+        g.run(r, lv, pa)
+    teps, edges = [], []
+    for r in rl:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        g.run(r, lv, pa)
+        e1.record(st)
+        e1.synchronize()
+        edges.append(g.stats().component_edges)
+        teps.append(edges[-1] / (e0.elapsed_time(e1) / 1e3))
+    g.close()
+    peak, kind_p = peaks()
+    v = hmean(teps)
+    roof = roofline_teps(statistics.median(edges), peak, one_sweep_bytes(n, idx.numel()))
+    return {"workload": f"{'er' if kind == gb.GEN_ER else 'rmat'}-scale{scale}-ef16-{roots}roots",
+            "value": v / 1e9, "unit": "GTEPS", "nnz": idx.numel(),
+            "teps_min_median_max": [min(teps) / 1e9, statistics.median(teps) / 1e9,
+                                    max(teps) / 1e9],
+            "sweep_roofline_frac": v / roof, "peak_kind": kind_p}
 
 
 def main():
@@ -768,21 +855,17 @@ def main():
     teps = [e / t for e, t in zip(edges, times)]
     my_hmean = hmean(teps)
     my_total_s = sum(times)
-    # roofline of the hub sweep kernel (bu_hub_kernel, the first pass of the
-    # dense bottom-up layers and the dominant kernel): algorithmic bytes per
-    # launch over its own CUDA-event duration. Per launch: the visited words
-    # read, the next / pend / visited words written (n/2 bytes together), one
-    # 8-byte head record per probed vertex (unvisited, degree >= 1) and the
-    # parent and level of each vertex its hub finds (8 bytes); the first
-    # sweep of a traversal (which, with bitmap claims, also writes the -1
-    # outputs) writes parent and level of every vertex not reached before it
-    # (8 bytes each).
-    hub_bytes = hub_ms = 0.0
+    # roofline of the hub sweep (the first pass of the dense bottom-up
+    # layers, the dominant kernel): algorithmic bytes per launch over its own
+    # CUDA-event duration, per kernel that ran it (the streaming sweep for
+    # layers with at least hub_stream_percent of n left to find, the
+    # gathering sweep for the rest); see hub_sweep_bytes
+    sweeps = {}
     scan_ms = 0.0
     bl_bytes = bl_ms = 0.0
     bu1_bytes = bu1_ms = 0.0
     td_bytes = td_ms = 0.0
-    n_hub = n_bl = n_bu1 = 0
+    n_bl = n_bu1 = 0
     fills_outputs = cfg.td_claim == 1 and not cfg.prune_components
     for _, _, st in recs:
         first_sweep = fills_outputs
@@ -790,10 +873,16 @@ def main():
             active = L["n_u"] - (n - deg1)  # unvisited vertices of degree >= 1
             if L["direction"] == 1 and L["converted"] == 3:
                 written = L["n_u"] if first_sweep else L["hub_found"]
+                stream = (cfg.hub_stream_stages > 0 and
+                          active * 100 >= cfg.hub_stream_percent * n)
+                name = "bu_hubc_stream_kernel" if stream else "bu_hubc_kernel"
+                e = sweeps.setdefault(name, {"bytes": 0.0, "ms": 0.0, "launches": 0,
+                                             "first": 0})
+                e["bytes"] += hub_sweep_bytes(n, active, written)
+                e["ms"] += L["ms_sweep"]
+                e["launches"] += 1
+                e["first"] += 1 if first_sweep else 0
                 first_sweep = False
-                hub_bytes += hub_sweep_bytes(n, active, written)
-                hub_ms += L["ms_sweep"]
-                n_hub += 1
     # the other kernels' sections: one untimed pass over the same roots with
     # events around every layer
     pcfg = gb.default_config()
@@ -882,7 +971,16 @@ def main():
             dist.destroy_process_group()
         return
     peak, peak_kind = peaks()
-    achieved = (hub_bytes / (hub_ms / 1e3)) / 1e9 if hub_ms > 0 else 0.0
+    roofs = {}
+    for name, e in sweeps.items():
+        ach = e["bytes"] / (e["ms"] / 1e3) / 1e9 if e["ms"] > 0 else 0.0
+        roofs[name] = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak,
+                       "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak,
+                       "traffic": measured_traffic(name, scale, ef, e["launches"], e["first"]),
+                       "algorithmic_bytes_per_launch": e["bytes"] / max(1, e["launches"]),
+                       "avg_launch_ms": e["ms"] / max(1, e["launches"]),
+                       "launches": e["launches"], "first_sweeps": e["first"]}
+    dominant = max(roofs, key=lambda k: sweeps[k]["ms"]) if roofs else None
     m_c = statistics.median(edges)
     b_sweep = one_sweep_bytes(n, nnz)
     roof_teps = roofline_teps(m_c, peak, b_sweep)
@@ -896,11 +994,8 @@ def main():
         "method": {"policy": f"edge alpha={cfg.alpha:g} beta={cfg.beta:g}",
                    "bu_probe": cfg.bu_probe, "bu_head": cfg.bu_head,
                    "device_loop": args.device_loop},
-        "roofline": {"bound": "hbm", "kernel": "bu_hub_kernel", "achieved": achieved,
-                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": measured_traffic(scale, ef),
-                     "algorithmic_bytes_per_launch": hub_bytes / max(1, n_hub),
-                     "avg_launch_ms": hub_ms / max(1, n_hub), "launches": n_hub},
+        "roofline": roofs.get(dominant),
+        "roofline_other_sweeps": [v for k, v in roofs.items() if k != dominant],
         "sweep_roofline": {"bytes": b_sweep, "teps": roof_teps / 1e9, "unit": "GTEPS",
                            "frac": value / roof_teps if world == 1 else None},
         "bu_scan_step": {"ms": scan_ms, "pass": "untimed, per-layer events"},
@@ -923,6 +1018,13 @@ def main():
     if not args.no_batch and world == 1:
         line["batched"] = batched_comparison(gb, torch, args.batch_scale)
         line["table3"] = table3_analogue(gb, torch)
+        # the other single-source configurations: scale 16, and scale 20 with
+        # its Erdos-Renyi control
+        line["configs"] = [small_config(gb, torch, 16), small_config(gb, torch, 20),
+                           small_config(gb, torch, 20, kind=gb.GEN_ER, seed=3)]
+        res, meta = serve_sweep(gb, torch, [3000, 10000, 20000], args.serve_queries,
+                                args.serve_seconds)
+        line["serving"] = dict(meta, rates=res)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args, (off, idx))
         line["cpu_throughput"] = cpu_throughput(args)

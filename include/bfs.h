@@ -194,7 +194,12 @@ typedef struct bfs_config {
                                 on first use per configuration (at most 256
                                 layers per graph launch, relaunched until the
                                 traversal ends); with timing = 1 the host
-                                loop runs instead                             */
+                                loop runs instead; 4 = hybrid: each stretch
+                                of top-down layers runs in one cooperative
+                                launch of the device loop (which returns at
+                                the first bottom-up decision), the bottom-up
+                                layers from the host (timing = 1: the host
+                                loop throughout)                              */
     int32_t host_async;      /* with host output buffers: 1 = bfs_run returns
                                 once the traversal is done and the copy of its
                                 results to the host runs on the graph's own
@@ -246,11 +251,13 @@ BFS_API void bfs_config_default(bfs_config *cfg);
                                entries). Failure: BFS_ERR_INVALID          */
 
 /* Creates a graph from a symmetric CSR (layout above) and allocates its
- * per-traversal scratch: four n-bit bitmaps (visited, frontier, next, and
- * the degree-0 mask), three n-entry vertex lists (two queues and the list of
- * grid-spread vertices) and a small counter block: about 12.5*n bytes. The
- * 8-byte head records (cfg.bu_head, 8*n bytes) are built here when cfg asks
- * for them (the defaults do), else by the first bfs_run that does.
+ * per-traversal scratch: five n-bit bitmaps (visited, frontier, next, the
+ * degree-0 mask and the two-pass step's hub misses), three n-entry vertex
+ * lists (two queues and the list of grid-spread vertices) and a small counter
+ * block: about 12.6*n bytes. The 8-byte head records (cfg.bu_head, 8*n bytes)
+ * are built here when cfg asks for them (the defaults do), else by the first
+ * bfs_run that does; whatever else a configuration needs is allocated by
+ * bfs_graph_reserve or, failing that, by the first bfs_run that needs it.
  * Without BFS_BORROW the CSR is copied into library memory and the caller may
  * free its arrays. cfg may be NULL (defaults). Synchronous. */
 BFS_API bfs_status bfs_graph_create(const int64_t *offsets, const int32_t *indices, int64_t n,
@@ -266,6 +273,28 @@ BFS_API bfs_status bfs_graph_info(const bfs_graph *g, const int64_t **offsets,
 
 /* Frees everything the graph owns. NULL is accepted. */
 BFS_API bfs_status bfs_graph_destroy(bfs_graph *g);
+
+/* Allocates and builds now, for the graph's current configuration, all
+ * that bfs_run would otherwise allocate on first use: the head records of
+ * the configured kind, the device-loop records or the graph loop's CUDA
+ * graph (cfg.device_loop), the component mask (cfg.prune_components: one
+ * traversal), the rows-sorted check (cfg.parent_min), and, per flags,
+ *   BFS_RESERVE_HOST_OUT   scratch for host output buffers (cfg.host_async:
+ *                          the two device output pairs and the copy stream)
+ *   BFS_RESERVE_NO_PARENT  scratch for parent_out = NULL
+ * After it, bfs_run calls with this configuration and those kinds of output
+ * make no device or pinned-host allocation (bfs_alloc_count() stays put),
+ * so no allocation, and no implicit synchronisation of one, lands inside a
+ * latency-measured call. Changing the configuration may need another call.
+ * Synchronous on `stream`. */
+#define BFS_RESERVE_HOST_OUT 1u
+#define BFS_RESERVE_NO_PARENT 2u
+BFS_API bfs_status bfs_graph_reserve(bfs_graph *g, uint32_t flags, void *stream);
+
+/* Number of device and pinned-host allocations this library has made in
+ * this process so far (cudaMalloc, cudaMallocAsync, cudaHostAlloc), for
+ * checking that a reserved or warmed-up path allocates nothing. */
+BFS_API int64_t bfs_alloc_count(void);
 
 /* Hybrid BFS from `root` (Alg. 3). level_out / parent_out are n int32 each,
  * caller-owned, either both device memory or both host memory (pageable or
@@ -388,6 +417,9 @@ typedef struct bfs_batch_layer_stats {
     int64_t e_u;         /* their degree sum                                  */
     float ms;            /* layer time when cfg.timing = 1                    */
     float pad2;
+    int64_t examined;    /* CSR entries the layer read: the rows scanned by the
+                            bottom-up step up to each vertex's early exit, or
+                            every frontier vertex's row in a top-down layer  */
 } bfs_batch_layer_stats;
 
 BFS_API bfs_status bfs_last_batch_stats(const bfs_graph *g, bfs_batch_layer_stats *out,
@@ -442,6 +474,9 @@ typedef struct bfs_serve_stats {
     double mean_batch;        /* mean roots per launch                         */
     double p50_us, p99_us;    /* submit-to-completion latency percentiles      */
     double qps;               /* completed / (last completion - first submit)  */
+    int64_t deep_fallbacks;   /* queries answered by the single-source
+                                 traversal because their batch went deeper than
+                                 an int8 level holds (BFS_ERR_DEPTH)           */
 } bfs_serve_stats;
 
 BFS_API void bfs_serve_config_default(bfs_serve_config *cfg);

@@ -70,7 +70,7 @@ class BatchLayerStats(ctypes.Structure):
     _fields_ = [("direction", ctypes.c_int32), ("pad", ctypes.c_int32),
                 ("v_f", ctypes.c_int64), ("e_f", ctypes.c_int64), ("pairs", ctypes.c_int64),
                 ("v_u", ctypes.c_int64), ("e_u", ctypes.c_int64), ("ms", ctypes.c_float),
-                ("pad2", ctypes.c_float)]
+                ("pad2", ctypes.c_float), ("examined", ctypes.c_int64)]
 
 
 class ServeConfig(ctypes.Structure):
@@ -83,7 +83,8 @@ class ServeStats(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("batches", ctypes.c_int64), ("deferred", ctypes.c_int64),
                 ("mean_batch", ctypes.c_double), ("p50_us", ctypes.c_double),
-                ("p99_us", ctypes.c_double), ("qps", ctypes.c_double)]
+                ("p99_us", ctypes.c_double), ("qps", ctypes.c_double),
+                ("deep_fallbacks", ctypes.c_int64)]
 
 
 _lib = None
@@ -94,6 +95,7 @@ I32, I64, U32, U64, DBL = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctype
 SIGNATURES = {
     "bfs_last_error": (ctypes.c_char_p, []),
     "bfs_launch_count": (I64, []),
+    "bfs_alloc_count": (I64, []),
     "bfs_generate_edges": (I32, [I32, I32, I32, U64, DBL, DBL, DBL, P, P, P]),
     "bfs_build_csr": (I32, [I64, I64, P, P, P, P, P, P]),
     "bfs_sample_roots": (I32, [P, I64, U64, I32, I64, P, P, P]),
@@ -102,6 +104,7 @@ SIGNATURES = {
     "bfs_graph_set_config": (I32, [P, P]),
     "bfs_graph_info": (I32, [P, P, P, P, P]),
     "bfs_graph_destroy": (I32, [P]),
+    "bfs_graph_reserve": (I32, [P, U32, P]),
     "bfs_run": (I32, [P, I32, P, P, P]),
     "bfs_graph_sync": (I32, [P]),
     "bfs_last_run_stats": (I32, [P, P, I32, P, P]),
@@ -166,6 +169,15 @@ def _ptr(t: torch.Tensor | None):
 
 def launch_count() -> int:
     return int(lib().bfs_launch_count())
+
+
+def alloc_count() -> int:
+    """Device and pinned-host allocations the library has made so far."""
+    return int(lib().bfs_alloc_count())
+
+
+RESERVE_HOST_OUT = 1
+RESERVE_NO_PARENT = 2
 
 
 def default_batch_config() -> BatchConfig:
@@ -269,6 +281,12 @@ class Graph:
             parent = torch.empty(self.n, dtype=torch.int32, device=level.device)
         _check(lib().bfs_run(self._h, int(root), _ptr(level), _ptr(parent), _stream(stream)))
         return level, parent
+
+    def reserve(self, host_out: bool = False, no_parent: bool = False, stream=None):
+        """bfs_graph_reserve: allocate now what bfs_run would allocate on
+        first use under the current configuration."""
+        flags = (RESERVE_HOST_OUT if host_out else 0) | (RESERVE_NO_PARENT if no_parent else 0)
+        _check(lib().bfs_graph_reserve(self._h, flags, _stream(stream)))
 
     def sync(self):
         """Waits for host copies left in flight by run() with config.host_async."""

@@ -108,6 +108,74 @@ __global__ void hub_head_kernel(const int64_t *__restrict__ off, const int32_t *
     }
 }
 
+// Exclusive prefix count of the degree >= 1 vertices per bitmap word:
+// wrank[w] = set bits of ~base in words 0..w-1, wrank[nw_pad] = the total.
+// One block walks the words 1024 at a time (once per graph).
+__global__ void __launch_bounds__(1024) word_rank_kernel(const uint32_t *__restrict__ base,
+                                                         int64_t nw_pad,
+                                                         uint32_t *__restrict__ wrank) {
+    __shared__ uint32_t warp_tot[32];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int64_t b = 0; b < nw_pad; b += 1024) {
+        const int64_t w = b + threadIdx.x;
+        const uint32_t c = w < nw_pad ? (uint32_t)__popc(~base[w]) : 0u;
+        uint32_t x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if ((int)lane >= o) x += y;
+        }
+        if (lane == 31) warp_tot[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            const uint32_t t = warp_tot[lane];
+            uint32_t sc = t;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, sc, o);
+                if ((int)lane >= o) sc += y;
+            }
+            warp_tot[lane] = sc - t;
+        }
+        __syncthreads();
+        if (w < nw_pad) wrank[w] = carry + warp_tot[wid] + x - c;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += warp_tot[wid] + x;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) wrank[nw_pad] = carry;
+}
+
+// Compact hub records: for every degree >= 1 vertex v (a clear bit of
+// base), hubc[rank(v)] = hub | (degree == 1) << 31, rank(v) = wrank[w] +
+// the degree >= 1 vertices before v in its word. A warp per word.
+__global__ void hubc_kernel(const int2 *__restrict__ head, const uint32_t *__restrict__ base,
+                            const uint32_t *__restrict__ wrank, int64_t nw_pad,
+                            uint32_t *__restrict__ hubc) {
+    const unsigned lane = lane_id();
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = gw; w < nw_pad; w += tw) {
+        const uint32_t live = ~base[w];
+        if ((live >> lane) & 1u) {
+            const int2 h = head[w * 32 + lane];
+            hubc[wrank[w] + __popc(live & lanemask_lt())] =
+                (uint32_t)h.x | (h.y == 1 ? 0x80000000u : 0u);
+        }
+    }
+}
+
+// {base word, rank} per bitmap word, the streaming sweep's per-word metadata.
+__global__ void wmeta_kernel(const uint32_t *__restrict__ base, const uint32_t *__restrict__ wrank,
+                             int64_t nw_pad, uint2 *__restrict__ wmeta) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nw_pad; w += stride)
+        wmeta[w] = make_uint2(base[w], wrank[w]);
+}
+
 // Highest-degree vertex (smallest id on ties), packed as degree << 32 | ~id.
 __global__ void max_degree_kernel(const int64_t *__restrict__ off, int64_t n,
                                   unsigned long long *best) {
@@ -948,7 +1016,10 @@ __device__ __forceinline__ void bu_list_phase(
     const int32_t *__restrict__ list, const unsigned long long *count,
     uint32_t *__restrict__ visited, const uint32_t *__restrict__ front,
     uint32_t *__restrict__ next_bm, int32_t *__restrict__ parent, int32_t *__restrict__ level,
-    int32_t new_level, int probe, unsigned long long *slot_next, int64_t *zero_slot) {
+    int32_t new_level, int probe, unsigned long long *slot_next, int64_t *zero_slot,
+    int mf_left = 0) {
+    // mf_left = 1 (after the compact hub sweep): T_MF receives the degree sum
+    // of the listed vertices left unvisited instead of that of the found ones
     // positions [p_start, lim) are tested by the lane itself
     const int p_start = head ? hskip : 0;
     const int lim = head ? (probe > hskip ? probe : hskip) : probe;
@@ -1052,8 +1123,10 @@ __device__ __forceinline__ void bu_list_phase(
             level[v] = new_level;
             atomicOr(next_bm + (v >> 5), bit);
             atomicOr(visited + (v >> 5), bit);
-            my_mf += deg;
+            if (!mf_left) my_mf += deg;
             my_nf += 1;
+        } else if (mf_left && have) {
+            my_mf += deg;
         }
         my_ex += ex;
     }
@@ -1107,15 +1180,16 @@ __device__ __forceinline__ void bu_hub_phase(
             const bool probed = h[k].x >= 0;
             const bool found = probed && ((fw[k] >> (h[k].x & 31)) & 1u);
             my_ex += probed ? (found || h[k].y > 1 ? 1 : 2) : 0;
+            // one store per array for the whole warp (see the streaming sweep)
+            const bool minus = !found && init_out && v < n && v != root &&
+                               !(((vw[k] & ~__ldg(base + w0 + k)) >> lane) & 1u);
+            if (found || minus) {
+                parent[v] = found ? h[k].x : -1;
+                level[v] = found ? new_level : -1;
+            }
             if (found) {
-                parent[v] = h[k].x;
-                level[v] = new_level;
                 my_mf += h[k].y;
                 my_nf += 1;
-            } else if (init_out && v < n && v != root &&
-                       !(((vw[k] & ~__ldg(base + w0 + k)) >> lane) & 1u)) {
-                parent[v] = -1;
-                level[v] = -1;
             }
             const unsigned fb = __ballot_sync(0xffffffffu, found);
             const unsigned pb = __ballot_sync(0xffffffffu, probed && !found && h[k].y > 1);
@@ -1141,21 +1215,29 @@ __global__ void __launch_bounds__(kBlock, 4) bu_hub_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// Streaming first pass for dense sweeps. Same per-vertex work as
-// bu_hub_phase, but the head records are not gathered by the warps: the
-// block's bulk-copy engine (cp.async.bulk, completion counted in bytes on an
-// mbarrier) streams every record of a tile of kHubTileWords bitmap words
-// (1024 vertices, 8 KB), with the tile's visited and base words, into shared
-// memory S tiles ahead. The warps then only make the frontier-bit loads (L2)
-// and the stores, so the one dependent global load per vertex is the
-// frontier word, while S - 1 tiles per block stay in flight from HBM. In a
-// dense sweep (most vertices unvisited) nearly every head sector is needed
-// anyway, so reading all of them costs little; sparse sweeps keep the
-// gathering kernel above.
+// First pass of the two-pass bottom-up step on the compact hub records
+// (hubc, 4 bytes per degree >= 1 vertex; host loop). Same per-vertex test as
+// bu_hub_phase (Sec. 5.1: filter the unvisited vertices, probe), but the
+// sweep needs no degree: a hit only stores its parent and level, and the
+// switch counter e_f of the layer (Sec. 4) is taken as e_u before the layer
+// minus e_u after it, where e_u after = the degree sum of the vertices still
+// unvisited: a degree-1 vertex whose hub missed (counted here, bit 31 of its
+// record) plus the hub misses the row scan does not find (counted by
+// bu_list_phase with mf_left). The rank of vertex v among the degree >= 1
+// vertices is wrank[v / 32] + the degree >= 1 vertices before it in its word.
+//
+// bu_hubc_stream_kernel (dense sweeps): the block's bulk-copy engine
+// (cp.async.bulk, completion counted in bytes on an mbarrier) streams the
+// records of a tile of kHubTileWords bitmap words (1024 vertices, at most
+// 4 KB of records) with the tile's visited, base and rank words into shared
+// memory, S tiles ahead, so the warps make only the frontier-bit loads (L2)
+// and the stores. bu_hubc_kernel (sparse sweeps) gathers the records of the
+// unvisited vertices itself, 8 words per warp round.
 // ---------------------------------------------------------------------------
 constexpr int kHubTileWords = 32;
 constexpr int kHubTileVerts = kHubTileWords * 32;
-constexpr unsigned kHubTileBytes = kHubTileVerts * sizeof(int2);
+// records of one tile, rounded out to 16-byte boundaries at both ends
+constexpr unsigned kHubTileRecBytes = (kHubTileVerts + 8) * 4;
 constexpr int kHubWordsPerWarp = kHubTileWords / (kBlock / 32);
 static_assert(kHubTileWords % (kBlock / 32) == 0, "the tile's words split evenly over the warps");
 constexpr unsigned long long kHubWaitNs = 1000000000ull;  // 1 s per bounded wait
@@ -1207,117 +1289,292 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity,
     return true;
 }
 
-template <int S>
-constexpr size_t hub_stream_smem() {
-    return (size_t)S * (kHubTileBytes + 2 * kHubTileWords * 4) + (size_t)S * 8;
+// L2 eviction policies (createpolicy): data streamed once through L2 is
+// marked evict-first, the L2-resident frontier bitmap evict-last, so a sweep
+// that moves a gigabyte through L2 does not push out the bitmap whose words
+// every probe reads.
+__device__ __forceinline__ uint64_t l2_evict_first() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_last() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint32_t ld_hint(const uint32_t *p, uint64_t pol) {
+    uint32_t v;
+    asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void bulk_g2s_hint(void *dst, const void *src, unsigned bytes,
+                                              uint64_t *bar, uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+        "[%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+
+// Streaming sweep, one pipeline per warp: a warp owns tiles of kWarpTile
+// bitmap words (256 vertices) and keeps S of them in flight in its own
+// shared-memory ring, filled by bulk copies its lane 0 issues (the tile's
+// compact records, its visited words and its {base, rank} words), each
+// stage completing on its own mbarrier. No block-wide barrier: a warp
+// waits only for its own copies and its own frontier loads.
+constexpr int kWarpTile = 8;                                 // bitmap words per warp tile
+constexpr unsigned kWarpRecBytes = (kWarpTile * 32 + 8) * 4;  // records, 16-byte rounded
+constexpr unsigned kWarpStageBytes = kWarpRecBytes + kWarpTile * 4 + kWarpTile * 8;
+static_assert(kWarpStageBytes % 16 == 0, "stages keep bulk-copy destinations 16-byte aligned");
+
+// Predicated global accesses written as one predicated instruction each.
+__device__ __forceinline__ uint32_t ld_hint_if(const uint32_t *p, uint64_t pol, bool pred) {
+    uint32_t v;
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %3, 0;\n\tmov.b32 %0, 0;\n\t"
+        "@q ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;\n\t}"
+        : "=r"(v)
+        : "l"(p), "l"(pol), "r"((unsigned)pred));
+    return v;
+}
+__device__ __forceinline__ void st_cs_if(int32_t *p, int32_t v, bool pred) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q st.global.cs.b32 [%0], %1;\n\t}"
+                 ::"l"(p), "r"(v), "r"((unsigned)pred)
+                 : "memory");
 }
 
 template <int S>
-__global__ void __launch_bounds__(kBlock) bu_hub_stream_kernel(
-    const int2 *__restrict__ head, int64_t nw_pad, uint32_t *__restrict__ visited,
+constexpr size_t hub_stream_smem() {
+    return (size_t)(kBlock / 32) * ((size_t)S * kWarpStageBytes + (size_t)S * 16);
+}
+
+template <int S, bool INIT>
+__global__ void __launch_bounds__(kBlock, 4) bu_hubc_stream_kernel(
+    const uint32_t *__restrict__ hubc, const uint32_t *__restrict__ wrank,
+    const uint2 *__restrict__ wmeta, int64_t nw_pad, uint32_t *__restrict__ visited,
     const uint32_t *__restrict__ front, uint32_t *__restrict__ next_bm,
     uint32_t *__restrict__ pend, int32_t *__restrict__ parent, int32_t *__restrict__ level,
-    int32_t new_level, unsigned long long *slot_next, int64_t *zero_slot, int init_out,
-    const uint32_t *__restrict__ base, int64_t n, int32_t root) {
+    int32_t new_level, unsigned long long *slot_next, int64_t *zero_slot, int64_t n,
+    int32_t root) {
     extern __shared__ __align__(128) unsigned char hub_smem[];
-    int2 *sh_head = reinterpret_cast<int2 *>(hub_smem);                        // [S][1024]
-    uint32_t *sh_vis = reinterpret_cast<uint32_t *>(sh_head + S * kHubTileVerts);  // [S][32]
-    uint32_t *sh_base = sh_vis + S * kHubTileWords;                               // [S][32]
-    uint64_t *full = reinterpret_cast<uint64_t *>(sh_base + S * kHubTileWords);   // [S]
-    if (blockIdx.x == 0 && threadIdx.x < kFields) zero_slot[threadIdx.x] = 0;
-    const int64_t tiles = nw_pad / kHubTileWords;  // nw_pad is a multiple of 32
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
-    // thread 0 fills stage s with tile t: head records, visited and base words
-    auto issue = [&](int64_t t, int s) {
-        mbar_expect_tx(full + s, kHubTileBytes + 2 * kHubTileWords * 4);
-        bulk_g2s(sh_head + s * kHubTileVerts, head + t * kHubTileVerts, kHubTileBytes, full + s);
-        bulk_g2s(sh_vis + s * kHubTileWords, visited + t * kHubTileWords, kHubTileWords * 4,
-                 full + s);
-        bulk_g2s(sh_base + s * kHubTileWords, base + t * kHubTileWords, kHubTileWords * 4,
+    unsigned char *mine = hub_smem + (size_t)warp * ((size_t)S * kWarpStageBytes + (size_t)S * 16);
+    uint64_t *full = reinterpret_cast<uint64_t *>(mine + (size_t)S * kWarpStageBytes);  // [S]
+    uint32_t *rec0 = reinterpret_cast<uint32_t *>(full + S);                            // [S]
+    if (blockIdx.x == 0 && threadIdx.x < kFields) zero_slot[threadIdx.x] = 0;
+    const int64_t tiles = nw_pad / kWarpTile;  // nw_pad is a multiple of 32
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t pol_stream = l2_evict_first(), pol_keep = l2_evict_last();
+    auto stage = [&](int s) { return mine + (size_t)s * kWarpStageBytes; };
+    // lane 0: fill stage s with tile t, whose records are [r0, r1)
+    auto issue = [&](int64_t t, int s, uint32_t r0, uint32_t r1) {
+        const uint32_t a0 = r0 & ~3u, a1 = (r1 + 3u) & ~3u;  // hubc has spare records
+        const unsigned rec_bytes = (a1 - a0) * 4u;
+        rec0[s] = a0;
+        mbar_expect_tx(full + s, rec_bytes + kWarpTile * 12);
+        unsigned char *st = stage(s);
+        if (rec_bytes) bulk_g2s_hint(st, hubc + a0, rec_bytes, full + s, pol_stream);
+        bulk_g2s(st + kWarpRecBytes, visited + t * kWarpTile, kWarpTile * 4, full + s);
+        bulk_g2s(st + kWarpRecBytes + kWarpTile * 4, wmeta + t * kWarpTile, kWarpTile * 8,
                  full + s);
     };
-    if (threadIdx.x == 0) {
+    uint32_t nr0 = 0, nr1 = 0;  // lane 0: record range of the next tile to issue
+    if (lane == 0) {
         for (int s = 0; s < S; ++s) mbar_init(full + s, 1);
         mbar_init_fence();
         for (int s = 0; s < S; ++s) {
-            const int64_t t = blockIdx.x + (int64_t)s * gridDim.x;
-            if (t < tiles) issue(t, s);
+            const int64_t t = gw + (int64_t)s * tw;
+            if (t < tiles) issue(t, s, wrank[t * kWarpTile], wrank[t * kWarpTile + kWarpTile]);
+        }
+        const int64_t t = gw + (int64_t)S * tw;
+        if (t < tiles) {
+            nr0 = wrank[t * kWarpTile];
+            nr1 = wrank[t * kWarpTile + kWarpTile];
         }
     }
-    __syncthreads();
-    int64_t my_nf = 0, my_mf = 0, my_ex = 0;
-    int64_t i = 0;
-    for (;; ++i) {
-        const int64_t t = blockIdx.x + i * gridDim.x;
+    __syncwarp();
+    uint32_t c_nf = 0, c_d1 = 0, c_pr = 0;  // found, degree-1 misses, probed
+    for (int64_t i = 0;; ++i) {
+        const int64_t t = gw + i * tw;
         if (t >= tiles) break;
         const int s = (int)(i % S);
         const bool ok = mbar_wait(full + s, (unsigned)((i / S) & 1), kHubWaitNs);
-        if (__syncthreads_or(!ok)) {
-            // a copy never completed: flag it, let this stage's and the later
-            // stages' copies land (bounded), and leave with the block
-            if (threadIdx.x == 0) {
+        if (__any_sync(0xffffffffu, !ok)) {
+            // a copy never completed: flag it, let this warp's copies in
+            // flight land (bounded) and stop
+            if (lane == 0) {
                 atomicExch(reinterpret_cast<unsigned long long *>(slot_next + T_ERR), 1ull);
-                for (int j = 0; j < S; ++j) {
-                    const int64_t tj = blockIdx.x + (i + j) * gridDim.x;
-                    if (tj < tiles)
+                for (int j = 0; j < S; ++j)
+                    if (gw + (i + j) * tw < tiles)
                         mbar_wait(full + (int)((i + j) % S), (unsigned)(((i + j) / S) & 1),
                                   kHubWaitNs);
-                }
             }
             break;
         }
-        const int2 *th = sh_head + s * kHubTileVerts;
-        const uint32_t *tv = sh_vis + s * kHubTileWords;
-        const uint32_t *tb = sh_base + s * kHubTileWords;
-        uint32_t vw[kHubWordsPerWarp];
-        int2 h[kHubWordsPerWarp];
-        uint32_t fw[kHubWordsPerWarp];
+        const unsigned char *st = stage(s);
+        const uint32_t *rec = reinterpret_cast<const uint32_t *>(st);
+        const uint32_t *tv = reinterpret_cast<const uint32_t *>(st + kWarpRecBytes);
+        const uint2 *tm = reinterpret_cast<const uint2 *>(st + kWarpRecBytes + kWarpTile * 4);
+        const uint32_t a0 = rec0[s];
+        const unsigned lt = lanemask_lt();
+        uint32_t vw[kWarpTile], bw[kWarpTile], h[kWarpTile], fw[kWarpTile];
+        const uint32_t bit = 1u << lane;
 #pragma unroll
-        for (int k = 0; k < kHubWordsPerWarp; ++k) {
-            const int j = warp * kHubWordsPerWarp + k;
-            vw[k] = tv[j];
-            h[k] = th[j * 32 + lane];
-            const bool unv = !((vw[k] >> lane) & 1u);  // bits past n are set
-            if (!unv) h[k].x = -1;
+        for (int k = 0; k < kWarpTile; ++k) {
+            vw[k] = tv[k];
+            const uint2 m = tm[k];  // {base word, rank of the word's first vertex}
+            bw[k] = m.x;
+            // the index stays inside the stage's records for every lane (the
+            // rank of the next degree >= 1 vertex), so the load needs no guard
+            h[k] = rec[m.y - a0 + __popc(~m.x & lt)];
+            fw[k] = ld_hint_if(front + ((h[k] & 0x7fffffffu) >> 5), pol_keep,
+                               (vw[k] & bit) == 0u);  // unvisited implies degree >= 1
+        }
+        uint32_t fbw[kWarpTile], d1w[kWarpTile];
+        // per-tile output pointers, the tile's vertices below n (ids past n
+        // are set in both vw and bw) and the root's position in the tile (a
+        // root of degree 0 is not "reached before" by the bitmaps)
+        const int64_t vbase = t * (kWarpTile * 32);
+        int32_t *const par_t = parent + vbase + lane;
+        int32_t *const lev_t = level + vbase + lane;
+        int lim = 0, rloc = -1;
+        if constexpr (INIT) {
+            lim = (int)min((int64_t)(kWarpTile * 32), n - vbase) - (int)lane;
+            const int64_t rk = (int64_t)root - vbase;
+            rloc = (rk >= 0 && rk < kWarpTile * 32) ? (int)rk - (int)lane : -1;
         }
 #pragma unroll
-        for (int k = 0; k < kHubWordsPerWarp; ++k)
-            fw[k] = h[k].x >= 0 ? __ldg(front + (h[k].x >> 5)) : 0u;
-#pragma unroll
-        for (int k = 0; k < kHubWordsPerWarp; ++k) {
-            const int j = warp * kHubWordsPerWarp + k;
-            const int64_t w = t * kHubTileWords + j;
-            const int64_t v = w * 32 + lane;
-            const bool probed = h[k].x >= 0;
-            const bool found = probed && ((fw[k] >> (h[k].x & 31)) & 1u);
-            my_ex += probed ? (found || h[k].y > 1 ? 1 : 2) : 0;
-            if (found) {
-                parent[v] = h[k].x;
-                level[v] = new_level;
-                my_mf += h[k].y;
-                my_nf += 1;
-            } else if (init_out && v < n && v != root && !(((vw[k] & ~tb[j]) >> lane) & 1u)) {
-                parent[v] = -1;
-                level[v] = -1;
-            }
-            const unsigned fb = __ballot_sync(0xffffffffu, found);
-            const unsigned pb = __ballot_sync(0xffffffffu, probed && !found && h[k].y > 1);
-            if (lane == 0) {
-                next_bm[w] = fb;
-                pend[w] = pb;
-                if (fb) visited[w] = vw[k] | fb;
+        for (int k = 0; k < kWarpTile; ++k) {
+            const bool probed = (vw[k] & bit) == 0u;
+            const int32_t hub = (int32_t)(h[k] & 0x7fffffffu);
+            const bool found = probed && ((fw[k] >> (hub & 31)) & 1u);
+            fbw[k] = __ballot_sync(0xffffffffu, found);
+            d1w[k] = __ballot_sync(0xffffffffu, (int32_t)h[k] < 0);  // degree 1 (where probed)
+            if constexpr (INIT) {
+                // one store per array for the whole warp (a hit's values,
+                // else the -1 of a vertex not reached before): whole sectors
+                const bool minus = !found && !(vw[k] & ~bw[k] & bit) && k * 32 < lim &&
+                                   k * 32 != rloc;
+                st_cs_if(par_t + k * 32, found ? hub : -1, found || minus);
+                st_cs_if(lev_t + k * 32, found ? new_level : -1, found || minus);
+            } else {
+                st_cs_if(par_t + k * 32, hub, found);
+                st_cs_if(lev_t + k * 32, new_level, found);
             }
         }
-        __syncthreads();  // every warp is done with stage s
-        if (threadIdx.x == 0) {
-            const int64_t t2 = t + (int64_t)S * gridDim.x;
+        if (lane == 0) {
+            uint32_t pbw[kWarpTile];
+#pragma unroll
+            for (int k = 0; k < kWarpTile; ++k) {
+                const uint32_t miss = ~vw[k] & ~fbw[k];  // probed, hub not in the frontier
+                pbw[k] = miss & ~d1w[k];                 // rows still to scan
+                c_nf += __popc(fbw[k]);
+                c_pr += __popc(~vw[k]);
+                c_d1 += __popc(miss & d1w[k]);           // degree-1 misses: left unvisited
+            }
+            uint4 *nx = reinterpret_cast<uint4 *>(next_bm + t * kWarpTile);
+            uint4 *pd = reinterpret_cast<uint4 *>(pend + t * kWarpTile);
+            uint4 *vs = reinterpret_cast<uint4 *>(visited + t * kWarpTile);
+            nx[0] = make_uint4(fbw[0], fbw[1], fbw[2], fbw[3]);
+            nx[1] = make_uint4(fbw[4], fbw[5], fbw[6], fbw[7]);
+            pd[0] = make_uint4(pbw[0], pbw[1], pbw[2], pbw[3]);
+            pd[1] = make_uint4(pbw[4], pbw[5], pbw[6], pbw[7]);
+            vs[0] = make_uint4(vw[0] | fbw[0], vw[1] | fbw[1], vw[2] | fbw[2], vw[3] | fbw[3]);
+            vs[1] = make_uint4(vw[4] | fbw[4], vw[5] | fbw[5], vw[6] | fbw[6], vw[7] | fbw[7]);
+        }
+        __syncwarp();  // the warp is done with stage s
+        if (lane == 0) {
+            const int64_t t2 = t + (int64_t)S * tw;
             if (t2 < tiles) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue(t2, s);
+                issue(t2, s, nr0, nr1);
+                const int64_t t3 = t2 + tw;
+                if (t3 < tiles) {
+                    nr0 = wrank[t3 * kWarpTile];
+                    nr1 = wrank[t3 * kWarpTile + kWarpTile];
+                }
             }
         }
     }
-    block_add4(my_nf, my_mf, my_ex, my_nf, slot_next + T_NF, slot_next + T_MF,
+    // the counts are held by lane 0
+    const int64_t nf = lane == 0 ? c_nf : 0, d1 = lane == 0 ? c_d1 : 0,
+                  pr = lane == 0 ? c_pr : 0;
+    block_add4(nf, d1, pr + d1, nf, slot_next + T_NF, slot_next + T_MF, slot_next + T_EXAM,
+               slot_next + T_HUB);
+}
+
+// Per-vertex step of the compact gather sweep for word w (visited word vw,
+// base word bw) and the lane's record h (valid when the lane is unvisited).
+__device__ __forceinline__ void hubc_word(
+    int64_t w, uint32_t vw, uint32_t bw, uint32_t h, uint32_t fw, unsigned lane,
+    uint32_t *__restrict__ visited, uint32_t *__restrict__ next_bm, uint32_t *__restrict__ pend,
+    int32_t *__restrict__ parent, int32_t *__restrict__ level, int32_t new_level, int init_out,
+    int64_t n, int32_t root, int64_t &my_nf, int64_t &my_left, int64_t &my_ex) {
+    const int64_t v = w * 32 + lane;
+    const bool probed = !((vw >> lane) & 1u);  // unvisited implies degree >= 1
+    const int32_t hub = (int32_t)(h & 0x7fffffffu);
+    const bool deg1 = (h >> 31) != 0u;
+    const bool found = probed && ((fw >> (hub & 31)) & 1u);
+    my_ex += probed ? (found || !deg1 ? 1 : 2) : 0;
+    my_left += (probed && !found && deg1) ? 1 : 0;
+    my_nf += found ? 1 : 0;
+    // one store per array for the whole warp (whole sectors)
+    const bool minus = !found && init_out && v < n && v != root && !(((vw & ~bw) >> lane) & 1u);
+    if (found || minus) {
+        __stcs(parent + v, found ? hub : -1);
+        __stcs(level + v, found ? new_level : -1);
+    }
+    const unsigned fb = __ballot_sync(0xffffffffu, found);
+    const unsigned pb = __ballot_sync(0xffffffffu, probed && !found && !deg1);
+    if (lane == 0) {
+        next_bm[w] = fb;
+        pend[w] = pb;
+        if (fb) visited[w] = vw | fb;
+    }
+}
+
+// Sparse sweeps: the warp gathers the records of its unvisited vertices,
+// 8 words per round (lane i = bit i of each).
+__global__ void __launch_bounds__(kBlock, 4) bu_hubc_kernel(
+    const uint32_t *__restrict__ hubc, const uint32_t *__restrict__ wrank, int64_t nw_pad,
+    uint32_t *__restrict__ visited, const uint32_t *__restrict__ front,
+    uint32_t *__restrict__ next_bm, uint32_t *__restrict__ pend, int32_t *__restrict__ parent,
+    int32_t *__restrict__ level, int32_t new_level, unsigned long long *slot_next,
+    int64_t *zero_slot, int init_out, const uint32_t *__restrict__ base, int64_t n,
+    int32_t root) {
+    constexpr int R = 8;
+    static_assert(32 % R == 0, "a round's R words must not cross nw_pad (a multiple of 32)");
+    if (blockIdx.x == 0 && threadIdx.x < kFields) zero_slot[threadIdx.x] = 0;
+    const unsigned lane = lane_id();
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t pol_stream = l2_evict_first(), pol_keep = l2_evict_last();
+    int64_t my_nf = 0, my_left = 0, my_ex = 0;
+    for (int64_t w0 = gw * R; w0 < nw_pad; w0 += tw * R) {
+        uint32_t vw[R], bw[R], h[R], fw[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            vw[k] = visited[w0 + k];
+            bw[k] = __ldg(base + w0 + k);
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const bool probed = !((vw[k] >> lane) & 1u);
+            h[k] = probed ? ld_hint(hubc + __ldg(wrank + w0 + k) + __popc(~bw[k] & lanemask_lt()),
+                                    pol_stream)
+                          : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+            fw[k] = !((vw[k] >> lane) & 1u) ? ld_hint(front + ((h[k] & 0x7fffffffu) >> 5), pol_keep)
+                                            : 0u;
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+            hubc_word(w0 + k, vw[k], bw[k], h[k], fw[k], lane, visited, next_bm, pend, parent,
+                      level, new_level, init_out, n, root, my_nf, my_left, my_ex);
+    }
+    block_add4(my_nf, my_left, my_ex, my_nf, slot_next + T_NF, slot_next + T_MF,
                slot_next + T_EXAM, slot_next + T_HUB);
 }
 
@@ -1327,9 +1584,10 @@ __global__ void __launch_bounds__(kBlock) bu_list_kernel(
     const int32_t *__restrict__ list, const unsigned long long *count,
     uint32_t *__restrict__ visited, const uint32_t *__restrict__ front,
     uint32_t *__restrict__ next_bm, int32_t *__restrict__ parent, int32_t *__restrict__ level,
-    int32_t new_level, int probe, unsigned long long *slot_next, int64_t *zero_slot) {
+    int32_t new_level, int probe, unsigned long long *slot_next, int64_t *zero_slot,
+    int mf_left) {
     bu_list_phase<false>(off, idx, head, hskip, list, count, visited, front, next_bm, parent,
-                         level, new_level, probe, slot_next, zero_slot);
+                         level, new_level, probe, slot_next, zero_slot, mf_left);
 }
 
 
@@ -1450,7 +1708,7 @@ bool config_ok(const bfs_config &c) {
     if (c.parent_min != 0 && c.parent_min != 1) return false;
     if (c.prune_components != 0 && c.prune_components != 1) return false;
     if (c.bu_list_percent < 0 || c.bu_list_percent > 100) return false;
-    if (c.device_loop < 0 || c.device_loop > 3) return false;
+    if (c.device_loop < 0 || c.device_loop > 4) return false;
     if (c.timing < 0 || c.timing > 2) return false;
     if (c.hub_stream_stages != 0 && c.hub_stream_stages != 2 && c.hub_stream_stages != 3 &&
         c.hub_stream_stages != 4 && c.hub_stream_stages != 6 && c.hub_stream_stages != 8)
@@ -1462,16 +1720,18 @@ bool config_ok(const bfs_config &c) {
 // The streaming hub sweep for a stage count, its dynamic shared memory, and
 // its resident blocks per SM (queried once per graph and stage count; the
 // shared-memory limit is raised where a count needs more than the default).
-using HubStreamFn = void (*)(const int2 *, int64_t, uint32_t *, const uint32_t *, uint32_t *,
-                             uint32_t *, int32_t *, int32_t *, int32_t, unsigned long long *,
-                             int64_t *, int, const uint32_t *, int64_t, int32_t);
-HubStreamFn hub_stream_fn(int stages) {
+using HubStreamFn = void (*)(const uint32_t *, const uint32_t *, const uint2 *, int64_t,
+                             uint32_t *, const uint32_t *, uint32_t *, uint32_t *, int32_t *,
+                             int32_t *, int32_t, unsigned long long *, int64_t *, int64_t,
+                             int32_t);
+// init: the sweep also writes the -1 of every vertex not reached before it
+HubStreamFn hub_stream_fn(int stages, bool init) {
     switch (stages) {
-        case 2: return bu_hub_stream_kernel<2>;
-        case 3: return bu_hub_stream_kernel<3>;
-        case 4: return bu_hub_stream_kernel<4>;
-        case 6: return bu_hub_stream_kernel<6>;
-        default: return bu_hub_stream_kernel<8>;
+        case 2: return init ? bu_hubc_stream_kernel<2, true> : bu_hubc_stream_kernel<2, false>;
+        case 3: return init ? bu_hubc_stream_kernel<3, true> : bu_hubc_stream_kernel<3, false>;
+        case 4: return init ? bu_hubc_stream_kernel<4, true> : bu_hubc_stream_kernel<4, false>;
+        case 6: return init ? bu_hubc_stream_kernel<6, true> : bu_hubc_stream_kernel<6, false>;
+        default: return init ? bu_hubc_stream_kernel<8, true> : bu_hubc_stream_kernel<8, false>;
     }
 }
 size_t hub_stream_smem_bytes(int stages) {
@@ -1534,6 +1794,11 @@ struct SsPersist {
     int32_t *err;
     bfs_config cfg;
     unsigned long long timeout_ns;
+    // start state (layer, Alg. 3 counters, direction, queue) and whether to
+    // stop at the first bottom-up decision: the hybrid loop runs stretches
+    // of top-down layers here and the bottom-up layers from the host
+    int64_t d0, n_f0, m_f0, n_u0, m_u0, degsum0;
+    int cur_bu0, have_queue0, stop_at_bu;
 };
 
 __global__ void __launch_bounds__(kBlock, 4) bfs_persistent_kernel(SsPersist p) {
@@ -1541,16 +1806,20 @@ __global__ void __launch_bounds__(kBlock, 4) bfs_persistent_kernel(SsPersist p) 
     const int64_t td_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int64_t n_f = 1, m_f = __ldcg(p.trace + T_MF);
-    int64_t n_u = p.n - 1, m_u = p.nnz - m_f, degsum = 0;
-    int cur_bu = 0, status = BFS_OK, d = 0;
-    bool have_queue = true;
+    // m_f0 < 0: a whole traversal from the root (its degree is in slot 0)
+    int64_t n_f = p.n_f0, m_f = p.m_f0 < 0 ? __ldcg(p.trace + T_MF) : p.m_f0;
+    int64_t n_u = p.n_u0, m_u = p.m_f0 < 0 ? p.nnz - m_f : p.m_u0, degsum = p.degsum0;
+    int cur_bu = p.cur_bu0, status = BFS_OK;
+    int d = (int)p.d0;
+    bool have_queue = p.have_queue0 != 0;
     for (; n_f > 0; ++d) {
         if (d > p.n) {  // a BFS has at most n layers: the counters are inconsistent
-            status = BFS_ERR_CUDA;
+            status = BFS_ERR_INTERNAL;
             break;
         }
-        cur_bu = decide(p.cfg, cur_bu, d, p.n, n_f, m_f, n_u, m_u);
+        const int next_bu = decide(p.cfg, cur_bu, d, p.n, n_f, m_f, n_u, m_u);
+        if (p.stop_at_bu && next_bu) break;  // the host runs the bottom-up layer
+        cur_bu = next_bu;
         degsum += m_f;
         int64_t *sc = p.trace + (d % kRing) * kFields;
         int64_t *sn = p.trace + ((d + 1) % kRing) * kFields;
@@ -1673,18 +1942,38 @@ __global__ void __launch_bounds__(kBlock, 4) bfs_persistent_kernel(SsPersist p) 
         p.result[0] = d;
         p.result[1] = status;
         p.result[2] = degsum;
+        p.result[8] = n_f;
+        p.result[9] = m_f;
+        p.result[10] = n_u;
+        p.result[11] = m_u;
+        p.result[12] = have_queue ? 1 : 0;
+        p.result[13] = cur_bu;
     }
 }
 
-constexpr size_t kPctlSsBytes = (size_t)kSsMaxRecords * 8 * 8 + 64;
+// result header: [0] layers (or the layer the run stopped at), [1] status,
+// [2] degree sum, [4..5] grid barrier and error word, [8..13] end state
+constexpr int kPctlHead = 16;
+constexpr size_t kPctlSsBytes = (size_t)kSsMaxRecords * 8 * 8 + kPctlHead * 8;
 constexpr int64_t kDeviceLoopAutoMaxN = 1ll << 25;  // device_loop = 2: on up to this n
 
-// Runs the traversal as one cooperative launch of bfs_persistent_kernel and
-// reads back the per-layer records (init_kernel has already run on `st`).
-bfs_status run_device_loop(bfs_graph *g, int32_t *level, int32_t *parent, cudaStream_t st) {
+// State of the layer loop between layers, shared by the host loop and the
+// persistent kernel's stretches of top-down layers.
+struct LoopState {
+    int64_t d = 0, n_f = 1, m_f = -1, n_u = 0, m_u = 0, degsum = 0;
+    int cur_bu = 0, have_queue = 1;
+};
+
+// Runs layers from state `s` in one cooperative launch of
+// bfs_persistent_kernel (init_kernel has already run on `st`), appends their
+// records to g->last and leaves the end state in `s`. With stop_at_bu the
+// launch returns at the first bottom-up decision (s.d is then that layer);
+// otherwise it runs to the end of the traversal.
+bfs_status run_device_segment(bfs_graph *g, int32_t *level, int32_t *parent, cudaStream_t st,
+                              LoopState &s, bool stop_at_bu) {
     if (!g->pctl) {
-        GB_CK(cudaMalloc(&g->pctl, kPctlSsBytes));
-        GB_CK(cudaMallocHost(&g->h_pctl, kPctlSsBytes));
+        GB_CK(dev_malloc(&g->pctl, kPctlSsBytes));
+        GB_CK(host_malloc(&g->h_pctl, kPctlSsBytes));
     }
     if (g->persist_blocks_per_sm <= 0) {
         GB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->persist_blocks_per_sm,
@@ -1694,10 +1983,10 @@ bfs_status run_device_loop(bfs_graph *g, int32_t *level, int32_t *parent, cudaSt
             return BFS_ERR_CUDA;
         }
     }
-    // layout: result[8] (layers, status, degree sum, barrier, error), then
-    // the per-layer records, so one small copy covers short traversals
+    // layout: the kPctlHead-word result header, then the per-layer records,
+    // so one small copy covers short traversals
     int64_t *result = g->pctl;
-    GB_CK(cudaMemsetAsync(result, 0, 64, st));
+    GB_CK(cudaMemsetAsync(result, 0, kPctlHead * 8, st));
     SsPersist p;
     p.off = g->off;
     p.idx = g->idx;
@@ -1715,16 +2004,24 @@ bfs_status run_device_loop(bfs_graph *g, int32_t *level, int32_t *parent, cudaSt
     p.parent = parent;
     p.level = level;
     p.trace = g->trace;
-    p.layers = g->pctl + 8;
+    p.layers = g->pctl + kPctlHead;
     p.result = result;
     p.bar = (unsigned *)(result + 4);
     p.err = (int32_t *)(p.bar + 2);
     p.cfg = g->cfg;
     p.head = g->cfg.bu_head ? g->head : nullptr;
     p.hskip = g->cfg.bu_head == 1 ? 1 : 0;
-    if (g->cfg.bu_head == 2 && !g->pend) GB_CK(cudaMalloc(&g->pend, (size_t)g->nw_pad * 4));
     p.pend = g->cfg.bu_head == 2 ? g->pend : nullptr;
     p.timeout_ns = 2000000000ull;  // 2 s per barrier wait
+    p.d0 = s.d;
+    p.n_f0 = s.n_f;
+    p.m_f0 = s.m_f;
+    p.n_u0 = s.n_u;
+    p.m_u0 = s.m_u;
+    p.degsum0 = s.degsum;
+    p.cur_bu0 = s.cur_bu;
+    p.have_queue0 = s.have_queue;
+    p.stop_at_bu = stop_at_bu ? 1 : 0;
     void *args[] = {&p};
     // Grid sized to the graph: barrier cost grows with the block count, and a
     // small graph cannot use the whole GPU anyway (one block per 2048
@@ -1736,19 +2033,20 @@ bfs_status run_device_loop(bfs_graph *g, int32_t *level, int32_t *parent, cudaSt
                                       args, 0, st));
     count_launch();
     constexpr int64_t kFirst = 64;  // records fetched with the result
-    GB_CK(cudaMemcpyAsync(g->h_pctl, g->pctl, (size_t)(8 + kFirst * 8) * 8, cudaMemcpyDeviceToHost,
-                          st));
+    const int64_t first = std::min<int64_t>(s.d + kFirst, kSsMaxRecords);
+    GB_CK(cudaMemcpyAsync(g->h_pctl, g->pctl, (size_t)(kPctlHead + first * 8) * 8,
+                          cudaMemcpyDeviceToHost, st));
     GB_CK(cudaStreamSynchronize(st));
     const int64_t *hres = g->h_pctl;
-    const int64_t L = hres[0];
-    if (L > kFirst) {
-        const int64_t more = std::min<int64_t>(L, kSsMaxRecords) - kFirst;
-        GB_CK(cudaMemcpyAsync(g->h_pctl + 8 + kFirst * 8, g->pctl + 8 + kFirst * 8,
+    const int64_t end = hres[0];
+    if (std::min<int64_t>(end, kSsMaxRecords) > first) {
+        const int64_t more = std::min<int64_t>(end, kSsMaxRecords) - first;
+        GB_CK(cudaMemcpyAsync(g->h_pctl + kPctlHead + first * 8, g->pctl + kPctlHead + first * 8,
                               (size_t)more * 64, cudaMemcpyDeviceToHost, st));
         GB_CK(cudaStreamSynchronize(st));
     }
-    for (int64_t d = 0; d < L && d < kSsMaxRecords; ++d) {
-        const int64_t *rec = g->h_pctl + 8 + d * 8;
+    for (int64_t d = s.d; d < end && d < kSsMaxRecords; ++d) {
+        const int64_t *rec = g->h_pctl + kPctlHead + d * 8;
         bfs_layer_stats ls;
         memset(&ls, 0, sizeof ls);
         ls.direction = (int32_t)rec[0];
@@ -1761,7 +2059,6 @@ bfs_status run_device_loop(bfs_graph *g, int32_t *level, int32_t *parent, cudaSt
         ls.found = rec[7];
         g->last.push_back(ls);
     }
-    g->last_component_edges = hres[2] / 2;
     if (hres[1] == BFS_ERR_TIMEOUT) {
         set_error("bfs_run: a grid barrier wait of the device loop ran out");
         return BFS_ERR_TIMEOUT;
@@ -1770,7 +2067,24 @@ bfs_status run_device_loop(bfs_graph *g, int32_t *level, int32_t *parent, cudaSt
         set_error("bfs_run: the device loop stopped (status %lld)", (long long)hres[1]);
         return (bfs_status)hres[1];
     }
+    s.d = end;
+    s.degsum = hres[2];
+    s.n_f = hres[8];
+    s.m_f = hres[9];
+    s.n_u = hres[10];
+    s.m_u = hres[11];
+    s.have_queue = (int)hres[12];
+    s.cur_bu = (int)hres[13];
     return BFS_OK;
+}
+
+// The whole traversal as one cooperative launch.
+bfs_status run_device_loop(bfs_graph *g, int32_t *level, int32_t *parent, cudaStream_t st) {
+    LoopState s;
+    s.n_u = g->n - 1;  // m_f < 0: the kernel reads the root's degree
+    const bfs_status r = run_device_segment(g, level, parent, st, s, false);
+    g->last_component_edges = s.degsum / 2;
+    return r;
 }
 
 // Graph loop (device_loop = 3): the layer loop as one CUDA graph whose
@@ -2046,10 +2360,9 @@ void free_graph_loop(bfs_graph *g) {
 bfs_status build_graph_loop(bfs_graph *g) {
     const bfs_config &cfg = g->cfg;
     if (!g->gl_mem) {
-        GB_CK(cudaMalloc(&g->gl_mem, kGlRunBytes + (size_t)kSsMaxRecords * kGlRec * 8));
-        GB_CK(cudaMallocHost(&g->h_gl, kGlRunBytes + (size_t)kSsMaxRecords * kGlRec * 8));
+        GB_CK(dev_malloc(&g->gl_mem, kGlRunBytes + (size_t)kSsMaxRecords * kGlRec * 8));
+        GB_CK(host_malloc(&g->h_gl, kGlRunBytes + (size_t)kSsMaxRecords * kGlRec * 8));
     }
-    if (cfg.bu_head == 2 && !g->pend) GB_CK(cudaMalloc(&g->pend, (size_t)g->nw_pad * 4));
     const int bw = cfg.bu_words;
     const int bsel = (bw == 4 ? 2 : bw - 1) + (cfg.bu_head ? 3 : 0);
     const void *one_fn[6] = {(const void *)gl_bu_kernel<1, 4, false>,
@@ -2215,8 +2528,10 @@ bfs_status run_graph_loop(bfs_graph *g, int32_t *level, int32_t *parent, int32_t
     int64_t counted = 0;
     for (int64_t launch = 0;; ++launch) {
         if (launch > g->n / kGlCap + 2) {
-            set_error("bfs_run: graph loop did not finish after %lld launches", (long long)launch);
-            return BFS_ERR_CUDA;
+            set_error("bfs_run: internal error, graph loop did not finish after %lld launches",
+                      (long long)launch);
+            cudaStreamSynchronize(st);
+            return BFS_ERR_INTERNAL;
         }
         GB_CK(cudaGraphLaunch(g->gl_exec, st));
         GB_CK(cudaMemcpyAsync(g->h_gl, g->gl_mem, first_bytes, cudaMemcpyDeviceToHost, st));
@@ -2273,6 +2588,9 @@ void free_graph(bfs_graph *g) {
     cudaFree(g->visited);
     cudaFree(g->base_vis);
     cudaFree(g->head);
+    cudaFree(g->hubc);
+    cudaFree(g->wrank);
+    cudaFree(g->wmeta);
     cudaFree(g->comp_in);
     cudaFree(g->pctl);
     if (g->h_pctl) cudaFreeHost(g->h_pctl);
@@ -2294,6 +2612,7 @@ void free_graph(bfs_graph *g) {
     if (g->hout_ready) cudaEventDestroy(g->hout_ready);
     if (g->copy_st) cudaStreamDestroy(g->copy_st);
     cudaFree(g->trace);
+    cudaFree(g->misc);
     if (g->h_slot) cudaFreeHost(g->h_slot);
     if (g->h_pub) cudaFreeHost(g->h_pub);
     for (cudaEvent_t e : g->events) cudaEventDestroy(e);
@@ -2308,7 +2627,7 @@ bfs_status build_head(bfs_graph *g, int kind, cudaStream_t st) {
     // the records past n hold {-1, -1} (no probe)
     const size_t recs = (size_t)g->nw_pad * 32;
     if (!g->head) {
-        GB_CK(cudaMalloc(&g->head, recs * sizeof(int2)));
+        GB_CK(dev_malloc(&g->head, recs * sizeof(int2)));
         GB_CK(cudaMemsetAsync(g->head + g->n, 0xff, (recs - (size_t)g->n) * sizeof(int2), st));
     }
     if (kind == 1)
@@ -2317,6 +2636,19 @@ bfs_status build_head(bfs_graph *g, int kind, cudaStream_t st) {
     else
         GB_LAUNCH(hub_head_kernel, grid_cap(g->n, kBlock / 32, 8), kBlock, 0, st, g->off,
                   g->idx, g->n, g->head);
+    if (kind == 2 && !g->hubc) {
+        // the compact 4-byte hub records the host loop's two-pass sweeps read
+        g->n1 = g->n - g->deg0;
+        GB_CK(dev_malloc(&g->wrank, (size_t)(g->nw_pad + 1) * 4));
+        GB_CK(dev_malloc(&g->hubc, (size_t)(g->n1 + 16) * 4));
+        GB_CK(cudaMemsetAsync(g->hubc + g->n1, 0xff, 16 * 4, st));
+        GB_LAUNCH(word_rank_kernel, 1, 1024, 0, st, g->base_vis, g->nw_pad, g->wrank);
+        GB_LAUNCH(hubc_kernel, grid_cap(g->nw_pad, kBlock / 32, 8), kBlock, 0, st, g->head,
+                  g->base_vis, g->wrank, g->nw_pad, g->hubc);
+        GB_CK(dev_malloc(&g->wmeta, (size_t)g->nw_pad * sizeof(uint2)));
+        GB_LAUNCH(wmeta_kernel, grid_cap(g->nw_pad, kBlock, 8), kBlock, 0, st, g->base_vis,
+                  g->wrank, g->nw_pad, g->wmeta);
+    }
     g->head_kind = kind;
     return BFS_OK;
 }
@@ -2375,8 +2707,9 @@ extern "C" BFS_API void bfs_config_default(bfs_config *c) {
     c->prune_components = 0;
     c->bu_list_percent = 10;
     c->device_loop = 2;
-    c->hub_stream_stages = 0;
-    c->hub_stream_percent = 20;
+    // measured at scale 26: 2 stages per warp, every two-pass sweep streamed
+    c->hub_stream_stages = 2;
+    c->hub_stream_percent = 0;
 }
 
 extern "C" BFS_API bfs_status bfs_graph_create(const int64_t *offsets, const int32_t *indices,
@@ -2419,29 +2752,31 @@ extern "C" BFS_API bfs_status bfs_graph_create(const int64_t *offsets, const int
     } else {
         const cudaMemcpyKind kind =
             (flags & BFS_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-        GB_CKG(cudaMalloc(&g->off_own, (size_t)(n + 1) * 8));
-        GB_CKG(cudaMalloc(&g->idx_own, (size_t)std::max<int64_t>(nnz, 1) * 4));
+        GB_CKG(dev_malloc(&g->off_own, (size_t)(n + 1) * 8));
+        GB_CKG(dev_malloc(&g->idx_own, (size_t)std::max<int64_t>(nnz, 1) * 4));
         GB_CKG(cudaMemcpy(g->off_own, offsets, (size_t)(n + 1) * 8, kind));
         if (nnz) GB_CKG(cudaMemcpy(g->idx_own, indices, (size_t)nnz * 4, kind));
         g->off = g->off_own;
         g->idx = g->idx_own;
     }
     const size_t bmb = (size_t)g->nw_pad * 4;
-    GB_CKG(cudaMalloc(&g->visited, bmb));
-    GB_CKG(cudaMalloc(&g->base_vis, bmb));
-    GB_CKG(cudaMalloc(&g->bm_a, bmb));
-    GB_CKG(cudaMalloc(&g->bm_b, bmb));
-    GB_CKG(cudaMalloc(&g->q_a, (size_t)n * 4));
-    GB_CKG(cudaMalloc(&g->q_b, (size_t)n * 4));
-    GB_CKG(cudaMalloc(&g->big, (size_t)n * 4));
-    GB_CKG(cudaMalloc(&g->trace, (size_t)kRing * kFields * 8));
-    GB_CKG(cudaMallocHost(&g->h_slot, kFields * 8));
-    GB_CKG(cudaHostAlloc((void **)&g->h_pub, (kFields + 1) * 8, cudaHostAllocMapped));
+    GB_CKG(dev_malloc(&g->visited, bmb));
+    GB_CKG(dev_malloc(&g->base_vis, bmb));
+    GB_CKG(dev_malloc(&g->bm_a, bmb));
+    GB_CKG(dev_malloc(&g->bm_b, bmb));
+    GB_CKG(dev_malloc(&g->q_a, (size_t)n * 4));
+    GB_CKG(dev_malloc(&g->q_b, (size_t)n * 4));
+    GB_CKG(dev_malloc(&g->big, (size_t)n * 4));
+    GB_CKG(dev_malloc(&g->trace, (size_t)kRing * kFields * 8));
+    GB_CKG(dev_malloc(&g->misc, 64));
+    GB_CKG(dev_malloc(&g->pend, bmb));  // two-pass bottom-up: vertices whose hub missed
+    GB_CKG(host_malloc(&g->h_slot, kFields * 8));
+    GB_CKG(host_malloc((void **)&g->h_pub, (kFields + 1) * 8, cudaHostAllocMapped));
     GB_CKG(cudaHostGetDevicePointer((void **)&g->d_pub, g->h_pub, 0));
     g->h_pub[kFields] = 0;
     if (flags & (BFS_VALIDATE | BFS_VALIDATE_SYMMETRIC)) {
         int *bad = nullptr, hbad = 0;
-        GB_CKG(cudaMalloc(&bad, sizeof(int)));
+        GB_CKG(dev_malloc(&bad, sizeof(int)));
         cudaMemset(bad, 0, sizeof(int));
         validate_kernel<<<grid_cap(std::max(n, nnz), kBlock, 8), kBlock>>>(g->off, g->idx, n, nnz,
                                                                            bad);
@@ -2469,7 +2804,7 @@ extern "C" BFS_API bfs_status bfs_graph_create(const int64_t *offsets, const int
     count_launch();
     {  // degree-0 vertices = set bits of base_vis minus the padding bits
         unsigned long long *cnt = nullptr, hc = 0;
-        GB_CKG(cudaMalloc(&cnt, 8));
+        GB_CKG(dev_malloc(&cnt, 8));
         cudaMemset(cnt, 0, 8);
         count_bits_kernel<<<grid_cap(g->nw_pad, kBlock, 8), kBlock>>>(g->base_vis, g->nw_pad, cnt);
         count_launch();
@@ -2490,6 +2825,8 @@ extern "C" BFS_API bfs_status bfs_graph_create(const int64_t *offsets, const int
     GB_CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->bu_list_blocks_per_sm, bu_list_kernel,
                                                          kBlock, 0));
     GB_CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->bu_hub_blocks_per_sm, bu_hub_kernel,
+                                                         kBlock, 0));
+    GB_CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->hubc_blocks_per_sm, bu_hubc_kernel,
                                                          kBlock, 0));
     if (g->cfg.bu_head) {
         const bfs_status hs = build_head(g, g->cfg.bu_head, 0);
@@ -2541,6 +2878,112 @@ extern "C" BFS_API bfs_status bfs_graph_destroy(bfs_graph *g) {
     return BFS_OK;
 }
 
+// Everything bfs_run would otherwise allocate or build on first use under
+// the graph's current configuration, for outputs in host memory (host_out)
+// or not, and with or without a caller-given parent array: output scratch or
+// the host_async output pairs and copy stream, the head records of the
+// configured kind, the component mask (prune_components, one traversal), the
+// device-loop records, the graph loop's graph, the rows-sorted check of
+// parent_min and the streaming sweep's shared-memory limit.
+static bfs_status prepare(bfs_graph *g, bool host_out, bool have_parent, void *stream) {
+    cudaStream_t st = as_stream(stream);
+    const bfs_config &cfg = g->cfg;
+    const int64_t n = g->n;
+    if (host_out && cfg.host_async) {
+        if (!g->copy_st) {
+            GB_CK(cudaStreamCreateWithFlags(&g->copy_st, cudaStreamNonBlocking));
+            GB_CK(cudaEventCreateWithFlags(&g->hout_ready, cudaEventDisableTiming));
+            for (int i = 0; i < 2; ++i)
+                GB_CK(cudaEventCreateWithFlags(&g->hout_done[i], cudaEventDisableTiming));
+        }
+        for (int i = 0; i < 2; ++i)
+            if (!g->hout_level[i]) {
+                GB_CK(dev_malloc(&g->hout_level[i], (size_t)n * 4));
+                GB_CK(dev_malloc(&g->hout_parent[i], (size_t)n * 4));
+            }
+    } else if (host_out) {
+        if (!g->level_scratch) GB_CK(dev_malloc(&g->level_scratch, (size_t)n * 4));
+        have_parent = false;  // the parent is computed in scratch and copied
+    }
+    if (!have_parent && !(host_out && cfg.host_async) && !g->parent_scratch)
+        GB_CK(dev_malloc(&g->parent_scratch, (size_t)n * 4));
+    if (cfg.prune_components && g->comp_rep < 0) {
+        // The component of the highest-degree vertex, found once by one
+        // traversal without pruning, kept as a bitmap.
+        unsigned long long *best = reinterpret_cast<unsigned long long *>(g->misc);
+        unsigned long long hb = 0;
+        GB_CK(cudaMemsetAsync(best, 0, 8, st));
+        GB_LAUNCH(max_degree_kernel, grid_cap(n, kBlock, 8), kBlock, 0, st, g->off, n, best);
+        GB_CK(cudaMemcpyAsync(&hb, best, 8, cudaMemcpyDeviceToHost, st));
+        GB_CK(cudaStreamSynchronize(st));
+        const int32_t rep = (int32_t)(0xffffffffull - (hb & 0xffffffffull));
+        if (!g->comp_in) GB_CK(dev_malloc(&g->comp_in, (size_t)g->nw_pad * 4));
+        if (!g->level_scratch) GB_CK(dev_malloc(&g->level_scratch, (size_t)n * 4));
+        if (!g->parent_scratch) GB_CK(dev_malloc(&g->parent_scratch, (size_t)n * 4));
+        const bfs_config saved = g->cfg;
+        g->cfg.prune_components = 0;
+        g->cfg.timing = 0;
+        const bfs_status s = bfs_run(g, rep, g->level_scratch, g->parent_scratch, stream);
+        g->cfg = saved;
+        if (s != BFS_OK) return s;
+        GB_LAUNCH(reached_bits_kernel, grid_cap(g->nw_pad, kBlock, 8), kBlock, 0, st,
+                  g->level_scratch, n, g->nw_pad, g->comp_in);
+        GB_CK(cudaStreamSynchronize(st));
+        g->comp_rep = rep;
+    }
+    if (cfg.bu_head && g->head_kind != cfg.bu_head) {
+        const bfs_status hs = build_head(g, cfg.bu_head, st);
+        if (hs != BFS_OK) return hs;
+    }
+    const bool dev_loop = cfg.device_loop == 1 || cfg.device_loop == 4 ||
+                          (cfg.device_loop == 2 && n <= kDeviceLoopAutoMaxN);
+    if (dev_loop && !g->pctl) {
+        GB_CK(dev_malloc(&g->pctl, kPctlSsBytes));
+        GB_CK(host_malloc(&g->h_pctl, kPctlSsBytes));
+    }
+    if (cfg.device_loop == 3 && cfg.timing == 0) {
+        if (g->gl_exec &&
+            memcmp(&((const GlStatic *)g->gl_static)->cfg, &g->cfg, sizeof g->cfg) != 0)
+            destroy_graph_loop(g);  // built for another configuration
+        if (!g->gl_exec) {
+            const bfs_status bs = build_graph_loop(g);
+            if (bs != BFS_OK) return bs;
+        }
+    }
+    if (cfg.parent_min && g->rows_sorted < 0) {  // checked once per graph
+        int *flag = reinterpret_cast<int *>(g->misc);
+        int h = 1;
+        GB_CK(cudaMemcpyAsync(flag, &h, 4, cudaMemcpyHostToDevice, st));
+        GB_LAUNCH(rows_sorted_kernel, grid_cap(n, kBlock, 8), kBlock, 0, st, g->off, g->idx, n,
+                  flag);
+        GB_CK(cudaMemcpyAsync(&h, flag, 4, cudaMemcpyDeviceToHost, st));
+        GB_CK(cudaStreamSynchronize(st));
+        g->rows_sorted = h;
+    }
+    if (cfg.hub_stream_stages > 0 && g->hub_stream_occ_stages != cfg.hub_stream_stages) {
+        const size_t smem = hub_stream_smem_bytes(cfg.hub_stream_stages);
+        for (int init = 0; init < 2; ++init)
+            GB_CK(cudaFuncSetAttribute(hub_stream_fn(cfg.hub_stream_stages, init != 0),
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        GB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &g->hub_stream_occ, hub_stream_fn(cfg.hub_stream_stages, true), kBlock, smem));
+        g->hub_stream_occ_stages = cfg.hub_stream_stages;
+    }
+    return BFS_OK;
+}
+
+extern "C" BFS_API bfs_status bfs_graph_reserve(bfs_graph *g, uint32_t flags, void *stream) {
+    clear_error();
+    if (!g || (flags & ~(BFS_RESERVE_HOST_OUT | BFS_RESERVE_NO_PARENT))) {
+        set_error("bfs_graph_reserve: need a graph and known flags");
+        return BFS_ERR_INVALID;
+    }
+    const bfs_status s = prepare(g, (flags & BFS_RESERVE_HOST_OUT) != 0,
+                                 (flags & BFS_RESERVE_NO_PARENT) == 0, stream);
+    if (s == BFS_OK) GB_CK(cudaStreamSynchronize(as_stream(stream)));
+    return s;
+}
+
 extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level_out,
                                       int32_t *parent_out, void *stream) {
     clear_error();
@@ -2555,6 +2998,10 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
         set_error("bfs_run: level_out and parent_out must both be host or both be device memory");
         return BFS_ERR_INVALID;
     }
+    {
+        const bfs_status ps = prepare(g, host_out, parent_out != nullptr, stream);
+        if (ps != BFS_OK) return ps;
+    }
     int32_t *level = level_out, *parent = parent_out;
     const bool async_out = host_out && g->cfg.host_async;
     int slot = 0;
@@ -2562,28 +3009,14 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
         // device outputs used in turn: pair `slot` was last copied two calls ago
         slot = g->hout_turn;
         g->hout_turn ^= 1;
-        if (!g->copy_st) {
-            GB_CK(cudaStreamCreateWithFlags(&g->copy_st, cudaStreamNonBlocking));
-            GB_CK(cudaEventCreateWithFlags(&g->hout_ready, cudaEventDisableTiming));
-            for (int i = 0; i < 2; ++i)
-                GB_CK(cudaEventCreateWithFlags(&g->hout_done[i], cudaEventDisableTiming));
-        }
-        if (!g->hout_level[slot]) {
-            GB_CK(cudaMalloc(&g->hout_level[slot], (size_t)n * 4));
-            GB_CK(cudaMalloc(&g->hout_parent[slot], (size_t)n * 4));
-        }
         GB_CK(cudaEventSynchronize(g->hout_done[slot]));
         level = g->hout_level[slot];
         parent = g->hout_parent[slot];
     } else if (host_out) {
-        if (!g->level_scratch) GB_CK(cudaMalloc(&g->level_scratch, (size_t)n * 4));
         level = g->level_scratch;
         parent = nullptr;
     }
-    if (!parent) {
-        if (!g->parent_scratch) GB_CK(cudaMalloc(&g->parent_scratch, (size_t)n * 4));
-        parent = g->parent_scratch;
-    }
+    if (!parent) parent = g->parent_scratch;
     const bfs_config &cfg = g->cfg;
     const bool timing = cfg.timing != 0;
     const bool all_events = cfg.timing == 1;  // 2: only around the hub sweeps
@@ -2596,36 +3029,6 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
         return g->events[i];
     };
 
-    if (cfg.prune_components && g->comp_rep < 0) {
-        // The component of the highest-degree vertex, found once by one
-        // traversal without pruning, kept as a bitmap.
-        unsigned long long *best = nullptr;
-        unsigned long long hb = 0;
-        GB_CK(cudaMallocAsync(&best, 8, st));
-        GB_CK(cudaMemsetAsync(best, 0, 8, st));
-        GB_LAUNCH(max_degree_kernel, grid_cap(n, kBlock, 8), kBlock, 0, st, g->off, n, best);
-        GB_CK(cudaMemcpyAsync(&hb, best, 8, cudaMemcpyDeviceToHost, st));
-        GB_CK(cudaFreeAsync(best, st));
-        GB_CK(cudaStreamSynchronize(st));
-        const int32_t rep = (int32_t)(0xffffffffull - (hb & 0xffffffffull));
-        if (!g->comp_in) GB_CK(cudaMalloc(&g->comp_in, (size_t)g->nw_pad * 4));
-        if (!g->level_scratch) GB_CK(cudaMalloc(&g->level_scratch, (size_t)n * 4));
-        if (!g->parent_scratch) GB_CK(cudaMalloc(&g->parent_scratch, (size_t)n * 4));
-        const bfs_config saved = g->cfg;
-        g->cfg.prune_components = 0;
-        g->cfg.timing = 0;
-        const bfs_status s = bfs_run(g, rep, g->level_scratch, g->parent_scratch, stream);
-        g->cfg = saved;
-        if (s != BFS_OK) return s;
-        GB_LAUNCH(reached_bits_kernel, grid_cap(g->nw_pad, kBlock, 8), kBlock, 0, st,
-                  g->level_scratch, n, g->nw_pad, g->comp_in);
-        GB_CK(cudaStreamSynchronize(st));
-        g->comp_rep = rep;
-    }
-    if (cfg.bu_head && g->head_kind != cfg.bu_head) {  // head records are built on first use
-        const bfs_status hs = build_head(g, cfg.bu_head, st);
-        if (hs != BFS_OK) return hs;
-    }
     const int hskip = cfg.bu_head == 1 ? 1 : 0;
     g->last.clear();
     uint32_t *front = g->bm_a, *next = g->bm_b;
@@ -2651,15 +3054,41 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
         const bfs_status gs = run_graph_loop(g, level, parent, root, fuse_init ? 0 : 1, st);
         if (gs != BFS_OK) return gs;
     } else {
-        {
-            const bfs_status ps = publish_and_wait(g, g->trace, st);
-            if (ps != BFS_OK) return ps;
-        }
-        int64_t n_f = 1, m_f = g->h_slot[T_MF];
-        int64_t n_u = n - 1, m_u = g->nnz - m_f;
+        // hybrid: stretches of top-down layers run in the persistent kernel
+        // (no host round trip per layer), bottom-up layers from the host
+        const bool hybrid = cfg.device_loop == 4 && !all_events;
+        int64_t n_f = 1, m_f = 0, n_u = n - 1, m_u = 0;
         int cur_bu = 0;
         bool have_queue = true;
         int64_t degree_sum = 0;
+        int d_first = 0;
+        // takes over the state a device stretch ended in
+        auto adopt = [&](const LoopState &s2) {
+            d_first = (int)s2.d;
+            n_f = s2.n_f;
+            m_f = s2.m_f;
+            n_u = s2.n_u;
+            m_u = s2.m_u;
+            degree_sum = s2.degsum;
+            cur_bu = s2.cur_bu;
+            have_queue = s2.have_queue != 0;
+            front = (s2.d & 1) ? g->bm_b : g->bm_a;
+            next = (s2.d & 1) ? g->bm_a : g->bm_b;
+            q_cur = (s2.d & 1) ? g->q_b : g->q_a;
+            q_next = (s2.d & 1) ? g->q_a : g->q_b;
+        };
+        if (hybrid) {
+            LoopState s0;
+            s0.n_u = n - 1;  // m_f < 0: the kernel reads the root's degree
+            const bfs_status ss = run_device_segment(g, level, parent, st, s0, true);
+            if (ss != BFS_OK) return ss;
+            adopt(s0);
+        } else {
+            const bfs_status ps = publish_and_wait(g, g->trace, st);
+            if (ps != BFS_OK) return ps;
+            m_f = g->h_slot[T_MF];
+            m_u = g->nnz - m_f;
+        }
         const int bw = cfg.bu_words;
         const int bsel = (bw == 4 ? 2 : bw - 1) + (cfg.bu_head ? 3 : 0);
         const int64_t bu_full = (int64_t)sm_count() * g->bu_blocks_per_sm[bsel];
@@ -2675,12 +3104,30 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
             filled = true;
             return BFS_OK;
         };
-        for (int d = 0; n_f > 0; ++d) {
+        for (int d = d_first; n_f > 0; ++d) {
             if (d > n) {  // a BFS has at most n layers: the counters are inconsistent
                 set_error("bfs_run: internal error, traversal did not terminate after %lld layers",
                           (long long)n);
                 cudaStreamSynchronize(st);
                 return BFS_ERR_INTERNAL;
+            }
+            if (hybrid && !decide(cfg, cur_bu, d, n, n_f, m_f, n_u, m_u)) {
+                // a top-down layer: the device runs it and the ones after it
+                // up to the next bottom-up decision (or the end)
+                LoopState s1;
+                s1.d = d;
+                s1.n_f = n_f;
+                s1.m_f = m_f;
+                s1.n_u = n_u;
+                s1.m_u = m_u;
+                s1.degsum = degree_sum;
+                s1.cur_bu = cur_bu;
+                s1.have_queue = have_queue ? 1 : 0;
+                const bfs_status ss = run_device_segment(g, level, parent, st, s1, true);
+                if (ss != BFS_OK) return ss;
+                adopt(s1);
+                d = d_first - 1;  // the loop resumes at the layer the stretch stopped at
+                continue;
             }
             cur_bu = decide(cfg, cur_bu, d, n, n_f, m_f, n_u, m_u);
             bfs_layer_stats ls;
@@ -2758,37 +3205,28 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                               kBlock, 0, st, g->off, g->idx, cfg.bu_head ? g->head : nullptr,
                               hskip, q_next, (const unsigned long long *)(slot_cur + T_ULIST),
                               g->visited, front, next, parent, level, d + 1, cfg.bu_probe,
-                              (unsigned long long *)slot_next, slot_zero);
+                              (unsigned long long *)slot_next, slot_zero, 0);
                 } else if (two_pass) {
                     // two passes: hub probes over the words, then the rows of
                     // the vertices whose hub missed, one lane each
                     ls.converted = 3;
-                    if (!g->pend) GB_CK(cudaMalloc(&g->pend, (size_t)g->nw_pad * 4));
                     const bool stream = cfg.hub_stream_stages > 0 &&
                                         active * 100 >= (int64_t)cfg.hub_stream_percent * n;
-                    if (stream && g->hub_stream_occ_stages != cfg.hub_stream_stages) {
-                        const HubStreamFn fn = hub_stream_fn(cfg.hub_stream_stages);
-                        const size_t smem = hub_stream_smem_bytes(cfg.hub_stream_stages);
-                        GB_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)smem));
-                        GB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g->hub_stream_occ, fn,
-                                                                            kBlock, smem));
-                        g->hub_stream_occ_stages = cfg.hub_stream_stages;
-                    }
                     if (timing && !all_events) GB_CK(cudaEventRecord(event(e0 + 1), st));
                     if (stream) {
-                        GB_LAUNCH(hub_stream_fn(cfg.hub_stream_stages),
-                                  grid_cap(g->nw_pad / kHubTileWords, 1, g->hub_stream_occ), kBlock,
-                                  hub_stream_smem_bytes(cfg.hub_stream_stages), st, g->head,
-                                  g->nw_pad, g->visited, front, next, g->pend, parent, level, d + 1,
+                        GB_LAUNCH(hub_stream_fn(cfg.hub_stream_stages, !filled),
+                                  grid_cap(g->nw_pad / kWarpTile, kBlock / 32, g->hub_stream_occ),
+                                  kBlock, hub_stream_smem_bytes(cfg.hub_stream_stages), st,
+                                  g->hubc, g->wrank, g->wmeta, g->nw_pad, g->visited, front, next,
+                                  g->pend, parent, level, d + 1, (unsigned long long *)slot_next,
+                                  slot_zero, n, root);
+                    } else {
+                        GB_LAUNCH(bu_hubc_kernel,
+                                  grid_cap(g->nw_pad, kBlock / 32 * 8, g->hubc_blocks_per_sm),
+                                  kBlock, 0, st, g->hubc, g->wrank, g->nw_pad, g->visited, front,
+                                  next, g->pend, parent, level, d + 1,
                                   (unsigned long long *)slot_next, slot_zero, filled ? 0 : 1,
                                   g->base_vis, n, root);
-                    } else {
-                        GB_LAUNCH(bu_hub_kernel,
-                                  grid_cap(g->nw_pad, kBlock / 32 * 8, g->bu_hub_blocks_per_sm),
-                                  kBlock, 0, st, g->head, g->nw_pad, g->visited, front, next,
-                                  g->pend, parent, level, d + 1, (unsigned long long *)slot_next,
-                                  slot_zero, filled ? 0 : 1, g->base_vis, n, root);
                     }
                     filled = true;
                     if (timing) GB_CK(cudaEventRecord(event(e0 + 3), st));
@@ -2800,7 +3238,7 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                               kBlock, 0, st, g->off, g->idx, nullptr, 0, q_next,
                               (const unsigned long long *)(slot_cur + T_ULIST), g->visited, front,
                               next, parent, level, d + 1, cfg.bu_probe,
-                              (unsigned long long *)slot_next, slot_zero);
+                              (unsigned long long *)slot_next, slot_zero, 1);
                 } else {
                     if (!filled) {
                         const bfs_status fs = fill_outputs();
@@ -2824,7 +3262,11 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                 GB_CK(cudaStreamSynchronize(st));
                 return BFS_ERR_TIMEOUT;
             }
-            const int64_t found = g->h_slot[T_NF], m_new = g->h_slot[T_MF];
+            const int64_t found = g->h_slot[T_NF];
+            // after a two-pass layer T_MF holds e_u after the layer (the
+            // degree sum of the vertices still unvisited): e_f = e_u - that
+            const int64_t m_new =
+                (ls.converted == 3 && cur_bu) ? m_u - g->h_slot[T_MF] : g->h_slot[T_MF];
             ls.examined = cur_bu ? g->h_slot[T_EXAM] : m_f;
             ls.found = found;
             if (ls.converted == 3 && cur_bu) ls.hub_found = g->h_slot[T_HUB];
@@ -2858,18 +3300,6 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
         }
     }
     if (cfg.parent_min) {
-        if (g->rows_sorted < 0) {  // checked once per graph
-            int *flag = nullptr;
-            int h = 1;
-            GB_CK(cudaMallocAsync(&flag, 4, st));
-            GB_CK(cudaMemcpyAsync(flag, &h, 4, cudaMemcpyHostToDevice, st));
-            GB_LAUNCH(rows_sorted_kernel, grid_cap(n, kBlock, 8), kBlock, 0, st, g->off, g->idx, n,
-                      flag);
-            GB_CK(cudaMemcpyAsync(&h, flag, 4, cudaMemcpyDeviceToHost, st));
-            GB_CK(cudaFreeAsync(flag, st));
-            GB_CK(cudaStreamSynchronize(st));
-            g->rows_sorted = h;
-        }
         GB_LAUNCH(min_parent_kernel, grid_cap(n, kBlock, 8), kBlock, 0, st, g->off, g->idx,
                   level, parent, n, root, g->rows_sorted);
         if (!host_out) GB_CK(cudaStreamSynchronize(st));

@@ -40,6 +40,25 @@ bfs_status cuda_status(cudaError_t e, const char *what, const char *file, int li
         GB_CK(cudaGetLastError());                                                   \
     } while (0)
 
+// Device and pinned host allocations, counted behind bfs_alloc_count() so a
+// test can check that a warmed-up (or reserved) path allocates nothing.
+extern std::atomic<int64_t> g_allocs;
+template <typename T>
+inline cudaError_t dev_malloc(T **p, size_t bytes) {
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
+    return cudaMalloc(reinterpret_cast<void **>(p), bytes);
+}
+template <typename T>
+inline cudaError_t dev_malloc_async(T **p, size_t bytes, cudaStream_t st) {
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
+    return cudaMallocAsync(reinterpret_cast<void **>(p), bytes, st);
+}
+template <typename T>
+inline cudaError_t host_malloc(T **p, size_t bytes, unsigned flags = cudaHostAllocDefault) {
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
+    return cudaHostAlloc(reinterpret_cast<void **>(p), bytes, flags);
+}
+
 // Number of SMs of the current device (cached per device).
 int sm_count();
 

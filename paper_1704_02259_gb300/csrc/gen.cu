@@ -385,7 +385,7 @@ struct AsyncBuf {
     void *p = nullptr;
     cudaStream_t st;
     explicit AsyncBuf(cudaStream_t s) : st(s) {}
-    cudaError_t alloc(size_t bytes) { return cudaMallocAsync(&p, bytes ? bytes : 16, st); }
+    cudaError_t alloc(size_t bytes) { return dev_malloc_async(&p, bytes ? bytes : 16, st); }
     ~AsyncBuf() {
         if (p) cudaFreeAsync(p, st);
     }

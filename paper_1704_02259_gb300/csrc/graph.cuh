@@ -35,9 +35,16 @@ struct bfs_graph {
     uint32_t *pend = nullptr;      // vertices whose hub missed (two-pass bottom-up)
     int rows_sorted = -1;          // every CSR row ascending: -1 not checked yet
     int bu_hub_blocks_per_sm = 0;
+    int hubc_blocks_per_sm = 1;    // resident blocks per SM of the compact gather sweep
     int hub_stream_occ = 0;        // resident blocks per SM of the streaming sweep
     int hub_stream_occ_stages = 0; // ... for this stage count (0 = not queried)
     int2 *head = nullptr;          // {first probe (-1 if none), degree}
+    // compact hub records of the degree >= 1 vertices, in id order: hub id,
+    // bit 31 set when the vertex has degree 1; wrank[w] = degree >= 1
+    // vertices before bitmap word w (nw_pad + 1 entries)
+    uint32_t *hubc = nullptr, *wrank = nullptr;
+    uint2 *wmeta = nullptr;        // {base word, wrank} per word, for the streaming sweep
+    int64_t n1 = 0;                // vertices of degree >= 1
     int head_kind = 0;             // what head holds: 1 first neighbour, 2 hub
     uint32_t *comp_in = nullptr;   // vertices in the component of comp_rep
     int32_t comp_rep = -1;         // highest-degree vertex; -1 = not built yet
@@ -53,6 +60,7 @@ struct bfs_graph {
     cudaStream_t copy_st = nullptr;
     int hout_turn = 0;
     int64_t *trace = nullptr;
+    int64_t *misc = nullptr;    // 8 device words for one-off flags and maxima
     int64_t *h_slot = nullptr;  // pinned, kFields entries
     // mapped pinned block the host loop polls: kFields counters then a
     // sequence number, written by publish_kernel (d_pub = device address)

@@ -106,6 +106,7 @@ constexpr int kMsBlock = 256;
 constexpr int kMsBigBatch = 1024;
 constexpr int kMaxRoots = 512;
 constexpr int kMaxSlots = 16;
+constexpr int kPctlLayers = 128;  // layer records of the device loop (depth <= 127)
 
 template <int W>
 struct Lanes {
@@ -876,6 +877,8 @@ __global__ void __launch_bounds__(kMsBlock) ms_persistent_kernel(MsPersist p) {
         int64_t *sn = p.trace + ((d + 1) % kMsRingP) * kMsFieldsP;
         int64_t *sz = p.trace + ((d + 2) % kMsRingP) * kMsFieldsP;
         const int64_t v_f = __ldcg(sc + M_NV), e_f = __ldcg(sc + M_MF);
+        if (d > 0 && d - 1 < kPctlLayers && blockIdx.x == 0 && threadIdx.x == 0)
+            p.layers[(int64_t)(d - 1) * 8 + 6] = __ldcg(sc + M_EXAM);  // the last layer's edges
         if (v_f == 0) break;
         if (d + 1 > 127) {
             status = BFS_ERR_DEPTH;
@@ -982,13 +985,13 @@ bfs_status ensure_ms(bfs_graph *g, int W) {
     }
     MsState *m = g->ms;
     if (!m->list) {
-        GB_CK(cudaMalloc(&m->list, (size_t)g->n * 4));
-        GB_CK(cudaMalloc(&m->big, (size_t)g->n * 4));
-        GB_CK(cudaMalloc(&m->roots, kMaxRoots * 4));
-        GB_CK(cudaMalloc(&m->trace, (size_t)kMsRing * kMsFields * 8));
-        GB_CK(cudaMalloc(&m->live, 3 * 8 * 8));
-        GB_CK(cudaMallocHost(&m->h_slot, 16 * 8));
-        GB_CK(cudaHostAlloc((void **)&m->h_pub, 17 * 8, cudaHostAllocMapped));
+        GB_CK(dev_malloc(&m->list, (size_t)g->n * 4));
+        GB_CK(dev_malloc(&m->big, (size_t)g->n * 4));
+        GB_CK(dev_malloc(&m->roots, kMaxRoots * 4));
+        GB_CK(dev_malloc(&m->trace, (size_t)kMsRing * kMsFields * 8));
+        GB_CK(dev_malloc(&m->live, 3 * 8 * 8));
+        GB_CK(host_malloc(&m->h_slot, 16 * 8));
+        GB_CK(host_malloc((void **)&m->h_pub, 17 * 8, cudaHostAllocMapped));
         GB_CK(cudaHostGetDevicePointer((void **)&m->d_pub, m->h_pub, 0));
         m->h_pub[16] = 0;
     }
@@ -1007,8 +1010,8 @@ bfs_status ensure_ms(bfs_graph *g, int W) {
             GB_CK(cudaMemGetInfo(&fb, &tb));
             lcap = (int)std::max<size_t>(4, std::min<size_t>(kMaxSlots, fb / 4 / slot));
         }
-        GB_CK(cudaMalloc(&m->seen, slot));
-        GB_CK(cudaMalloc(&m->fr, slot * lcap));
+        GB_CK(dev_malloc(&m->seen, slot));
+        GB_CK(dev_malloc(&m->fr, slot * lcap));
         m->W = W;
         m->lcap = lcap;
     }
@@ -1181,6 +1184,7 @@ bfs_status run_batch_w(bfs_graph *g, const int32_t *roots, int k, int8_t *levels
             const bfs_status ps = ms_publish_and_wait(m, slot_next, live_next, st);
             if (ps != BFS_OK) return ps;
         }
+        ls.examined = m->h_slot[M_EXAM];
         m->last.push_back(ls);
         v_f = m->h_slot[M_NV];
         e_f = m->h_slot[M_MF];
@@ -1199,7 +1203,6 @@ bfs_status run_batch_w(bfs_graph *g, const int32_t *roots, int k, int8_t *levels
     return BFS_OK;
 }
 
-constexpr int kPctlLayers = 128;
 constexpr size_t kPctlBytes = kPctlLayers * 8 * 8 + 64;  // records, result, barrier, err
 
 // The same traversal as run_batch_w, as one CUDA graph: clearing, roots and
@@ -1211,8 +1214,8 @@ bfs_status run_batch_graph(bfs_graph *g, const int32_t *roots, int k, int8_t *le
     MsState *m = g->ms;
     const int64_t n = g->n;
     if (!m->pctl) {
-        GB_CK(cudaMalloc(&m->pctl, kPctlBytes));
-        GB_CK(cudaMallocHost(&m->h_pctl, kPctlBytes));
+        GB_CK(dev_malloc(&m->pctl, kPctlBytes));
+        GB_CK(host_malloc(&m->h_pctl, kPctlBytes));
     }
     const bool stale = !m->exec || m->g_W != W || m->g_k != k || m->g_levels != levels ||
                        m->g_seen != m->seen || memcmp(&m->g_cfg, &m->cfg, sizeof m->cfg) != 0;
@@ -1310,6 +1313,7 @@ bfs_status run_batch_graph(bfs_graph *g, const int32_t *roots, int k, int8_t *le
         ls.pairs = rec[3];
         ls.v_u = rec[4];
         ls.e_u = rec[5];
+        ls.examined = rec[6];
         m->last.push_back(ls);
         m->last_pairs += ls.pairs;
     }
@@ -1527,7 +1531,7 @@ extern "C" BFS_API bfs_status bfs_selftest_grid_barrier(int32_t missing_blocks, 
     }
     cudaStream_t st = as_stream(stream);
     int32_t *buf = nullptr;  // bar[2], err, ok
-    GB_CK(cudaMallocAsync(&buf, 16, st));
+    GB_CK(dev_malloc_async(&buf, 16, st));
     const int32_t init[4] = {0, 0, 0, 1};
     int32_t out[4] = {0, 0, 0, 0};
     cudaError_t e = cudaMemcpyAsync(buf, init, 16, cudaMemcpyHostToDevice, st);

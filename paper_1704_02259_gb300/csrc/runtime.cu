@@ -11,6 +11,7 @@
 namespace gbfs {
 
 std::atomic<int64_t> g_launches{0};
+std::atomic<int64_t> g_allocs{0};
 
 static thread_local std::string t_error;
 
@@ -54,4 +55,8 @@ extern "C" BFS_API const char *bfs_last_error(void) { return gbfs::t_error.c_str
 
 extern "C" BFS_API int64_t bfs_launch_count(void) {
     return gbfs::g_launches.load(std::memory_order_relaxed);
+}
+
+extern "C" BFS_API int64_t bfs_alloc_count(void) {
+    return gbfs::g_allocs.load(std::memory_order_relaxed);
 }

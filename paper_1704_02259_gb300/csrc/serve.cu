@@ -55,9 +55,9 @@ __global__ void unpack_row_kernel(const int8_t *__restrict__ row, int64_t n,
 }
 
 // Device bytes a worker's view of an n-vertex graph holds: the single-source
-// scratch (bitmaps, queues) plus the batched lists; view_lane_bytes adds the
-// bitsets for W lane words.
-int64_t view_base_bytes(int64_t n) { return 21 * n + (1 << 16); }
+// scratch (bitmaps, queues, the parent scratch of the depth fallback) plus the
+// batched lists; view_lane_bytes adds the bitsets for W lane words.
+int64_t view_base_bytes(int64_t n) { return 26 * n + (1 << 16); }
 // seen and kViewSlots frontier slots of n * W 64-bit words
 constexpr int kViewSlots = 8;
 int64_t view_lane_bytes(int64_t n, int W) { return 8 * (1 + kViewSlots) * n * (int64_t)W; }
@@ -92,6 +92,7 @@ struct bfs_server {
     std::vector<std::thread> workers;
     std::vector<double> lat_us;
     int64_t completed = 0, failed = 0, batches = 0, deferred = 0, roots_launched = 0;
+    int64_t deep_fallbacks = 0;
     bool any_submit = false;
     clk::time_point first_submit, last_done;
 };
@@ -192,6 +193,12 @@ void worker_main(bfs_server *s, int wid) {
             vc.bu_head = 0;
             status = bfs_graph_create(g_off, g_idx, n, nnz, BFS_DEVICE_PTRS | BFS_BORROW, &vc,
                                       &v);
+            // the single-source fallback below then allocates nothing
+            if (status == BFS_OK) status = bfs_graph_reserve(v, BFS_RESERVE_NO_PARENT, st);
+            if (status != BFS_OK && v) {
+                bfs_graph_destroy(v);
+                v = nullptr;
+            }
             if (status == BFS_OK) {
                 bfs_batch_config bc;
                 bfs_graph_get_batch_config(g_src, &bc);
@@ -205,11 +212,11 @@ void worker_main(bfs_server *s, int wid) {
             cudaFree(staging);
             staging = nullptr;
             staging_n = 0;
-            if (cudaMalloc(&staging, (size_t)n * 4) == cudaSuccess) staging_n = n;
+            if (dev_malloc(&staging, (size_t)n * 4) == cudaSuccess) staging_n = n;
             else status = BFS_ERR_OOM;
         }
         int8_t *rows = nullptr;
-        if (status == BFS_OK && cudaMallocAsync(&rows, (size_t)rows_bytes, st) != cudaSuccess) {
+        if (status == BFS_OK && dev_malloc_async(&rows, (size_t)rows_bytes, st) != cudaSuccess) {
             cudaGetLastError();
             status = BFS_ERR_OOM;
         }
@@ -219,7 +226,23 @@ void worker_main(bfs_server *s, int wid) {
             status = bfs_run_batch(views[gi], roots.data(), k, rows, st);
             if (status == BFS_OK) view_w[gi] = std::max(view_w[gi], lane_words(k));
         }
-        if (status == BFS_OK) {
+        int deep = 0;
+        if (status == BFS_ERR_DEPTH) {
+            // The batch went deeper than an int8 level holds (127): each of
+            // its queries is answered by the single-source traversal, which
+            // has no depth limit and writes int32 levels directly.
+            status = BFS_OK;
+            for (int i = 0; i < k && status == BFS_OK; ++i) {
+                Req *r = batch[i];
+                int32_t *dst = r->out_host ? staging : r->out;
+                status = bfs_run(views[gi], r->root, dst, nullptr, st);
+                if (status == BFS_OK && r->out_host &&
+                    cudaMemcpyAsync(r->out, staging, (size_t)n * 4, cudaMemcpyDeviceToHost, st) !=
+                        cudaSuccess)
+                    status = BFS_ERR_CUDA;
+            }
+            deep = k;
+        } else if (status == BFS_OK) {
             const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
             for (int i = 0; i < k && status == BFS_OK; ++i) {
                 Req *r = batch[i];
@@ -240,6 +263,7 @@ void worker_main(bfs_server *s, int wid) {
         s->mem_used -= rows_bytes;
         if (status != BFS_OK) s->mem_used -= keep_bytes;  // nothing new is kept on failure
         s->running -= 1;
+        s->deep_fallbacks += deep;
         const clk::time_point now = clk::now();
         for (Req *r : batch) finish(s, r, status, now);
         s->cv_done.notify_all();
@@ -387,6 +411,7 @@ extern "C" BFS_API bfs_status bfs_serve_stats_get(bfs_server *s, bfs_serve_stats
     o->failed = s->failed;
     o->batches = s->batches;
     o->deferred = s->deferred;
+    o->deep_fallbacks = s->deep_fallbacks;
     o->mean_batch = s->batches ? (double)s->roots_launched / s->batches : 0.0;
     if (!s->lat_us.empty()) {
         std::vector<double> v = s->lat_us;
@@ -412,6 +437,7 @@ extern "C" BFS_API bfs_status bfs_serve_stats_reset(bfs_server *s) {
     std::lock_guard<std::mutex> lk(s->mu);
     s->lat_us.clear();
     s->completed = s->failed = s->batches = s->deferred = s->roots_launched = 0;
+    s->deep_fallbacks = 0;
     s->any_submit = false;
     return BFS_OK;
 }

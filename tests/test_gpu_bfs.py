@@ -69,7 +69,7 @@ FORCED = {"td": [0], "bu": [1], "alt": [0, 1] * 32, "alt2": [1, 0] * 32,
                                   "union", "single", "ragged"])
 @pytest.mark.parametrize("pat", list(FORCED))
 @pytest.mark.parametrize("prune", [0, 1])
-@pytest.mark.parametrize("loop", [0, 1, 3])
+@pytest.mark.parametrize("loop", [0, 1, 3, 4])
 def test_closed_form_graphs_forced_directions(name, pat, prune, loop):
     if name == "path":
         n, (s, d) = 77, inputs.path_edges(77)
@@ -112,7 +112,7 @@ def test_policies_on_skewed_graphs(seed, policy, claim):
     o_off, o_idx, g = make(n, s, d, policy=policy, td_claim=claim, bu_words=[1, 2, 4][seed % 3],
                            bu_head=(seed // 2 + claim) % 3, prune_components=(seed + claim) % 2,
                            bu_list_percent=[0, 10, 100][(seed + claim) % 3],
-                           device_loop=[0, 1, 3][(seed + 2 * claim) % 3])
+                           device_loop=[0, 1, 3, 4][(seed + 2 * claim) % 4])
     for r in oracle.sample_roots(o_off, n, seed, 4):
         check_run(o_off, o_idx, g, int(r), policy=policy)
 
@@ -215,7 +215,7 @@ def test_large_top_down_layers(pat, loop):
 
 @pytest.mark.parametrize("cfg", [dict(), dict(forced=[0, 0, 1]), dict(forced=[1]),
                                  dict(bu_list_percent=100), dict(forced=[0])])
-@pytest.mark.parametrize("loop", [0, 3])
+@pytest.mark.parametrize("loop", [0, 3, 4])
 def test_outputs_written_by_first_sweep(cfg, loop):
     # scale 21 with the host loop: dense bottom-up layers run in two passes
     # and (td_claim = 1) the first hub sweep writes the -1 of every vertex not
@@ -242,6 +242,87 @@ def test_outputs_written_by_first_sweep(cfg, loop):
         assert oracle.check_parents(o_off, o_idx, r, got, par) == 0
         assert (par[ref < 0] == -1).all()
     check_run(o_off, o_idx, g, roots[0], forced=cfg.get("forced"))
+
+
+_R21 = {}
+
+
+def _rmat21_seed11():
+    if not _R21:
+        _R21["g"] = _rmat_both(21, 16, 11)
+    return _R21["g"]
+
+
+@pytest.mark.parametrize("stages", [0, 2, 3, 4, 6, 8])
+@pytest.mark.parametrize("percent", [0, 50])
+def test_streaming_hub_sweep(stages, percent):
+    # scale 21 (two-pass bottom-up layers): the hub sweep that streams whole
+    # tiles of head records through shared memory (every sweep at percent 0,
+    # only the dense ones at 50) gives the same levels, bottom-up parents,
+    # counters and -1 outputs as the oracle's hub-first Alg. 3 run
+    n, o_off, o_idx, g_off, g_idx = _rmat21_seed11()
+    g = gb.Graph(g_off, g_idx, config(device_loop=0, hub_stream_stages=stages,
+                                      hub_stream_percent=percent))
+    deg = np.diff(o_off)
+    roots = [int(r) for r in oracle.sample_roots(o_off, n, 5, 3)]
+    roots.append(int(np.nonzero(deg == 0)[0][0]))
+    lv = torch.full((n,), 77, dtype=torch.int32, device="cuda")
+    pa = torch.full((n,), 77, dtype=torch.int32, device="cuda")
+    for r in roots:
+        lv.fill_(77)
+        pa.fill_(77)       # stale values that must all be overwritten
+        g.run(r, lv, pa)
+        torch.cuda.synchronize()
+        got, par = lv.cpu().numpy(), pa.cpu().numpy()
+        ref, _ = oracle.bfs(o_off, o_idx, r)
+        assert np.array_equal(got, ref)
+        assert oracle.check_parents(o_off, o_idx, r, got, par) == 0
+        assert (par[ref < 0] == -1).all()
+    for r in roots[:2]:
+        check_run(o_off, o_idx, g, r)
+        assert any(x["converted"] == 3 for x in g.stats().layers)
+
+
+@pytest.mark.parametrize("cfg", [dict(), dict(device_loop=1), dict(device_loop=3),
+                                 dict(parent_min=1), dict(prune_components=1),
+                                 dict(host_async=1), dict(timing=1), dict(bu_head=1)])
+def test_reserved_runs_allocate_nothing(cfg):
+    # after bfs_graph_reserve, traversals under that configuration make no
+    # device or pinned allocation in the library (scale 21: two-pass layers)
+    n, o_off, o_idx, g_off, g_idx = _rmat21_seed11()
+    g = gb.Graph(g_off, g_idx, config(**cfg))
+    host = cfg.get("host_async", 0) == 1
+    g.reserve(host_out=host, no_parent=True)
+    roots = [int(r) for r in oracle.sample_roots(o_off, n, 7, 3)]
+    if host:
+        bufs = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in range(2)]
+    else:
+        bufs = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in range(2)]
+    before = gb.alloc_count()
+    for r in roots:
+        g.run(r, bufs[0], bufs[1])
+        g.run(r, bufs[0], None, want_parent=False)
+    g.sync()
+    torch.cuda.synchronize()
+    assert gb.alloc_count() == before, "bfs_run allocated after bfs_graph_reserve"
+    ref, _ = oracle.bfs(o_off, o_idx, roots[-1])
+    assert np.array_equal(bufs[0].cpu().numpy(), ref)
+
+
+def test_first_run_allocates_then_warm_runs_do_not():
+    # without a reserve call the first traversal of a configuration may
+    # allocate (host-output scratch here); the warmed-up ones do not
+    n, o_off, o_idx, g_off, g_idx = _rmat21_seed11()
+    g = gb.Graph(g_off, g_idx)
+    lv = torch.empty(n, dtype=torch.int32)
+    pa = torch.empty(n, dtype=torch.int32)
+    a0 = gb.alloc_count()
+    g.run(0, lv, pa)
+    a1 = gb.alloc_count()
+    assert a1 > a0
+    for r in (1, 2, 3):
+        g.run(r, lv, pa)
+    assert gb.alloc_count() == a1
 
 
 @pytest.mark.parametrize("kind,seed", [(oracle.RMAT, 1), (oracle.ER, 3)])
@@ -561,17 +642,22 @@ def test_graph_loop_layer_records_equal_host_loop(scale):
     # the same decisions and the same per-layer variant (queue rebuilt,
     # list, two-pass) and hub hits as the host-driven loop
     n, o_off, o_idx, g_off, g_idx = _rmat_both(scale, 16, 3)
+    # (and so does the hybrid loop, whose top-down stretches run on the device)
     gh = gb.Graph(g_off, g_idx, config(device_loop=0))
     g3 = gb.Graph(g_off, g_idx, config(device_loop=3))
+    g4 = gb.Graph(g_off, g_idx, config(device_loop=4))
+    keys = ("direction", "converted", "n_f", "m_f", "n_u", "m_u", "examined", "found",
+            "hub_found")
     for r in oracle.sample_roots(o_off, n, 11, 6):
         lh, ph = run_gpu(gh, int(r))
-        l3, p3 = run_gpu(g3, int(r))
-        assert np.array_equal(lh, l3)
-        assert oracle.check_parents(o_off, o_idx, int(r), l3, p3) == 0
-        keys = ("direction", "converted", "n_f", "m_f", "n_u", "m_u", "examined", "found",
-                "hub_found")
-        assert [{k: x[k] for k in keys} for x in g3.stats().layers] == \
-            [{k: x[k] for k in keys} for x in gh.stats().layers]
+        recs_h = [{k: x[k] for k in keys} for x in gh.stats().layers]
+        ce_h = gh.stats().component_edges
+        for gx in (g3, g4):
+            lx, px = run_gpu(gx, int(r))
+            assert np.array_equal(lh, lx)
+            assert oracle.check_parents(o_off, o_idx, int(r), lx, px) == 0
+            assert [{k: x[k] for k in keys} for x in gx.stats().layers] == recs_h
+            assert gx.stats().component_edges == ce_h
 
 
 def test_timing_modes():

@@ -81,6 +81,39 @@ def test_each_result_same_alone_and_in_the_mix(graphs):
     srv.close()
 
 
+def test_deep_queries_fall_back_to_single_source(graphs):
+    # a 400-vertex path is 399 levels deep from its end, more than an int8
+    # batch level holds: the batch returns BFS_ERR_DEPTH inside the worker,
+    # which answers each of its queries with the single-source traversal;
+    # mixed with ordinary queries of the other graphs, every result equals
+    # the oracle's
+    from tests import inputs
+    n = 400
+    s, d = inputs.path_edges(n)
+    o_off, o_idx, g_off, g_idx = both_csr(n, s, d)
+    path = (n, o_off, o_idx, gb.Graph(g_off, g_idx))
+    allg = graphs + [path]
+    srv, ids = server_with(allg, workers=2, max_batch=8)
+    rng = np.random.default_rng(3)
+    reqs = []
+    for i in range(60):
+        gi = len(allg) - 1 if i % 3 == 0 else int(rng.integers(0, len(graphs)))
+        nn = allg[gi][0]
+        root = [0, n - 1, 150, 300][i % 4] if gi == len(allg) - 1 else int(rng.integers(0, nn))
+        out = (torch.full((nn,), 99, dtype=torch.int32).pin_memory() if i % 2 else
+               torch.full((nn,), 99, dtype=torch.int32, device="cuda"))
+        reqs.append((gi, root, out, srv.submit(ids[gi], root, out)))
+    for gi, root, out, t in reqs:
+        assert srv.wait(t) == 0
+    torch.cuda.synchronize()
+    for gi, root, out, t in reqs:
+        assert np.array_equal(out.cpu().numpy(), expected(allg, gi, root)), (gi, root)
+    assert (expected(allg, len(allg) - 1, 0) == np.arange(n)).all()   # depth 399
+    st = srv.stats()
+    assert st["failed"] == 0 and st["deep_fallbacks"] >= 1
+    srv.close()
+
+
 def test_poisson_stream_reports_latency(graphs):
     srv, ids = server_with(graphs, workers=2, max_batch=128)
     rng = np.random.default_rng(1)

@@ -46,8 +46,11 @@ def _check_against_both(o_off, o_idx, off, idx, roots):
         ref_lv, _ = g.run(int(r))
         level.fill_(123)
         parent.fill_(456)
+        torch.cuda.synchronize()
+        a0 = gb.alloc_count()
         gb.run_noalloc(off, idx, int(r), level, parent)
         torch.cuda.synchronize()
+        assert gb.alloc_count() == a0, "bfs_run_noalloc allocated"
         lv = level.cpu().numpy()
         want, _ = oracle.bfs(o_off, o_idx, int(r))
         assert np.array_equal(lv, want), f"levels differ from the oracle (root {r})"
