@@ -1029,7 +1029,24 @@ __device__ __forceinline__ void bu_list_phase(
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int64_t my_nf = 0, my_mf = 0, my_ex = 0;
-    for (int64_t base = gw * 32; base < cnt; base += tw * 32) {
+    // Without head records (the row scans of the two-pass step) a lane's
+    // list entry is loaded two iterations ahead and its row bounds one
+    // iteration ahead, so an iteration's dependent chain is only row entries
+    // then frontier words.
+    const bool ahead = head == nullptr;
+    const int64_t wstride = tw * 32;
+    int32_t v_n1 = 0, v_n2 = 0;
+    int64_t b_n1 = 0, e_n1 = 0;
+    if (ahead) {
+        const int64_t i1 = gw * 32 + lane, i2 = i1 + wstride;
+        if (i1 < cnt) {
+            v_n1 = ld<CO>(list + i1);
+            b_n1 = off[v_n1];
+            e_n1 = off[v_n1 + 1];
+        }
+        if (i2 < cnt) v_n2 = ld<CO>(list + i2);
+    }
+    for (int64_t base = gw * 32; base < cnt; base += wstride) {
         const int64_t i = base + lane;
         const bool have = i < cnt;
         int32_t v = 0;
@@ -1037,7 +1054,18 @@ __device__ __forceinline__ void bu_list_phase(
         int deg = 0, ex = 0;
         bool found = false;
         int32_t p = -1;
-        if (have) {
+        if (have && ahead) {
+            v = v_n1;
+            row = idx + b_n1;
+            deg = (int)(e_n1 - b_n1);
+            // move the window: bounds of the next entry, the entry after it
+            if (i + wstride < cnt) {
+                b_n1 = off[v_n2];
+                e_n1 = off[v_n2 + 1];
+            }
+            v_n1 = v_n2;
+            v_n2 = i + 2 * wstride < cnt ? ld<CO>(list + i + 2 * wstride) : 0;
+        } else if (have) {
             v = ld<CO>(list + i);
             if (head) {
                 const int2 h = __ldg(head + v);
@@ -1323,10 +1351,12 @@ __device__ __forceinline__ void bulk_g2s_hint(void *dst, const void *src, unsign
 // compact records, its visited words and its {base, rank} words), each
 // stage completing on its own mbarrier. No block-wide barrier: a warp
 // waits only for its own copies and its own frontier loads.
-constexpr int kWarpTile = 8;                                 // bitmap words per warp tile
+constexpr int kWarpTile = 8;  // bitmap words per warp tile (a multiple of 4, dividing 32)
 constexpr unsigned kWarpRecBytes = (kWarpTile * 32 + 8) * 4;  // records, 16-byte rounded
 constexpr unsigned kWarpStageBytes = kWarpRecBytes + kWarpTile * 4 + kWarpTile * 8;
 static_assert(kWarpStageBytes % 16 == 0, "stages keep bulk-copy destinations 16-byte aligned");
+static_assert(kWarpTile % 4 == 0 && 32 % kWarpTile == 0, "tiles of 16-byte word groups that "
+              "never cross nw_pad (a multiple of 32)");
 
 // Predicated global accesses written as one predicated instruction each.
 __device__ __forceinline__ uint32_t ld_hint_if(const uint32_t *p, uint64_t pol, bool pred) {
@@ -1349,7 +1379,7 @@ constexpr size_t hub_stream_smem() {
 }
 
 template <int S, bool INIT>
-__global__ void __launch_bounds__(kBlock, 4) bu_hubc_stream_kernel(
+__global__ void __launch_bounds__(kBlock, 3) bu_hubc_stream_kernel(
     const uint32_t *__restrict__ hubc, const uint32_t *__restrict__ wrank,
     const uint2 *__restrict__ wmeta, int64_t nw_pad, uint32_t *__restrict__ visited,
     const uint32_t *__restrict__ front, uint32_t *__restrict__ next_bm,
@@ -1476,12 +1506,14 @@ __global__ void __launch_bounds__(kBlock, 4) bu_hubc_stream_kernel(
             uint4 *nx = reinterpret_cast<uint4 *>(next_bm + t * kWarpTile);
             uint4 *pd = reinterpret_cast<uint4 *>(pend + t * kWarpTile);
             uint4 *vs = reinterpret_cast<uint4 *>(visited + t * kWarpTile);
-            nx[0] = make_uint4(fbw[0], fbw[1], fbw[2], fbw[3]);
-            nx[1] = make_uint4(fbw[4], fbw[5], fbw[6], fbw[7]);
-            pd[0] = make_uint4(pbw[0], pbw[1], pbw[2], pbw[3]);
-            pd[1] = make_uint4(pbw[4], pbw[5], pbw[6], pbw[7]);
-            vs[0] = make_uint4(vw[0] | fbw[0], vw[1] | fbw[1], vw[2] | fbw[2], vw[3] | fbw[3]);
-            vs[1] = make_uint4(vw[4] | fbw[4], vw[5] | fbw[5], vw[6] | fbw[6], vw[7] | fbw[7]);
+#pragma unroll
+            for (int q = 0; q < kWarpTile / 4; ++q) {
+                const int k = 4 * q;
+                nx[q] = make_uint4(fbw[k], fbw[k + 1], fbw[k + 2], fbw[k + 3]);
+                pd[q] = make_uint4(pbw[k], pbw[k + 1], pbw[k + 2], pbw[k + 3]);
+                vs[q] = make_uint4(vw[k] | fbw[k], vw[k + 1] | fbw[k + 1], vw[k + 2] | fbw[k + 2],
+                                   vw[k + 3] | fbw[k + 3]);
+            }
         }
         __syncwarp();  // the warp is done with stage s
         if (lane == 0) {
