@@ -78,14 +78,15 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def hub_sweep_bytes(n, probed, written):
+def hub_sweep_bytes(n, probed, written, out_bytes=8):
     """Algorithmic bytes of one hub sweep launch (compact records): the
     visited words read and the next, pend and visited words written (n/8
     bytes each), the base and rank words read (n/4), one 4-byte hub record
-    per probed vertex (unvisited, degree >= 1), and 8 bytes (parent, level)
-    per written vertex: the hub hits, or in the first sweep of a traversal
-    every vertex not reached before it."""
-    return 3 * n / 4 + 4 * probed + 8 * written
+    per probed vertex (unvisited, degree >= 1), and out_bytes per written
+    vertex (the hub hits, or in the first sweep of a traversal every vertex
+    not reached before it): 8 for parent and level, 4 for the parent alone
+    when the levels are written by the level pass after the traversal."""
+    return 3 * n / 4 + 4 * probed + out_bytes * written
 
 
 def one_sweep_bytes(n, nnz):
@@ -878,7 +879,8 @@ def main():
                 name = "bu_hubc_stream_kernel" if stream else "bu_hubc_kernel"
                 e = sweeps.setdefault(name, {"bytes": 0.0, "ms": 0.0, "launches": 0,
                                              "first": 0})
-                e["bytes"] += hub_sweep_bytes(n, active, written)
+                e["bytes"] += hub_sweep_bytes(n, active, written,
+                                              4 if cfg.level_pass else 8)
                 e["ms"] += L["ms_sweep"]
                 e["launches"] += 1
                 e["first"] += 1 if first_sweep else 0

@@ -229,6 +229,16 @@ typedef struct bfs_config {
     int32_t hub_stream_percent; /* a hub sweep streams when at least this
                                 percentage of n vertices is still to find
                                 (unvisited, degree > 0); 0..100              */
+    int32_t level_pass;      /* host loop: 1 = the layers do not
+                                store levels; each layer's frontier bitmap is
+                                kept in a ring of 16 (2n bytes) and one pass
+                                after the traversal writes every level as
+                                whole rows, so the scattered 4-byte level
+                                stores of later layers (and the sector fills
+                                they cost) disappear; a traversal that reaches
+                                layer 15 writes the levels so far and stores
+                                the rest as found. 0 (default) = levels
+                                stored as found                              */
 } bfs_config;
 
 /* Fills `cfg` with the defaults (edge policy, alpha 20, beta 200, hub head

@@ -47,7 +47,7 @@ class Config(ctypes.Structure):
                 ("prune_components", ctypes.c_int32), ("bu_list_percent", ctypes.c_int32),
                 ("device_loop", ctypes.c_int32), ("host_async", ctypes.c_int32),
                 ("parent_min", ctypes.c_int32), ("hub_stream_stages", ctypes.c_int32),
-                ("hub_stream_percent", ctypes.c_int32)]
+                ("hub_stream_percent", ctypes.c_int32), ("level_pass", ctypes.c_int32)]
 
 
 class LayerStats(ctypes.Structure):

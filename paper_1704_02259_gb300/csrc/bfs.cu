@@ -355,7 +355,7 @@ __device__ __forceinline__ void out_fill_phase(int64_t n, int32_t root,
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += stride) {
         const uint32_t reached = visited[v >> 5] & ~base[v >> 5];
         if (v != root && !((reached >> (v & 31)) & 1u)) {
-            level[v] = -1;
+            if (level) level[v] = -1;
             parent[v] = -1;
         }
     }
@@ -365,6 +365,47 @@ __global__ void out_fill_kernel(int64_t n, int32_t root, const uint32_t *__restr
                                 const uint32_t *__restrict__ base,
                                 int32_t *__restrict__ level, int32_t *__restrict__ parent) {
     out_fill_phase(n, root, visited, base, level, parent);
+}
+
+// Level pass: the levels of a traversal whose layers kept their frontier
+// bitmaps in a ring (slot j = the vertices of level j, j < slots <= 16):
+// vertex v gets the j whose slot holds it, or -1 when no slot does (each
+// vertex is in at most one). A warp covers 8 consecutive words per round:
+// lane j loads slot j's 8 words (two 16-byte loads); for each word, OR
+// reductions over the lanes give the union of the slots and the 4 bit planes
+// of j (plane p = OR of the slots whose j has bit p), from which lane i reads
+// vertex i's level; the level stores are whole 128-byte rows.
+static_assert(kLevelRing <= 16, "the level pass reads levels as 4 bit planes");
+__global__ void level_pass_kernel(const uint32_t *__restrict__ ring, int64_t nw_pad, int slots,
+                                  int64_t n, int32_t *__restrict__ level) {
+    constexpr int R = 8;
+    static_assert(32 % R == 0, "a round's R words must not cross nw_pad (a multiple of 32)");
+    const unsigned lane = lane_id();
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w0 = gw * R; w0 < nw_pad && w0 * 32 < n; w0 += tw * R) {
+        uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
+        if ((int)lane < slots) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(ring + (int64_t)lane * nw_pad + w0);
+            lo = __ldg(src);
+            hi = __ldg(src + 1);
+        }
+        const uint32_t x[R] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const uint32_t any = __reduce_or_sync(0xffffffffu, x[k]);
+            const uint32_t p0 = __reduce_or_sync(0xffffffffu, (lane & 1u) ? x[k] : 0u);
+            const uint32_t p1 = __reduce_or_sync(0xffffffffu, (lane & 2u) ? x[k] : 0u);
+            const uint32_t p2 = __reduce_or_sync(0xffffffffu, (lane & 4u) ? x[k] : 0u);
+            const uint32_t p3 = __reduce_or_sync(0xffffffffu, (lane & 8u) ? x[k] : 0u);
+            const int lv = ((any >> lane) & 1u)
+                               ? (int)(((p0 >> lane) & 1u) | (((p1 >> lane) & 1u) << 1) |
+                                       (((p2 >> lane) & 1u) << 2) | (((p3 >> lane) & 1u) << 3))
+                               : -1;
+            const int64_t v = (w0 + k) * 32 + lane;
+            if (v < n) __stcs(level + v, lv);
+        }
+    }
 }
 
 __device__ __forceinline__ void block_add4(int64_t a, int64_t b, int64_t c, int64_t e,
@@ -471,7 +512,7 @@ __device__ __forceinline__ void td_visit(const TdArgs &a, const bool (&valid)[K]
         if (won[k]) {
             atomicOr(a.next_bm + (v[k] >> 5), 1u << (v[k] & 31));
             if (!a.defer) {
-                a.level[v[k]] = a.new_level;
+                if (a.level) a.level[v[k]] = a.new_level;
                 mf += deg_of(a.off, v[k]);
                 nf += 1;
             }
@@ -717,7 +758,7 @@ __device__ __forceinline__ void td_post_phase(const int64_t *__restrict__ off,
             const bool on = (x[k] >> lane) & 1u;
             b[k] = on ? off[v] : 0;
             e[k] = on ? off[v + 1] : 0;
-            if (on) level[v] = new_level;
+            if (on && level) level[v] = new_level;
         }
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
@@ -922,7 +963,7 @@ __device__ __forceinline__ void bu_phase(
                 const unsigned fm = __ballot_sync(0xffffffffu, found[k]);
                 if (found[k]) {
                     parent[v] = p[k];
-                    level[v] = new_level;
+                    if (level) level[v] = new_level;
                     my_mf += deg[k];
                 }
                 my_ex += ex[k];
@@ -1148,7 +1189,7 @@ __device__ __forceinline__ void bu_list_phase(
         if (found) {
             const uint32_t bit = 1u << (v & 31);
             parent[v] = p;
-            level[v] = new_level;
+            if (level) level[v] = new_level;
             atomicOr(next_bm + (v >> 5), bit);
             atomicOr(visited + (v >> 5), bit);
             if (!mf_left) my_mf += deg;
@@ -1213,7 +1254,7 @@ __device__ __forceinline__ void bu_hub_phase(
                                !(((vw[k] & ~__ldg(base + w0 + k)) >> lane) & 1u);
             if (found || minus) {
                 parent[v] = found ? h[k].x : -1;
-                level[v] = found ? new_level : -1;
+                if (level) level[v] = found ? new_level : -1;
             }
             if (found) {
                 my_mf += h[k].y;
@@ -1467,7 +1508,9 @@ __global__ void __launch_bounds__(kBlock, 3) bu_hubc_stream_kernel(
         // root of degree 0 is not "reached before" by the bitmaps)
         const int64_t vbase = t * (kWarpTile * 32);
         int32_t *const par_t = parent + vbase + lane;
-        int32_t *const lev_t = level + vbase + lane;
+        // level null: levels are written after the traversal (level pass)
+        const bool lev_on = level != nullptr;
+        int32_t *const lev_t = (lev_on ? level : parent) + vbase + lane;  // stores need lev_on
         int lim = 0, rloc = -1;
         if constexpr (INIT) {
             lim = (int)min((int64_t)(kWarpTile * 32), n - vbase) - (int)lane;
@@ -1487,10 +1530,10 @@ __global__ void __launch_bounds__(kBlock, 3) bu_hubc_stream_kernel(
                 const bool minus = !found && !(vw[k] & ~bw[k] & bit) && k * 32 < lim &&
                                    k * 32 != rloc;
                 st_cs_if(par_t + k * 32, found ? hub : -1, found || minus);
-                st_cs_if(lev_t + k * 32, found ? new_level : -1, found || minus);
+                st_cs_if(lev_t + k * 32, found ? new_level : -1, (found || minus) && lev_on);
             } else {
                 st_cs_if(par_t + k * 32, hub, found);
-                st_cs_if(lev_t + k * 32, new_level, found);
+                st_cs_if(lev_t + k * 32, new_level, found && lev_on);
             }
         }
         if (lane == 0) {
@@ -1555,7 +1598,7 @@ __device__ __forceinline__ void hubc_word(
     const bool minus = !found && init_out && v < n && v != root && !(((vw & ~bw) >> lane) & 1u);
     if (found || minus) {
         __stcs(parent + v, found ? hub : -1);
-        __stcs(level + v, found ? new_level : -1);
+        if (level) __stcs(level + v, found ? new_level : -1);
     }
     const unsigned fb = __ballot_sync(0xffffffffu, found);
     const unsigned pb = __ballot_sync(0xffffffffu, probed && !found && !deg1);
@@ -1746,6 +1789,7 @@ bool config_ok(const bfs_config &c) {
         c.hub_stream_stages != 4 && c.hub_stream_stages != 6 && c.hub_stream_stages != 8)
         return false;
     if (c.hub_stream_percent < 0 || c.hub_stream_percent > 100) return false;
+    if (c.level_pass != 0 && c.level_pass != 1) return false;
     return true;
 }
 
@@ -2629,6 +2673,7 @@ void free_graph(bfs_graph *g) {
     free_graph_loop(g);
     cudaFree(g->bm_a);
     cudaFree(g->bm_b);
+    cudaFree(g->ring);
     cudaFree(g->pend);
     cudaFree(g->q_a);
     cudaFree(g->q_b);
@@ -2742,6 +2787,10 @@ extern "C" BFS_API void bfs_config_default(bfs_config *c) {
     // measured at scale 26: 2 stages per warp, every two-pass sweep streamed
     c->hub_stream_stages = 2;
     c->hub_stream_percent = 0;
+    // measured at scale 26: 1033 GTEPS storing levels as found, 1007 with the
+    // level pass (the first hub sweep writes whole rows anyway, and the pass
+    // rewrites every level)
+    c->level_pass = 0;
 }
 
 extern "C" BFS_API bfs_status bfs_graph_create(const int64_t *offsets, const int32_t *indices,
@@ -2973,6 +3022,11 @@ static bfs_status prepare(bfs_graph *g, bool host_out, bool have_parent, void *s
         GB_CK(dev_malloc(&g->pctl, kPctlSsBytes));
         GB_CK(host_malloc(&g->h_pctl, kPctlSsBytes));
     }
+    const bool host_loop = !(cfg.device_loop == 1 || cfg.device_loop == 4 ||
+                             (cfg.device_loop == 2 && n <= kDeviceLoopAutoMaxN) ||
+                             (cfg.device_loop == 3 && cfg.timing == 0));
+    if (cfg.level_pass && host_loop && !g->ring)
+        GB_CK(dev_malloc(&g->ring, (size_t)kLevelRing * g->nw_pad * 4));
     if (cfg.device_loop == 3 && cfg.timing == 0) {
         if (g->gl_exec &&
             memcmp(&((const GlStatic *)g->gl_static)->cfg, &g->cfg, sizeof g->cfg) != 0)
@@ -3063,11 +3117,15 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
 
     const int hskip = cfg.bu_head == 1 ? 1 : 0;
     g->last.clear();
-    uint32_t *front = g->bm_a, *next = g->bm_b;
     int32_t *q_cur = g->q_a, *q_next = g->q_b;
     const bool dev_loop = cfg.device_loop == 1 || (cfg.device_loop == 2 && n <= kDeviceLoopAutoMaxN);
     // the graph loop has no per-layer events: timed runs take the host loop
     const bool graph_loop = cfg.device_loop == 3 && !timing;
+    // level pass (host loop): the frontiers stay in the ring, levels are
+    // written once at the end (or at the flush before the ring wraps)
+    const bool lpass = cfg.level_pass && !dev_loop && !graph_loop && cfg.device_loop != 4;
+    uint32_t *front = lpass ? g->ring : g->bm_a;
+    uint32_t *next = lpass ? g->ring + g->nw_pad : g->bm_b;
     // dense bottom-up layers run in two passes on hub records
     const bool two_pass =
         cfg.bu_head == 2 &&
@@ -3130,9 +3188,11 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                                  bu_full));
         const int64_t td_warps = (int64_t)sm_count() * g->td_blocks_per_sm * (kBlock / 32);
         bool filled = !fuse_init;  // outputs of unreached vertices hold -1
+        bool level_direct = !lpass;  // the layers store levels themselves
+        int32_t *lvl = level_direct ? level : nullptr;
         auto fill_outputs = [&]() -> bfs_status {
             GB_LAUNCH(out_fill_kernel, grid_cap(n, kBlock, 8), kBlock, 0, st, n, root, g->visited,
-                      g->base_vis, level, parent);
+                      g->base_vis, lvl, parent);
             filled = true;
             return BFS_OK;
         };
@@ -3142,6 +3202,14 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                           (long long)n);
                 cudaStreamSynchronize(st);
                 return BFS_ERR_INTERNAL;
+            }
+            if (!level_direct && d + 1 >= kLevelRing) {
+                // the next frontier would reuse slot 0: write the levels of
+                // layers 0..d now and let the layers store theirs from here
+                GB_LAUNCH(level_pass_kernel, grid_cap(g->nw_pad, kBlock / 32 * 8, 8), kBlock, 0, st,
+                          g->ring, g->nw_pad, d + 1, n, level);
+                level_direct = true;
+                lvl = level;
             }
             if (hybrid && !decide(cfg, cur_bu, d, n, n_f, m_f, n_u, m_u)) {
                 // a top-down layer: the device runs it and the ones after it
@@ -3188,7 +3256,7 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                 // queue is rebuilt by b2q if the next layer is top-down too.
                 const int queue_mode = m_f <= kQueueModeMaxEdges ? 1 : 0;
                 const int defer = td_defer(queue_mode, n_u - g->deg0, g->nw);
-                TdArgs a{g->off, g->idx, g->visited, next, parent, level, q_next,
+                TdArgs a{g->off, g->idx, g->visited, next, parent, lvl, q_next,
                          (unsigned long long *)(slot_next + T_NF), d + 1, queue_mode, cfg.td_claim,
                          defer};
                 // Entries per warp so that a small frontier still covers the GPU,
@@ -3213,7 +3281,7 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                 }
                 if (defer)
                     GB_LAUNCH(td_post_kernel, grid_cap(g->nw, kBlock / 4, 8), kBlock, 0, st,
-                              g->off, next, g->nw, level, d + 1,
+                              g->off, next, g->nw, lvl, d + 1,
                               (unsigned long long *)(slot_next + T_NF),
                               (unsigned long long *)(slot_next + T_MF));
                 have_queue = queue_mode != 0;
@@ -3236,7 +3304,7 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                               grid_cap((active + 31) / 32, kBlock / 32, g->bu_list_blocks_per_sm),
                               kBlock, 0, st, g->off, g->idx, cfg.bu_head ? g->head : nullptr,
                               hskip, q_next, (const unsigned long long *)(slot_cur + T_ULIST),
-                              g->visited, front, next, parent, level, d + 1, cfg.bu_probe,
+                              g->visited, front, next, parent, lvl, d + 1, cfg.bu_probe,
                               (unsigned long long *)slot_next, slot_zero, 0);
                 } else if (two_pass) {
                     // two passes: hub probes over the words, then the rows of
@@ -3250,13 +3318,13 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                                   grid_cap(g->nw_pad / kWarpTile, kBlock / 32, g->hub_stream_occ),
                                   kBlock, hub_stream_smem_bytes(cfg.hub_stream_stages), st,
                                   g->hubc, g->wrank, g->wmeta, g->nw_pad, g->visited, front, next,
-                                  g->pend, parent, level, d + 1, (unsigned long long *)slot_next,
+                                  g->pend, parent, lvl, d + 1, (unsigned long long *)slot_next,
                                   slot_zero, n, root);
                     } else {
                         GB_LAUNCH(bu_hubc_kernel,
                                   grid_cap(g->nw_pad, kBlock / 32 * 8, g->hubc_blocks_per_sm),
                                   kBlock, 0, st, g->hubc, g->wrank, g->nw_pad, g->visited, front,
-                                  next, g->pend, parent, level, d + 1,
+                                  next, g->pend, parent, lvl, d + 1,
                                   (unsigned long long *)slot_next, slot_zero, filled ? 0 : 1,
                                   g->base_vis, n, root);
                     }
@@ -3269,7 +3337,7 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                               grid_cap((active + 31) / 32, kBlock / 32, g->bu_list_blocks_per_sm),
                               kBlock, 0, st, g->off, g->idx, nullptr, 0, q_next,
                               (const unsigned long long *)(slot_cur + T_ULIST), g->visited, front,
-                              next, parent, level, d + 1, cfg.bu_probe,
+                              next, parent, lvl, d + 1, cfg.bu_probe,
                               (unsigned long long *)slot_next, slot_zero, 1);
                 } else {
                     if (!filled) {
@@ -3279,7 +3347,7 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                     decltype(BU1) const kernels[6] = {BU1, BU2, BU4, BU1H, BU2H, BU4H};
                     auto bu = kernels[bsel];
                     GB_LAUNCH(bu, bu_grid, kBlock, 0, st, g->off, g->idx, g->head, g->nw_pad,
-                              g->visited, front, next, parent, level, d + 1, cfg.bu_probe,
+                              g->visited, front, next, parent, lvl, d + 1, cfg.bu_probe,
                               (unsigned long long *)slot_next, slot_zero, bu_span_w, hskip);
                 }
                 have_queue = false;
@@ -3307,12 +3375,23 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
             m_u -= m_new;
             n_f = found;
             m_f = m_new;
-            std::swap(front, next);
+            if (lpass) {
+                front = next;
+                next = g->ring + (int64_t)((d + 2) % kLevelRing) * g->nw_pad;
+            } else {
+                std::swap(front, next);
+            }
             std::swap(q_cur, q_next);
         }
         if (!filled) {
             const bfs_status fs = fill_outputs();
             if (fs != BFS_OK) return fs;
+        }
+        if (!level_direct) {
+            // slot j of the ring holds level j, for every layer run
+            const int slots = (int)std::min<size_t>(g->last.size() + 1, kLevelRing);
+            GB_LAUNCH(level_pass_kernel, grid_cap(g->nw_pad, kBlock / 32 * 8, 8), kBlock, 0, st,
+                      g->ring, g->nw_pad, slots, n, level);
         }
         GB_CK(cudaStreamSynchronize(st));  // outputs complete, late errors surface
         g->last_component_edges = degree_sum / 2;

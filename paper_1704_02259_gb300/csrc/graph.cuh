@@ -19,6 +19,7 @@ constexpr int kBlock = 256;
 constexpr int kBigBatch = 1024;
 constexpr int64_t kQueueModeMaxEdges = 1 << 18;
 constexpr int kTdK = 4;  // edges per lane in flight in the warp and grid top-down paths
+constexpr int kLevelRing = 16;  // frontier bitmaps kept for the level pass
 
 }  // namespace gbfs
 
@@ -52,6 +53,9 @@ struct bfs_graph {
     uint32_t *base_vis = nullptr;  // bits that start every traversal visited:
                                    // degree-0 vertices and ids past n
     int32_t *q_a = nullptr, *q_b = nullptr, *big = nullptr;
+    // level pass: kLevelRing frontier bitmaps of nw_pad words (slot j holds
+    // the vertices of level j), allocated on first use
+    uint32_t *ring = nullptr;
     int32_t *parent_scratch = nullptr, *level_scratch = nullptr;
     // host_async: two device output pairs used in turn, copied to the host on
     // copy_st; hout_done[i] marks the end of pair i's copy

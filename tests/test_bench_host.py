@@ -30,6 +30,7 @@ def test_byte_models():
     assert bench.one_sweep_bytes(1024, 5000) == 20000 + 8200 + 256 + 8192
     # 3n/4 + 4 per probed vertex + 8 per written vertex
     assert bench.hub_sweep_bytes(1024, 300, 20) == 768 + 1200 + 160
+    assert bench.hub_sweep_bytes(1024, 300, 20, 4) == 768 + 1200 + 80
     # 1e9 edges at 1000 GB/s with 1e10 bytes per traversal: 100 GTEPS
     assert bench.roofline_teps(1e9, 1000.0, 1e10) == pytest.approx(1e11)
     # batched: k = 128 (W = 2), n = 1000, two layers examining 10 and 30

@@ -214,7 +214,8 @@ def test_large_top_down_layers(pat, loop):
 
 
 @pytest.mark.parametrize("cfg", [dict(), dict(forced=[0, 0, 1]), dict(forced=[1]),
-                                 dict(bu_list_percent=100), dict(forced=[0])])
+                                 dict(bu_list_percent=100), dict(forced=[0]), dict(level_pass=0),
+                                 dict(level_pass=0, forced=[1])])
 @pytest.mark.parametrize("loop", [0, 3, 4])
 def test_outputs_written_by_first_sweep(cfg, loop):
     # scale 21 with the host loop: dense bottom-up layers run in two passes
@@ -658,6 +659,20 @@ def test_graph_loop_layer_records_equal_host_loop(scale):
             assert oracle.check_parents(o_off, o_idx, int(r), lx, px) == 0
             assert [{k: x[k] for k in keys} for x in gx.stats().layers] == recs_h
             assert gx.stats().component_edges == ce_h
+
+
+@pytest.mark.parametrize("level_pass", [0, 1])
+@pytest.mark.parametrize("pat", ["td", "bu", "alt"])
+def test_level_pass_on_deep_paths(level_pass, pat):
+    # paths of 15, 16, 17 and 300 vertices: depths around the 16-slot ring
+    # of the level pass (levels written after the traversal, or written so
+    # far at the flush before the ring wraps and stored as found after it)
+    for n in (15, 16, 17, 18, 300):
+        s, d = inputs.path_edges(n)
+        o_off, o_idx, g = make(n, s, d, forced=FORCED[pat], level_pass=level_pass,
+                               device_loop=0)
+        for r in sorted({0, n // 2, n - 1}):
+            check_run(o_off, o_idx, g, r, forced=FORCED[pat])
 
 
 def test_timing_modes():
