@@ -743,27 +743,49 @@ __device__ __forceinline__ void td_post_phase(const int64_t *__restrict__ off,
                                               int32_t *__restrict__ level, int32_t new_level,
                                               unsigned long long *next_nf,
                                               unsigned long long *next_mf) {
+    // A warp takes 32 words per round (one coalesced load, lane i word i)
+    // and then gives each lane one of the round's set bits at a time: lane j
+    // finds the word holding the j-th set bit by a binary search over the
+    // lanes' exclusive bit counts (shuffles) and the bit by halving popcounts.
+    // The row bounds of up to 32 found vertices are then loaded together.
     const unsigned lane = lane_id();
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int64_t my_nf = 0, my_mf = 0;
-    for (int64_t w0 = gw * 8; w0 < nw; w0 += tw * 8) {
-        uint32_t x[8];
+    for (int64_t w0 = gw * 32; w0 < nw; w0 += tw * 32) {
+        const uint32_t x = w0 + lane < nw ? ld<CO>(next + w0 + lane) : 0u;
+        const int cnt = __popc(x);
+        int tot;
+        const int excl = warp_exclusive_scan(cnt, &tot);
+        my_nf += cnt;
+        for (int base = 0; base < tot; base += 32) {
+            const int j = base + (int)lane;
+            int owner = 0;  // the last lane whose exclusive count is <= j
 #pragma unroll
-        for (int k = 0; k < 8; ++k) x[k] = w0 + k < nw ? ld<CO>(next + w0 + k) : 0u;
-        int64_t b[8], e[8];
+            for (int step = 16; step > 0; step >>= 1) {
+                const int cand = owner + step;
+                const int ec = __shfl_sync(0xffffffffu, excl, cand & 31);
+                if (cand < 32 && ec <= j) owner = cand;
+            }
+            const uint32_t xo = __shfl_sync(0xffffffffu, x, owner);
+            const int eo = __shfl_sync(0xffffffffu, excl, owner);
+            if (j < tot) {
+                // position of set bit number r of xo
+                uint32_t m = xo;
+                int r = j - eo, pos = 0;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int64_t v = (w0 + k) * 32 + lane;
-            const bool on = (x[k] >> lane) & 1u;
-            b[k] = on ? off[v] : 0;
-            e[k] = on ? off[v + 1] : 0;
-            if (on && level) level[v] = new_level;
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            my_mf += e[k] - b[k];
-            my_nf += (x[k] >> lane) & 1u;
+                for (int h = 16; h > 0; h >>= 1) {
+                    const int c = __popc(m & ((1u << h) - 1u));
+                    if (r >= c) {
+                        r -= c;
+                        m >>= h;
+                        pos += h;
+                    }
+                }
+                const int64_t v = (w0 + owner) * 32 + pos;
+                my_mf += off[v + 1] - off[v];
+                if (level) level[v] = new_level;
+            }
         }
     }
     block_add3(my_nf, my_mf, 0, next_nf, next_mf, nullptr);
@@ -3280,7 +3302,7 @@ extern "C" BFS_API bfs_status bfs_run(bfs_graph *g, int32_t root, int32_t *level
                               (unsigned long long *)(slot_next + T_MF));
                 }
                 if (defer)
-                    GB_LAUNCH(td_post_kernel, grid_cap(g->nw, kBlock / 4, 8), kBlock, 0, st,
+                    GB_LAUNCH(td_post_kernel, grid_cap(g->nw, kBlock, 8), kBlock, 0, st,
                               g->off, next, g->nw, lvl, d + 1,
                               (unsigned long long *)(slot_next + T_NF),
                               (unsigned long long *)(slot_next + T_MF));
