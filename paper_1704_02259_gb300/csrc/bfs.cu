@@ -1067,11 +1067,13 @@ __global__ void __launch_bounds__(kBlock) bits_list_kernel(const uint32_t *__res
 
 
 // Bottom-up step over a compacted list of the vertices still to find: one
-// lane per vertex, so a sparse layer keeps every lane busy. Same probe and
-// warp-cooperative tail as bu_kernel (first frontier neighbour in CSR
-// order, after the head record's probe when head is set); a found vertex
-// sets its next and visited bits with atomicOr, since no warp owns its word
-// here.
+// lane per vertex, so a sparse layer keeps every lane busy. Each lane tests
+// the first entries of its row itself, then the warp scans the rest of its
+// lanes' rows together (first frontier neighbour in CSR order, after the
+// head record's probe when head is set); a found vertex sets its next and
+// visited bits with atomicOr, since no warp owns its word here.
+constexpr int kFlat = 2;  // 32-entry chunks per round of the warp's flat row scan
+
 template <bool CO>
 __device__ __forceinline__ void bu_list_phase(
     const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
@@ -1172,41 +1174,70 @@ __device__ __forceinline__ void bu_list_phase(
                 }
             }
         }
-        unsigned pend = __ballot_sync(0xffffffffu, have && !found && lim < deg);
-        while (pend) {
-            const int L = __ffs(pend) - 1;
-            pend &= pend - 1;
-            const int32_t *lrow =
-                (const int32_t *)__shfl_sync(0xffffffffu, (unsigned long long)row, L);
-            const int ld = __shfl_sync(0xffffffffu, deg, L);
-            bool hit_any = false;
-            for (int q0 = lim; q0 < ld; q0 += 64) {
-                int32_t uu[2];
-                bool hit[2];
+        // Rows longer than lim: the warp scans the rest of all its lanes'
+        // rows as one sequence, kFlat x 32 entries per round whatever the
+        // rows' lengths (a short remainder no longer takes a whole round of
+        // dependent loads). A row leaves the sequence at its first frontier
+        // neighbour; the entries after it in the same round are loaded but
+        // not counted, so parent and examined counts are those of a scan in
+        // CSR order.
+        int rem = (have && !found && lim < deg) ? deg - lim : 0;
+        // address of sequence position 0 of this lane's rest (rest entry j of
+        // the round is at seq + 4 j, for j in [excl, excl + rem))
+        unsigned long long seq = (unsigned long long)(row + lim);
+        while (__any_sync(0xffffffffu, rem > 0)) {
+            int tot;
+            const int excl = warp_exclusive_scan(rem, &tot);
+            const unsigned long long at = seq - 4ull * (unsigned)excl;
+            int32_t uu[kFlat];
+            unsigned hb[kFlat];
 #pragma unroll
-                for (int t = 0; t < 2; ++t) {
-                    const int q = q0 + 32 * t + (int)lane;
-                    uu[t] = q < ld ? __ldg(lrow + q) : -1;
+            for (int c = 0; c < kFlat; ++c) {
+                const int j = 32 * c + (int)lane;
+                // owner = the last lane whose exclusive prefix is <= j
+                int o = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int e = __shfl_sync(0xffffffffu, excl, o + step);
+                    if (e <= j) o += step;
                 }
+                const unsigned long long oat = __shfl_sync(0xffffffffu, at, o);
+                uu[c] = j < tot ? __ldg(reinterpret_cast<const int32_t *>(oat + 4ull * (unsigned)j))
+                                : -1;
+            }
 #pragma unroll
-                for (int t = 0; t < 2; ++t)
-                    hit[t] = uu[t] >= 0 && ((ldro<CO>(front + (uu[t] >> 5)) >> (uu[t] & 31)) & 1u);
-                const unsigned h0 = __ballot_sync(0xffffffffu, hit[0]);
-                const unsigned h1 = __ballot_sync(0xffffffffu, hit[1]);
-                if (h0 | h1) {
-                    const int t = h0 ? 0 : 1;
-                    const int first = __ffs(h0 ? h0 : h1) - 1;
-                    const int32_t pu = __shfl_sync(0xffffffffu, t ? uu[1] : uu[0], first);
-                    if ((int)lane == L) {
-                        found = true;
-                        p = pu;
-                        ex += (q0 - lim) + 32 * t + first + 1;
-                    }
-                    hit_any = true;
-                    break;
+            for (int c = 0; c < kFlat; ++c)
+                hb[c] = __ballot_sync(0xffffffffu, uu[c] >= 0 && ((ldro<CO>(front + (uu[c] >> 5)) >>
+                                                                   (uu[c] & 31)) & 1u));
+            // this lane's entries of the round: [excl, hi); the first hit among them
+            const int hi = min(excl + rem, 32 * kFlat);
+            int first = -1;
+#pragma unroll
+            for (int c = kFlat - 1; c >= 0; --c) {
+                const int a = max(excl - 32 * c, 0), b = min(hi - 32 * c, 32);
+                if (a < b) {
+                    const unsigned m = hb[c] & (b == 32 ? ~0u : (1u << b) - 1u) & ~((1u << a) - 1u);
+                    if (m) first = 32 * c + __ffs(m) - 1;
                 }
             }
-            if (!hit_any && (int)lane == L) ex += ld - lim;
+            int32_t pu = -1;
+#pragma unroll
+            for (int c = 0; c < kFlat; ++c) {
+                const int32_t x = __shfl_sync(0xffffffffu, uu[c], first & 31);
+                if (first >> 5 == c) pu = x;
+            }
+            if (rem > 0 && excl < 32 * kFlat) {
+                if (first >= 0) {
+                    found = true;
+                    p = pu;
+                    ex += (deg - rem - lim) + (first - excl) + 1;  // up to and including the hit
+                    rem = 0;
+                } else {
+                    rem -= hi - excl;
+                    seq += 4ull * (unsigned)(hi - excl);
+                    if (rem == 0) ex += deg - lim;
+                }
+            }
         }
         if (found) {
             const uint32_t bit = 1u << (v & 31);
