@@ -1452,18 +1452,28 @@ static_assert(kWarpStageBytes % 16 == 0, "stages keep bulk-copy destinations 16-
 static_assert(kWarpTile % 4 == 0 && 32 % kWarpTile == 0, "tiles of 16-byte word groups that "
               "never cross nw_pad (a multiple of 32)");
 
-// Predicated global accesses written as one predicated instruction each.
-__device__ __forceinline__ uint32_t ld_hint_if(const uint32_t *p, uint64_t pol, bool pred) {
+// Predicated global accesses written as one predicated instruction each. The
+// predicate is a word that is nonzero where the access happens, made by bit
+// operations on the bitmap words, so no boolean is turned back into a word.
+__device__ __forceinline__ uint32_t ld_hint_nz(const uint32_t *p, uint64_t pol, uint32_t u) {
     uint32_t v;
     asm("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %3, 0;\n\tmov.b32 %0, 0;\n\t"
         "@q ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;\n\t}"
         : "=r"(v)
-        : "l"(p), "l"(pol), "r"((unsigned)pred));
+        : "l"(p), "l"(pol), "r"(u));
     return v;
 }
-__device__ __forceinline__ void st_cs_if(int32_t *p, int32_t v, bool pred) {
+__device__ __forceinline__ void st_cs_nz(int32_t *p, int32_t v, uint32_t u) {
     asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q st.global.cs.b32 [%0], %1;\n\t}"
-                 ::"l"(p), "r"(v), "r"((unsigned)pred)
+                 ::"l"(p), "r"(v), "r"(u)
+                 : "memory");
+}
+// Both stores under one predicate (parent and level of the same vertex).
+__device__ __forceinline__ void st2_cs_nz(int32_t *p1, int32_t v1, int32_t *p2, int32_t v2,
+                                          uint32_t u) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+                 "@q st.global.cs.b32 [%0], %1;\n\t@q st.global.cs.b32 [%2], %3;\n\t}"
+                 ::"l"(p1), "r"(v1), "l"(p2), "r"(v2), "r"(u)
                  : "memory");
 }
 
@@ -1552,41 +1562,52 @@ __global__ void __launch_bounds__(kBlock, 3) bu_hubc_stream_kernel(
             // the index stays inside the stage's records for every lane (the
             // rank of the next degree >= 1 vertex), so the load needs no guard
             h[k] = rec[m.y - a0 + __popc(~m.x & lt)];
-            fw[k] = ld_hint_if(front + ((h[k] & 0x7fffffffu) >> 5), pol_keep,
-                               (vw[k] & bit) == 0u);  // unvisited implies degree >= 1
+            // fw stays 0 where the lane is visited (unvisited implies degree >= 1)
+            fw[k] = ld_hint_nz(front + ((h[k] & 0x7fffffffu) >> 5), pol_keep, ~vw[k] & bit);
         }
         uint32_t fbw[kWarpTile], d1w[kWarpTile];
-        // per-tile output pointers, the tile's vertices below n (ids past n
-        // are set in both vw and bw) and the root's position in the tile (a
-        // root of degree 0 is not "reached before" by the bitmaps)
         const int64_t vbase = t * (kWarpTile * 32);
         int32_t *const par_t = parent + vbase + lane;
         // level null: levels are written after the traversal (level pass)
         const bool lev_on = level != nullptr;
         int32_t *const lev_t = (lev_on ? level : parent) + vbase + lane;  // stores need lev_on
-        int lim = 0, rloc = -1;
         if constexpr (INIT) {
-            lim = (int)min((int64_t)(kWarpTile * 32), n - vbase) - (int)lane;
-            const int64_t rk = (int64_t)root - vbase;
-            rloc = (rk >= 0 && rk < kWarpTile * 32) ? (int)rk - (int)lane : -1;
+            // A vertex not reached before is unvisited or of degree 0 (set in
+            // both the visited and the base word) and gets -1 outputs, except
+            // the ids past n (set in both as well) and a root of degree 0. In
+            // the one or two tiles that hold those, they leave the tile's base
+            // words here, so they count as reached and get no store.
+            if (vbase + kWarpTile * 32 > n ||
+                (uint64_t)((int64_t)root - vbase) < (uint64_t)(kWarpTile * 32)) {
+#pragma unroll
+                for (int k = 0; k < kWarpTile; ++k) {
+                    const int64_t v = vbase + k * 32 + lane;
+                    bw[k] &= ~__ballot_sync(0xffffffffu, v >= n || v == (int64_t)root);
+                }
+            }
         }
 #pragma unroll
         for (int k = 0; k < kWarpTile; ++k) {
-            const bool probed = (vw[k] & bit) == 0u;
+            // fw is 0 where the lane is visited: a set bit is a probed hit
+            const uint32_t fbit = (fw[k] >> (h[k] & 31u)) & 1u;
+            const bool found = fbit != 0u;
             const int32_t hub = (int32_t)(h[k] & 0x7fffffffu);
-            const bool found = probed && ((fw[k] >> (hub & 31)) & 1u);
             fbw[k] = __ballot_sync(0xffffffffu, found);
             d1w[k] = __ballot_sync(0xffffffffu, (int32_t)h[k] < 0);  // degree 1 (where probed)
             if constexpr (INIT) {
                 // one store per array for the whole warp (a hit's values,
                 // else the -1 of a vertex not reached before): whole sectors
-                const bool minus = !found && !(vw[k] & ~bw[k] & bit) && k * 32 < lim &&
-                                   k * 32 != rloc;
-                st_cs_if(par_t + k * 32, found ? hub : -1, found || minus);
-                st_cs_if(lev_t + k * 32, found ? new_level : -1, (found || minus) && lev_on);
+                const uint32_t out = ~(vw[k] & ~bw[k]) & bit;
+                if (lev_on)
+                    st2_cs_nz(par_t + k * 32, found ? hub : -1, lev_t + k * 32,
+                              found ? new_level : -1, out);
+                else
+                    st_cs_nz(par_t + k * 32, found ? hub : -1, out);
             } else {
-                st_cs_if(par_t + k * 32, hub, found);
-                st_cs_if(lev_t + k * 32, new_level, found && lev_on);
+                if (lev_on)
+                    st2_cs_nz(par_t + k * 32, hub, lev_t + k * 32, new_level, fbit);
+                else
+                    st_cs_nz(par_t + k * 32, hub, fbit);
             }
         }
         if (lane == 0) {
