@@ -1348,20 +1348,14 @@ __global__ void __launch_bounds__(kBlock, 4) bu_hub_kernel(
 // bu_list_phase with mf_left). The rank of vertex v among the degree >= 1
 // vertices is wrank[v / 32] + the degree >= 1 vertices before it in its word.
 //
-// bu_hubc_stream_kernel (dense sweeps): the block's bulk-copy engine
-// (cp.async.bulk, completion counted in bytes on an mbarrier) streams the
-// records of a tile of kHubTileWords bitmap words (1024 vertices, at most
-// 4 KB of records) with the tile's visited, base and rank words into shared
-// memory, S tiles ahead, so the warps make only the frontier-bit loads (L2)
-// and the stores. bu_hubc_kernel (sparse sweeps) gathers the records of the
-// unvisited vertices itself, 8 words per warp round.
+// bu_hubc_stream_kernel (dense sweeps): bulk copies (cp.async.bulk,
+// completion counted in bytes on an mbarrier) stream each warp's tiles of 8
+// bitmap words (256 vertices, at most 1 KB of records) with the tile's
+// visited, base and rank words into the warp's shared-memory ring, S tiles
+// ahead, so the lanes make only the frontier-bit loads (L2) and the stores.
+// bu_hubc_kernel (sparse sweeps) gathers the records of the unvisited
+// vertices itself, 8 words per warp round.
 // ---------------------------------------------------------------------------
-constexpr int kHubTileWords = 32;
-constexpr int kHubTileVerts = kHubTileWords * 32;
-// records of one tile, rounded out to 16-byte boundaries at both ends
-constexpr unsigned kHubTileRecBytes = (kHubTileVerts + 8) * 4;
-constexpr int kHubWordsPerWarp = kHubTileWords / (kBlock / 32);
-static_assert(kHubTileWords % (kBlock / 32) == 0, "the tile's words split evenly over the warps");
 constexpr unsigned long long kHubWaitNs = 1000000000ull;  // 1 s per bounded wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
