@@ -517,42 +517,42 @@ __device__ __forceinline__ void ms_td_phase(
                 }
             }
         }
-        return;
-    }
-    for (int64_t base = gw * 32; base < cnt; base += tw * 32) {
-        const int64_t i = base + lane;
-        int64_t u = 0, beg = 0, end = 0;
-        unsigned long long cu[W];
+    } else {
+        for (int64_t base = gw * 32; base < cnt; base += tw * 32) {
+            const int64_t i = base + lane;
+            int64_t u = 0, beg = 0, end = 0;
+            unsigned long long cu[W];
 #pragma unroll
-        for (int j = 0; j < W; ++j) cu[j] = 0ull;
-        if (i < cnt) {
-            u = ld<CO>(list + i);
-            beg = off[u];
-            end = off[u + 1];
-            load_lanes<W, CO>(cur + u * W, cu);
-        }
-        const bool wide = end - beg >= 32;
-        if (!wide) {
-            // 4 edges in flight per lane
-            for (int64_t e = beg; e < end; e += 4) {
-                int64_t v[4];
-#pragma unroll
-                for (int t = 0; t < 4; ++t) v[t] = e + t < end ? (int64_t)__ldg(idx + e + t) : -1;
-#pragma unroll
-                for (int t = 0; t < 4; ++t)
-                    if (v[t] >= 0) ms_push<W>(cu, v[t], nxt);
+            for (int j = 0; j < W; ++j) cu[j] = 0ull;
+            if (i < cnt) {
+                u = ld<CO>(list + i);
+                beg = off[u];
+                end = off[u + 1];
+                load_lanes<W, CO>(cur + u * W, cu);
             }
-        }
-        unsigned wm = __ballot_sync(0xffffffffu, wide);
-        while (wm) {
-            const int L = __ffs(wm) - 1;
-            wm &= wm - 1;
-            const int64_t lb = __shfl_sync(0xffffffffu, beg, L);
-            const int64_t le = __shfl_sync(0xffffffffu, end, L);
-            unsigned long long cL[W];
+            const bool wide = end - beg >= 32;
+            if (!wide) {
+                // 4 edges in flight per lane
+                for (int64_t e = beg; e < end; e += 4) {
+                    int64_t v[4];
 #pragma unroll
-            for (int j = 0; j < W; ++j) cL[j] = __shfl_sync(0xffffffffu, cu[j], L);
-            for (int64_t e = lb + lane; e < le; e += 32) ms_push<W>(cL, __ldg(idx + e), nxt);
+                    for (int t = 0; t < 4; ++t) v[t] = e + t < end ? (int64_t)__ldg(idx + e + t) : -1;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        if (v[t] >= 0) ms_push<W>(cu, v[t], nxt);
+                }
+            }
+            unsigned wm = __ballot_sync(0xffffffffu, wide);
+            while (wm) {
+                const int L = __ffs(wm) - 1;
+                wm &= wm - 1;
+                const int64_t lb = __shfl_sync(0xffffffffu, beg, L);
+                const int64_t le = __shfl_sync(0xffffffffu, end, L);
+                unsigned long long cL[W];
+#pragma unroll
+                for (int j = 0; j < W; ++j) cL[j] = __shfl_sync(0xffffffffu, cu[j], L);
+                for (int64_t e = lb + lane; e < le; e += 32) ms_push<W>(cL, __ldg(idx + e), nxt);
+            }
         }
     }
 }
